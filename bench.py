@@ -1,0 +1,429 @@
+"""LDNI benchmark: one JSON line on stdout.
+
+Workload (one GPU): the 1,310,720-triangle noisy geodesic sphere (frequency
+256, r 0.35, 4-octave radial noise of amplitude 0.05) sampled into the three
+1024^2 LDNIs (exact two-pass), united per axis with a resident LDNI set of a
+(2,3) torus-knot tube (16,384 triangles, sampled once before timing), and
+the volume of each united image.  One step = that whole pass over all rays
+of the three images; value = 3 * 1024^2 rays / step time.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the plain FP64 statement of the
+method) on the host cores instead; multi-GPU runs are independent replicas
+(weak scaling), one process per GPU under torchrun.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "LDNI rays/s & samples/s at 1024²; learned-sized 1-pass vs exact 2-pass speedup"
+RES = 1024
+WORKLOAD = ("noisy geodesic sphere freq 256 (655,362 verts / 1,310,720 tris, r 0.35, 4-octave radial noise 0.05)"
+            " -> 3 LDNIs at 1024^2 (exact two-pass) -> union with resident (2,3) torus-knot LDNIs -> volume")
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _meshes():
+    import meshgen
+    return meshgen.scale_sphere(), meshgen.torus_knot(2, 3, 0.25, 0.1, 0.035, 256, 32)
+
+
+# ----------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "", 1).isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "", 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg
+# ----------------------------------------------------------------------------
+def _oracle_step(sphere, knot_ref, axes, res):
+    import oracle
+    o = (-0.5, -0.5, -0.5)
+    rays = 0
+    for a in axes:
+        L = oracle.as_f32(oracle.sample(*sphere, o, 1.0, res, a, "scan"))
+        U = oracle.boolean(L, knot_ref[a], "union")
+        oracle.volume(U, 1.0 / res)
+        rays += res * res
+    return rays
+
+
+def cpu_baseline(sphere, knot, budget_s: float = 10.0) -> dict:
+    """The oracle as it stands (single thread) on a bounded sample of the
+    same workload: whole steps (3 axes) repeated for about budget_s."""
+    import oracle
+    o = (-0.5, -0.5, -0.5)
+    knot_ref = [oracle.as_f32(oracle.sample(*knot, o, 1.0, RES, a, "scan")) for a in range(3)]
+    t0 = time.perf_counter()
+    rays, steps = 0, 0
+    while True:
+        rays += _oracle_step(sphere, knot_ref, (0, 1, 2), RES)
+        steps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": rays / dt, "unit": "rays/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full steps (3 axes at {RES}^2: scan-mode FP64 sampling, union, volume), "
+                      f"{dt:.1f} s single-threaded C"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    sphere, knot = _meshes()
+    o = (-0.5, -0.5, -0.5)
+    knot_ref = [oracle.as_f32(oracle.sample(*knot, o, 1.0, RES, a, "scan")) for a in range(3)]
+    for w in range(args.warmup):
+        _oracle_step(sphere, knot_ref, (w % 3,), RES)
+    times = []
+    rays = 0
+    for k in range(args.steps):
+        t0 = time.perf_counter()
+        rays += _oracle_step(sphere, knot_ref, (k % 3,), RES)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = rays / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "res": RES,
+                       "reference_step": "one axis per step (x, y, z in turn): oracle sampling + union + volume"},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of one axis each, single-threaded C"},
+            "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: list, n_union: list) -> float:
+    """Bytes the method must move for one launch of kernel `kid` (all three
+    images where the kernel covers them; per launch)."""
+    N = res * res
+    mesh = 12.0 * nv + 12.0 * nt
+    ntot = float(sum(n))
+    table = {
+        1: mesh + 3 * 4.0 * N,                        # count: mesh read, counts written
+        6: mesh + 3 * 4.0 * (N + 1) + 20.0 * ntot,    # fill: mesh, offsets read, samples written
+        8: 3 * 4.0 * (N + 1) + 40.0 * ntot,           # sort: offsets, samples read + written
+        3: 3 * 4.0 * N, 5: 3 * 8.0 * N,               # scan phases
+    }
+    if kid in table:
+        return table[kid]
+    a_mean = lambda xs: float(sum(xs)) / 3.0
+    if kid == 9:   # boolean count, one image
+        return 8.0 * (N + 1) + 4.0 * (a_mean(n) + a_mean(n_knot)) + 4.0 * N
+    if kid == 10:  # boolean write, one image
+        return 12.0 * (N + 1) + 20.0 * (a_mean(n) + a_mean(n_knot)) + 20.0 * a_mean(n_union)
+    if kid == 11:  # volume, one image
+        return 4.0 * (N + 1) + 4.0 * a_mean(n_union)
+    return 0.0
+
+
+def run_ours(args):
+    import torch
+    import paper_1009_0794_gb300 as ldni
+    from paper_1009_0794_gb300 import _lib
+
+    ws, rank, local = _dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = _lib.load()
+    (sv, st), (kv, kt) = _meshes()
+    grid = ldni.Grid.cube((-0.5, -0.5, -0.5), 1.0, RES)
+    vt = torch.from_numpy(sv).to(dev)
+    tt = torch.from_numpy(st).to(dev)
+    # resident partner LDNIs and exact capacities from one sizing call
+    K = ldni.sample(kv, kt, grid, "all", check_odd=True)
+    A0 = ldni.sample(vt, tt, grid, "all", check_odd=True)
+    n_sphere = [L.n for L in A0]
+    plan = ldni.SamplePlan(len(sv), len(st), grid, n_sphere)
+    bws = torch.empty(ldni.boolean_workspace_size(RES), dtype=torch.uint8, device=dev)
+    vws = torch.empty(ldni.volume_workspace_size(RES), dtype=torch.uint8, device=dev)
+    binfo = ldni.new_info()
+    U = [ldni.empty_layers(grid, a, plan.outs[a].capacity + K[a].capacity) for a in range(3)]
+    vols = torch.zeros(3, dtype=torch.float64, device=dev)
+    vol_views = [vols[a:a + 1] for a in range(3)]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step():
+        plan.run(vt, tt)
+        for a in range(3):
+            ldni.boolean(plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=False)
+            ldni.volume(U[a], out=vol_views[a], ws=vws, info=binfo, sync=False)
+
+    # per-kernel profile during warm-up: find the dominant kernel
+    cap = 64
+    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    import ctypes
+    arr_b = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_b])
+    arr_e = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_e])
+    ids = (ctypes.c_int32 * cap)()
+    for w in range(max(args.warmup, 3)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    _lib.check(lib.ldni_profile_set(arr_b, arr_e, ids, cap, 0), "ldni_profile_set")
+    flush.zero_()
+    step()
+    torch.cuda.synchronize()
+    nrec = min(int(lib.ldni_profile_recorded()), cap)
+    _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
+    per_kernel = {}
+    for k in range(nrec):
+        per_kernel.setdefault(int(ids[k]), []).append(ev_b[k].elapsed_time(ev_e[k]))
+    totals = {kid: sum(v) for kid, v in per_kernel.items()}
+    dominant = max(totals, key=totals.get)
+    launches_per_call = {kid: len(v) for kid, v in per_kernel.items()}
+    meta = plan.finish()
+    n_union = [int(x) for x in [0, 0, 0]]
+    # exact union sizes (one sync, outside the timed region)
+    for a in range(3):
+        Ua = ldni.boolean(plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=True)
+        n_union[a] = Ua.n
+
+    # timed region: K steps, per-step events, L2 flushed between steps,
+    # dominant kernel timed by its own events
+    steps = args.steps
+    dk_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps * launches_per_call[dominant])]
+    dk_e = [torch.cuda.Event(enable_timing=True) for _ in range(len(dk_b))]
+    dk_arr_b = (ctypes.c_void_p * len(dk_b))(*[e.cuda_event for e in dk_b])
+    dk_arr_e = (ctypes.c_void_p * len(dk_e))(*[e.cuda_event for e in dk_e])
+    st_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    st_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    # settle clocks under load before the measured steps
+    t_settle = time.perf_counter()
+    while time.perf_counter() - t_settle < 1.0:
+        flush.zero_()
+        step()
+        torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = int(lib.ldni_launch_count())
+    _lib.check(lib.ldni_profile_set(dk_arr_b, dk_arr_e, None, len(dk_b), dominant), "ldni_profile_set")
+    for k in range(steps):
+        flush.zero_()
+        st_b[k].record()
+        step()
+        st_e[k].record()
+    torch.cuda.synchronize()
+    _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
+    launches = int(lib.ldni_launch_count()) - launches0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [st_b[k].elapsed_time(st_e[k]) for k in range(steps)]
+    total_ms = float(sum(step_ms))
+    dk_ms = [dk_b[k].elapsed_time(dk_e[k]) for k in range(len(dk_b))]
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    plan.finish()  # raises if any step overflowed or mis-snapped
+
+    rays_per_step = 3 * RES * RES
+    value = ws * rays_per_step * steps / (total_ms * 1e-3)
+    samples_per_s = ws * sum(n_sphere) * steps / (total_ms * 1e-3)
+
+    # end to end through the public API from pinned host buffers
+    e2e = None
+    if rank == 0 or True:
+        hv = torch.from_numpy(sv).pin_memory()
+        ht = torch.from_numpy(st).pin_memory()
+        e2e_steps = max(3, min(steps, 20))
+        outs_host = None
+        for rep in range(2 + e2e_steps):
+            if rep == 2:
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                h0 = time.perf_counter()
+            dv = hv.to(dev, non_blocking=True)
+            dt_ = ht.to(dev, non_blocking=True)
+            A = ldni.sample(dv, dt_, grid, "all")
+            res_host = []
+            vol_dev = torch.zeros(3, dtype=torch.float64, device=dev)
+            for a in range(3):
+                Ua = ldni.boolean(A[a], K[a], "union", ws=bws)
+                ldni.volume(Ua, out=vol_dev[a:a + 1], ws=vws, sync=False)
+                res_host.append(Ua)
+            if outs_host is None:
+                outs_host = []
+                for Ua in res_host:
+                    outs_host.append([torch.empty(Ua.offsets.numel(), dtype=torch.int32, pin_memory=True)] +
+                                     [torch.empty(max(Ua.n, 1) * 2, dtype=torch.float32, pin_memory=True)
+                                      for _ in range(4)] +
+                                     [torch.empty(max(Ua.n, 1) * 2, dtype=torch.int32, pin_memory=True)])
+                vol_host = torch.empty(3, dtype=torch.float64, pin_memory=True)
+            d2h = 0
+            for Ua, hb in zip(res_host, outs_host):
+                n = Ua.n
+                srcs = [Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]]
+                for s_, h_ in zip(srcs, hb):
+                    h_[:s_.numel()].copy_(s_, non_blocking=True)
+                    d2h += s_.numel() * s_.element_size()
+            vol_host.copy_(vol_dev, non_blocking=True)
+            d2h += 24
+        e1 = torch.cuda.Event(enable_timing=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms = e0.elapsed_time(e1) / e2e_steps
+        e2e = {"value": ws * rays_per_step / (e2e_ms * 1e-3), "unit": "rays/s",
+               "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms, "wall_ms_per_step": 1e3 * (time.perf_counter() - h0) / e2e_steps,
+               "api": "paper_1009_0794_gb300.sample / boolean / volume (exact sizing, one count readback per call)"}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    import json as _json
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = _json.load(fh)
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    dk_avg_ms = float(np.mean(dk_ms)) if dk_ms else float("nan")
+    ab = algorithmic_bytes(dominant, len(sv), len(st), RES, n_sphere, [L.n for L in K], n_union)
+    achieved = ab / (dk_avg_ms * 1e-3) / 1e9
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            tj = _json.load(fh)
+        name = lib.ldni_kernel_name(dominant).decode()
+        if name in tj and tj[name].get("source_hash") == _source_hash():
+            traffic = tj[name]["bytes_per_launch"]
+    except Exception:
+        traffic = None
+    stages = {lib.ldni_kernel_name(k).decode(): {"ms_per_step": float(np.sum(v)), "launches_per_step": len(v)}
+              for k, v in sorted(per_kernel.items())}
+    line = {
+        "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "res": RES, "axes": 3, "verts": len(sv), "tris": len(st),
+                   "mode": "exact2", "partner": "(2,3) torus knot tube, 8,192 verts / 16,384 tris, resident LDNIs",
+                   "l2": "flushed between steps (256 MiB write, outside the per-step events)",
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+        "samples_per_s": samples_per_s,
+        "samples_per_step": int(sum(n_sphere)),
+        "learned_speedup": None,
+        "roofline": {"bound": "hbm", "kernel": lib.ldni_kernel_name(dominant).decode(), "achieved": achieved,
+                     "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dk_avg_ms},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "stages_ms_per_step": stages,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(*_meshes(), budget_s=args.cpu_budget)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def _source_hash() -> str:
+    from paper_1009_0794_gb300 import build as b
+    return b._stamp()[:16]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,230 @@
+/*
+ * ldni.h - C ABI of the GB300 LDNI library (libldni.so).
+ *
+ * Layered Depth-Normal Images (Wang & Chen): a closed triangle mesh is
+ * sampled by the pixel-centre rays of three axis-aligned images; every ray
+ * stores the ascending depths of its crossings with the surface, each with
+ * the unit surface normal (Section 2, Definitions 1-3).  Solids are combined
+ * per ray by 1D Boolean merges (Section 4.1).
+ *
+ * Conventions shared by every call
+ *  - All data pointers are DEVICE pointers (CUDA global memory of the current
+ *    device) unless a parameter says "host".  The caller owns every buffer;
+ *    the library allocates nothing and keeps no device state between calls.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *    NULL = legacy default stream).  Host-side validation errors are returned
+ *    immediately; conditions found on the device (capacity exceeded, odd
+ *    rays, scan overflow) are written to the caller's device `info` block
+ *    (ldni_info_t) and become visible once the stream has reached that point.
+ *  - Grid (Definition 3): one cube [origin, origin + width]^3 shared by the
+ *    three images; res x res pixels of pitch h = width / res.  Axis a in
+ *    {0:x, 1:y, 2:z}; in-plane coordinates (u, v) = (y, z), (z, x), (x, y).
+ *    Pixel (i, j), i along u and j along v, is row p = j * res + i; its ray
+ *    passes through the pixel centre (Section 3) and runs along +a.
+ *  - Depth is the world a-coordinate of a crossing, ascending along the ray
+ *    (Definition 1 measures depth to the viewing plane; the two differ by a
+ *    constant shift per image).
+ *  - Return codes: LDNI_OK (0) or a negative LDNI_E* code (ldni_strerror).
+ */
+#ifndef LDNI_H
+#define LDNI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes -------------------------------------------------- */
+#define LDNI_OK 0
+#define LDNI_EINVAL (-1)          /* bad argument (null pointer, res <= 0, axis, op, ...) */
+#define LDNI_EGRID_MISMATCH (-2)  /* Boolean operands on different grids (Section 4.1.1) */
+#define LDNI_EODD (-3)            /* an input ray has an odd sample count (Definition 4) */
+#define LDNI_ETOOLARGE (-4)       /* res or sample count beyond the int32 CSR range */
+#define LDNI_EWORKSPACE (-5)      /* workspace smaller than the *_workspace_size query */
+#define LDNI_ECUDA (-6)           /* a CUDA runtime call or launch failed */
+#define LDNI_ETIMEOUT (-7)        /* a bounded device wait gave up */
+#define LDNI_ERANGE (-8)          /* a vertex lies too far outside the cube to snap */
+#define LDNI_ECAPACITY (-9)       /* output capacity smaller than the sample count */
+
+/* ---- device-side status bits (ldni_info_t.status) ------------------- */
+#define LDNI_ST_CAPACITY 1u       /* an output had more samples than capacity; extra dropped */
+#define LDNI_ST_ODD 2u            /* an input or sampled ray had an odd count */
+#define LDNI_ST_TOOLARGE 4u       /* a sample total exceeded 2^31 - 1 */
+#define LDNI_ST_TIMEOUT 8u        /* a bounded device wait expired */
+#define LDNI_ST_RANGE 16u         /* a vertex could not be snapped (outside +-2^24 units) */
+#define LDNI_ST_INDEX 32u         /* a triangle referenced a vertex index outside [0, nv) */
+
+/* ---- modes and operations ------------------------------------------ */
+#define LDNI_AXIS_X 0
+#define LDNI_AXIS_Y 1
+#define LDNI_AXIS_Z 2
+#define LDNI_AXIS_ALL 3           /* the three images of Definition 3 in one call */
+
+#define LDNI_MODE_EXACT2 0        /* exact two-pass: count, scan, fill, sort */
+#define LDNI_MODE_LEARNED1 1      /* one pass into learned per-tile capacity, exact redo of overflow */
+
+#define LDNI_OP_UNION 0
+#define LDNI_OP_INTER 1
+#define LDNI_OP_DIFF 2
+
+/* Fixed-point subpixel bits of the snap: pixel centre i sits at 256 i + 128. */
+#define LDNI_SUBPIX_BITS 8
+
+/* ---- data ---------------------------------------------------------- */
+
+/* The cube shared by the three images (Definition 3). */
+typedef struct {
+    float origin[3]; /* minimum corner */
+    float width;     /* cube edge length W > 0 */
+    int32_t res;     /* pixels per image side, 1 .. 8192 */
+} ldni_grid_t;
+
+/* One layered depth-normal image in CSR form (Definitions 1-2).
+ * Samples of ray p are rows offsets[p] .. offsets[p+1]-1, ascending by
+ * (depth, tri_id).  SoA arrays, each `capacity` long; offsets has res*res+1
+ * entries.  tri_id is the index of the sampled triangle ("accurate normal
+ * sampling", Section 3 item 2); in a Boolean result bit 31 marks a sample
+ * taken from the second operand. */
+typedef struct {
+    int32_t *offsets;
+    float *depth;
+    float *nx;
+    float *ny;
+    float *nz;
+    int32_t *tri_id;
+    int64_t capacity; /* host value: length of the five sample arrays */
+} ldni_layers_t;
+
+/* Device block a call reports into (caller-owned, device memory).
+ * n[a]  : number of samples the call produced (or needed) for image a
+ *         (a = the axis, also for single-axis calls); Booleans use n[0].
+ * status: OR of LDNI_ST_* bits; the library ORs into it, the caller clears. */
+typedef struct {
+    int64_t n[3];
+    uint32_t status;
+    uint32_t odd_rays; /* rays with an odd count seen by the call */
+} ldni_info_t;
+
+/* ---- helpers ------------------------------------------------------- */
+
+/* Human-readable text for a return code (static storage, never NULL). */
+const char *ldni_strerror(int code);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ldni_version(void);
+
+/* Grid from a host bbox[6] = {min x, min y, min z, max x, max y, max z}:
+ * origin = bbox min, width = largest extent (the caller pads the box; the
+ * paper uses a working envelope slightly larger than the model, Section 3). */
+int ldni_grid_from_bbox(const float *bbox_host, int32_t res, ldni_grid_t *grid_host);
+
+/* ---- sampling (Section 3; Definitions 1-4; Remark 1) ---------------- */
+
+/* Bytes of device workspace ldni_sample / ldni_sample_count need for a mesh
+ * of nt triangles at grid->res and the given axis (0..2 or LDNI_AXIS_ALL). */
+int ldni_sample_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis, size_t *bytes_host);
+
+/*
+ * Sample a closed triangle mesh into one or three LDNIs.
+ *   verts  : device float[nv][3], world coordinates.
+ *   tris   : device int32[nt][3], vertex indices, outward winding.
+ *   grid   : host pointer to the cube.
+ *   axis   : 0, 1, 2, or LDNI_AXIS_ALL (out then points to 3 layers x, y, z).
+ *   mode   : LDNI_MODE_EXACT2 (this entry point) - count pass, scan, fill
+ *            pass, per-ray sort; the paper's stencil-counted multi-pass
+ *            rendering (Section 3, Appendix A) restated for CUDA.
+ *   out    : host pointer to 1 or 3 ldni_layers_t with caller buffers.
+ *   info   : device ldni_info_t; n[a] receives the sample count of image a.
+ *   ws     : device workspace of at least ldni_sample_workspace_size bytes.
+ * A ray crosses a triangle iff the ray's fixed-point pixel centre lies in the
+ * triangle's snapped projection under the top-left rule, so a shared
+ * non-silhouette edge is crossed once and a silhouette edge 0 or 2 times
+ * (Remark 1); faces parallel to the ray are not sampled (Definition 1 note).
+ * If a count exceeds out[a].capacity the extra samples are dropped, bit
+ * LDNI_ST_CAPACITY is set and info->n[a] holds the size needed.  An odd ray
+ * (a mesh that is not closed or self-intersects, Remark 2) sets LDNI_ST_ODD.
+ */
+int ldni_sample(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                int32_t axis, int32_t mode, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
+                void *stream);
+
+/* First half of ldni_sample (count pass + scan): writes out[a].offsets and
+ * info->n[a] so that a caller can size the sample arrays exactly, then calls
+ * ldni_sample_fill with the same workspace.  Only offsets of `out` are used. */
+int ldni_sample_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                      int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
+                      void *stream);
+
+/* Second half of ldni_sample (fill pass + per-ray sort + CSR write) after
+ * ldni_sample_count on the same workspace, same inputs and same offsets. */
+int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                     int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
+                     void *stream);
+
+/* ---- Boolean (Section 4.1, small-interval removal Section 4.1.1) ----- */
+
+/* Workspace bytes for ldni_boolean at resolution res. */
+int ldni_boolean_workspace_size(int32_t res, size_t *bytes_host);
+
+/*
+ * out = A op B (Section 4.1).  A, B, out: host pointers to layers with device
+ * buffers; grid_a, grid_b: host pointers to the operands' grids, which must
+ * be identical (same origin and sampling rate, Section 4.1.1), else
+ * LDNI_EGRID_MISMATCH.  Per ray the result is the boundary of
+ * {t : op(in_A(t), in_B(t))} where in_X(t) means an odd number of X samples
+ * lie below t; equal depths of A and B are one event; an emitted sample is
+ * copied from A when A's state flips there, else from B (normal inverted for
+ * LDNI_OP_DIFF; tri_id | 0x80000000).  Then every solid interval thinner than
+ * eps (FP32 difference, strict <) is removed.  out->capacity >=
+ * A.capacity + B.capacity always suffices; extra samples beyond capacity are
+ * dropped (LDNI_ST_CAPACITY).  info->n[0] = output count; odd input rays set
+ * LDNI_ST_ODD.
+ */
+int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B, const ldni_grid_t *grid_b,
+                 int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
+                 void *stream);
+
+/* ---- volume ----------------------------------------------------------- */
+
+/* Workspace bytes for ldni_volume at resolution res. */
+int ldni_volume_workspace_size(int32_t res, size_t *bytes_host);
+
+/*
+ * Enclosed volume seen by one LDNI: h^2 * sum over rays of
+ * (d[2k+1] - d[2k]) - the odd-to-even ranges are inside (Section 2, after
+ * Proposition 1).  vol: device double, written.  Deterministic (fixed
+ * reduction order).  Odd rays set LDNI_ST_ODD and are skipped.
+ */
+int ldni_volume(const ldni_layers_t *L, const ldni_grid_t *grid, double *vol, ldni_info_t *info, void *ws,
+                size_t ws_bytes, void *stream);
+
+/* ---- instrumentation (no counterpart in the paper) ------------------- */
+
+/* Number of kernels this process has launched through the library. */
+uint64_t ldni_launch_count(void);
+
+/*
+ * Optional per-kernel timing.  begin_events / end_events: host arrays of
+ * `capacity` cudaEvent_t (created by the caller); kernel_ids: optional host
+ * int32 array of the same length that receives each record's kernel id.
+ * From now on every launch of a kernel whose id equals `filter` (0 = every
+ * kernel) records begin_events[k] before and end_events[k] after it on its
+ * stream, k cycling through 0..capacity-1.  capacity 0 turns recording off.
+ * Host state of the process, not thread-safe; for benchmarks only.
+ */
+int ldni_profile_set(void **begin_events, void **end_events, int32_t *kernel_ids, int32_t capacity, int32_t filter);
+
+/* Records made since the last ldni_profile_set. */
+int64_t ldni_profile_recorded(void);
+
+/* Name of a kernel id (1 count_tri, 2 count_big, 3 scan_chunk_totals,
+ * 4 scan_totals, 5 scan_chunks, 6 fill_tri, 7 fill_big, 8 sort_rays,
+ * 9 bool_count, 10 bool_write, 11 volume_partial, 12 volume_final). */
+const char *ldni_kernel_name(int32_t id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDNI_H */

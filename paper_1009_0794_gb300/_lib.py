@@ -1,0 +1,103 @@
+"""ctypes view of libldni.so (the C ABI declared in include/ldni.h).
+
+Argument marshalling only: every step of sampling, Boolean and volume runs
+in the library's CUDA kernels.  There is no CPU fallback: if the library
+cannot be built or loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+LDNI_OK = 0
+AXIS_ALL = 3
+MODE_EXACT2 = 0
+MODE_LEARNED1 = 1
+OP_UNION, OP_INTER, OP_DIFF = 0, 1, 2
+
+ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX = 1, 2, 4, 8, 16, 32
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("width", ctypes.c_float), ("res", ctypes.c_int32)]
+
+
+class Layers(ctypes.Structure):
+    _fields_ = [("offsets", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("nx", ctypes.c_void_p),
+                ("ny", ctypes.c_void_p), ("nz", ctypes.c_void_p), ("tri_id", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64)]
+
+
+INFO_BYTES = 32  # ldni_info_t: int64 n[3]; uint32 status; uint32 odd_rays
+
+
+class LDNIError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_I32 = ctypes.c_int32
+_SZ = ctypes.c_size_t
+_PG = ctypes.POINTER(Grid)
+_PL = ctypes.POINTER(Layers)
+
+# name -> (restype, argtypes); every symbol include/ldni.h declares
+SIGNATURES = {
+    "ldni_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "ldni_version": (ctypes.c_int, []),
+    "ldni_grid_from_bbox": (ctypes.c_int, [_P, _I32, _PG]),
+    "ldni_sample_workspace_size": (ctypes.c_int, [_I64, _I64, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "ldni_sample": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _I32, _PL, _P, _P, _SZ, _P]),
+    "ldni_sample_count": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
+    "ldni_sample_fill": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
+    "ldni_boolean_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
+    "ldni_boolean": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P, _SZ, _P]),
+    "ldni_volume_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
+    "ldni_volume": (ctypes.c_int, [_PL, _PG, _P, _P, _P, _SZ, _P]),
+    "ldni_launch_count": (ctypes.c_uint64, []),
+    "ldni_profile_set": (ctypes.c_int, [_P, _P, _P, _I32, _I32]),
+    "ldni_profile_recorded": (ctypes.c_int64, []),
+    "ldni_kernel_name": (ctypes.c_char_p, [_I32]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load libldni.so (building it first if needed).  Raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libldni.so not found at {path}; run __graft_entry__.build()")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().ldni_strerror(int(code)).decode()
+    except Exception:  # library unavailable: still give the number
+        return f"ldni error {code}"
+
+
+def check(code: int, what: str) -> None:
+    if code != LDNI_OK:
+        raise LDNIError(code, what)

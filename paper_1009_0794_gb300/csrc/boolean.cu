@@ -1,0 +1,200 @@
+// Per-ray Boolean of two LDNIs on one grid (Section 4.1) with small-interval
+// removal (Section 4.1.1).
+//
+// The paper slices A's segments by B's samples and keeps, merges or removes
+// segments per operation.  Restated as a merge of two sorted sample lists
+// with inside-counters: walking the distinct depths in order, every sample
+// toggles its solid's state (odd-to-even ranges are inside, Section 2);
+// equal depths of A and B are one event; the output state op(inA, inB)
+// changes exactly at the result's boundary samples.  An emitted sample is
+// A's when A's state flipped at that depth, else B's (normal inverted for a
+// difference, Section 4.1).  Entering samples wait in registers until their
+// exit is known, so an interval thinner than eps is dropped without a second
+// pass over the output.
+//
+// Two passes: count (one output count per ray), scan to CSR offsets, write.
+#include <climits>
+
+#include "ldni_host.h"
+
+namespace ldni {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Side {
+    long long cap;  // samples beyond capacity are never read
+    const int *off;
+    const float *d;
+    const float *nx;
+    const float *ny;
+    const float *nz;
+    const int *tri;
+};
+
+struct Out {
+    const int *off;
+    float *d;
+    float *nx;
+    float *ny;
+    float *nz;
+    int *tri;
+    long long cap;
+};
+
+__device__ __forceinline__ bool op_apply(int op, bool a, bool b) {
+    return op == LDNI_OP_UNION ? (a || b) : (op == LDNI_OP_INTER ? (a && b) : (a && !b));
+}
+
+struct Pick {
+    bool from_b;
+    long long idx;
+    float d;
+};
+
+__device__ __forceinline__ void emit(const Pick &s, const Side &A, const Side &B, int op, const Out &o,
+                                     long long at, ldni_info_t *info) {
+    if (at >= o.cap) {
+        set_status(info, LDNI_ST_CAPACITY);
+        return;
+    }
+    o.d[at] = s.d;
+    if (!s.from_b) {
+        o.nx[at] = A.nx[s.idx];
+        o.ny[at] = A.ny[s.idx];
+        o.nz[at] = A.nz[s.idx];
+        o.tri[at] = A.tri[s.idx];
+    } else {
+        const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+        o.nx[at] = sg * B.nx[s.idx];
+        o.ny[at] = sg * B.ny[s.idx];
+        o.nz[at] = sg * B.nz[s.idx];
+        o.tri[at] = (int)((unsigned)B.tri[s.idx] | 0x80000000u);
+    }
+}
+
+template <bool kWrite>
+__global__ void __launch_bounds__(kThreads) bool_pass(long long nrays, Side A, Side B, int op, float eps,
+                                                      int *out_count, Out o, ldni_info_t *info) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
+         p += (long long)gridDim.x * blockDim.x) {
+        long long a = A.off[p];
+        long long ae = A.off[p + 1];
+        long long b = B.off[p];
+        long long be = B.off[p + 1];
+        if (!kWrite && (((ae - a) | (be - b)) & 1)) {
+            atomicAdd(&info->odd_rays, 1u);
+            set_status(info, LDNI_ST_ODD);
+        }
+        if (ae > A.cap || be > B.cap) {
+            // an operand whose samples were cut off by its own capacity
+            set_status(info, LDNI_ST_CAPACITY);
+            ae = min(ae, A.cap);
+            be = min(be, B.cap);
+            a = min(a, ae);
+            b = min(b, be);
+        }
+        bool inA = false, inB = false, out = false;
+        Pick pend{false, 0, 0.0f};
+        long long m = 0;
+        const long long base = kWrite ? (long long)o.off[p] : 0;
+        while (a < ae || b < be) {
+            float d;
+            if (a < ae && b < be) {
+                const float da = A.d[a], db = B.d[b];
+                d = da < db ? da : db;
+            } else {
+                d = a < ae ? A.d[a] : B.d[b];
+            }
+            const long long fa = a, fb = b;
+            while (a < ae && A.d[a] == d) ++a;
+            while (b < be && B.d[b] == d) ++b;
+            const bool flipA = ((a - fa) & 1) != 0;
+            const bool flipB = ((b - fb) & 1) != 0;
+            inA ^= flipA;
+            inB ^= flipB;
+            const bool now = op_apply(op, inA, inB);
+            if (now == out) continue;
+            out = now;
+            const Pick cur = flipA ? Pick{false, fa, d} : Pick{true, fb, d};
+            if (now) {
+                pend = cur;
+            } else if (!(__fsub_rn(d, pend.d) < eps)) {
+                if (kWrite) {
+                    emit(pend, A, B, op, o, base + m, info);
+                    emit(cur, A, B, op, o, base + m + 1, info);
+                }
+                m += 2;
+            }
+        }
+        if (!kWrite) out_count[p] = (int)m;
+    }
+}
+
+int grid_blocks(long long work) {
+    long long b = (work + kThreads - 1) / kThreads;
+    const long long lim = (long long)num_sms() * 16;
+    if (b > lim) b = lim;
+    return (int)(b > 0 ? b : 1);
+}
+
+struct BoolWs {
+    int *count;
+    long long *partials;
+};
+
+BoolWs carve_bool_ws(Carver &c, int res) {
+    BoolWs w;
+    const long long N = (long long)res * res;
+    w.count = c.take<int>((size_t)N);
+    w.partials = c.take<long long>(csr_scan_partials(N));
+    return w;
+}
+
+bool layers_ok(const ldni_layers_t *L, bool need) {
+    if (!L || !L->offsets || L->capacity < 0) return false;
+    if (need && L->capacity > 0 && (!L->depth || !L->nx || !L->ny || !L->nz || !L->tri_id)) return false;
+    return true;
+}
+
+}  // namespace
+}  // namespace ldni
+
+using namespace ldni;
+
+extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
+    if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
+    Carver c(nullptr, 0);
+    carve_bool_ws(c, res);
+    *bytes = align_up(c.off);
+    return LDNI_OK;
+}
+
+extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
+                            const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info,
+                            void *ws, size_t ws_bytes, void *stream) {
+    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !info || !ws ||
+        !grid_valid(grid_a) || !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
+        return LDNI_EINVAL;
+    if (grid_a->res != grid_b->res || grid_a->width != grid_b->width || grid_a->origin[0] != grid_b->origin[0] ||
+        grid_a->origin[1] != grid_b->origin[1] || grid_a->origin[2] != grid_b->origin[2])
+        return LDNI_EGRID_MISMATCH;
+    const int res = grid_a->res;
+    Carver c(ws, ws_bytes);
+    BoolWs w = carve_bool_ws(c, res);
+    if (!c.fits()) return LDNI_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long N = (long long)res * res;
+    Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
+    Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
+    Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
+    LDNI_LAUNCH(K_BOOL_COUNT, s, bool_pass<false><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
+    int rc = cuda_status();
+    if (rc != LDNI_OK) return rc;
+    const int *cnt[1] = {w.count};
+    int *off[1] = {out->offsets};
+    rc = csr_scan(cnt, off, 1, N, w.partials, info, 0, s);
+    if (rc != LDNI_OK) return rc;
+    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_pass<true><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
+    return cuda_status();
+}

@@ -1,0 +1,76 @@
+// Small C-ABI helpers: error strings, version, grid from a bounding box.
+#include <cmath>
+
+#include "ldni_host.h"
+
+extern "C" const char *ldni_strerror(int code) {
+    switch (code) {
+        case LDNI_OK: return "ok";
+        case LDNI_EINVAL: return "invalid argument";
+        case LDNI_EGRID_MISMATCH: return "Boolean operands are sampled on different grids";
+        case LDNI_EODD: return "an input ray has an odd number of samples";
+        case LDNI_ETOOLARGE: return "size beyond the int32 CSR range";
+        case LDNI_EWORKSPACE: return "workspace smaller than the size query";
+        case LDNI_ECUDA: return "CUDA runtime error";
+        case LDNI_ETIMEOUT: return "bounded device wait expired";
+        case LDNI_ERANGE: return "vertex outside the snappable range of the grid";
+        case LDNI_ECAPACITY: return "output capacity smaller than the sample count";
+        default: return "unknown ldni error";
+    }
+}
+
+extern "C" int ldni_version(void) { return 100; }
+
+extern "C" int ldni_grid_from_bbox(const float *bbox, int32_t res, ldni_grid_t *grid) {
+    if (!bbox || !grid || res < 1 || res > 8192) return LDNI_EINVAL;
+    float w = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+        if (!std::isfinite(bbox[k]) || !std::isfinite(bbox[k + 3]) || bbox[k + 3] < bbox[k]) return LDNI_EINVAL;
+        const float e = bbox[k + 3] - bbox[k];
+        if (e > w) w = e;
+    }
+    if (!(w > 0.0f)) return LDNI_EINVAL;
+    for (int k = 0; k < 3; ++k) grid->origin[k] = bbox[k];
+    grid->width = w;
+    grid->res = res;
+    return LDNI_OK;
+}
+
+// ---- launch accounting and optional per-kernel event timing -------------
+
+namespace ldni {
+ProfState &prof_state() {
+    static ProfState s;
+    return s;
+}
+std::atomic<uint64_t> &launch_counter() {
+    static std::atomic<uint64_t> c{0};
+    return c;
+}
+}  // namespace ldni
+
+extern "C" int ldni_profile_set(void **begin_events, void **end_events, int32_t *kernel_ids, int32_t capacity,
+                                int32_t filter) {
+    ldni::ProfState &P = ldni::prof_state();
+    if (capacity < 0 || filter < 0 || filter >= ldni::K_NUM) return LDNI_EINVAL;
+    if (capacity > 0 && (!begin_events || !end_events)) return LDNI_EINVAL;
+    P.begin = reinterpret_cast<cudaEvent_t *>(begin_events);
+    P.end = reinterpret_cast<cudaEvent_t *>(end_events);
+    P.ids = kernel_ids;
+    P.cap = capacity;
+    P.next = 0;
+    P.filter = filter;
+    return LDNI_OK;
+}
+
+extern "C" int64_t ldni_profile_recorded(void) { return ldni::prof_state().next; }
+
+extern "C" uint64_t ldni_launch_count(void) { return ldni::launch_counter().load(); }
+
+extern "C" const char *ldni_kernel_name(int32_t id) {
+    static const char *names[ldni::K_NUM] = {"none",        "count_tri",    "count_big",   "scan_chunk_totals",
+                                             "scan_totals", "scan_chunks",  "fill_tri",    "fill_big",
+                                             "sort_rays",   "bool_count",   "bool_write",  "volume_partial",
+                                             "volume_final"};
+    return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
+}

@@ -1,0 +1,73 @@
+// Host-side helpers shared by the C-ABI entry points: workspace carving,
+// grid validation and CUDA error mapping.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ldni.h"
+#include "ldni_device.cuh"
+#include "prof.h"
+
+namespace ldni {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Hands out aligned slices of one caller-provided workspace.  With base ==
+// nullptr it only measures.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    size_t cap;
+    Carver(void *b, size_t c) : base(static_cast<char *>(b)), cap(c) {}
+    template <class T>
+    T *take(size_t count) {
+        size_t at = align_up(off);
+        off = at + count * sizeof(T);
+        return base ? reinterpret_cast<T *>(base + at) : nullptr;
+    }
+    bool fits() const { return off <= cap; }
+};
+
+inline bool grid_valid(const ldni_grid_t *g) {
+    return g && g->res >= 1 && g->res <= 8192 && g->width > 0.0f && g->width < 3.0e38f;
+}
+
+inline GridDev make_grid(const ldni_grid_t *g) {
+    GridDev d;
+    d.o[0] = g->origin[0];
+    d.o[1] = g->origin[1];
+    d.o[2] = g->origin[2];
+    d.s = (float)((double)g->res * (double)kSubpix / (double)g->width);
+    d.res = g->res;
+    return d;
+}
+
+inline int cuda_status() {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? LDNI_OK : LDNI_ECUDA;
+}
+
+inline int num_sms() {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+            sms = 152;
+    }
+    return sms;
+}
+
+// ---- CSR scan (scan.cu) ------------------------------------------------
+// offsets[a][0..N] = exclusive prefix sum of counts[a][0..N-1], offsets[a][N]
+// = total; info->n[info_base + a] = total; totals above 2^31-1 set
+// LDNI_ST_TOOLARGE.  `partials` must hold csr_scan_partials(N) int64 per axis.
+size_t csr_scan_partials(long long N);
+int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long N, long long *partials,
+             ldni_info_t *info, int info_base, cudaStream_t s);
+
+}  // namespace ldni

@@ -1,0 +1,67 @@
+// Launch accounting and optional per-kernel CUDA-event timing.
+//
+// Every kernel launch of the library goes through LDNI_LAUNCH, which counts
+// it and, when a caller has installed event slots with ldni_profile_set and
+// the kernel id passes the filter, records a begin event before and an end
+// event after the launch on the same stream.
+#pragma once
+
+#include <atomic>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ldni {
+
+enum KernelId : int {
+    K_NONE = 0,
+    K_COUNT_TRI = 1,
+    K_COUNT_BIG = 2,
+    K_SCAN_CHUNK = 3,
+    K_SCAN_TOP = 4,
+    K_SCAN_DOWN = 5,
+    K_FILL_TRI = 6,
+    K_FILL_BIG = 7,
+    K_SORT = 8,
+    K_BOOL_COUNT = 9,
+    K_BOOL_WRITE = 10,
+    K_VOL_PARTIAL = 11,
+    K_VOL_FINAL = 12,
+    K_NUM = 13
+};
+
+struct ProfState {
+    cudaEvent_t *begin = nullptr;
+    cudaEvent_t *end = nullptr;
+    int32_t *ids = nullptr;
+    int32_t cap = 0;
+    int32_t next = 0;
+    int32_t filter = 0;  // 0 = every kernel, else one KernelId
+};
+
+ProfState &prof_state();
+std::atomic<uint64_t> &launch_counter();
+
+inline int prof_begin(int id, cudaStream_t s) {
+    launch_counter().fetch_add(1, std::memory_order_relaxed);
+    ProfState &P = prof_state();
+    if (P.cap <= 0 || (P.filter != 0 && P.filter != id)) return -1;
+    const int slot = P.next % P.cap;
+    P.next++;
+    if (P.ids) P.ids[slot] = id;
+    cudaEventRecord(P.begin[slot], s);
+    return slot;
+}
+
+inline void prof_end(int slot, cudaStream_t s) {
+    if (slot < 0) return;
+    cudaEventRecord(prof_state().end[slot], s);
+}
+
+}  // namespace ldni
+
+#define LDNI_LAUNCH(id, stream, ...)                  \
+    do {                                              \
+        const int ldni_slot_ = ::ldni::prof_begin((id), (stream)); \
+        __VA_ARGS__;                                  \
+        ::ldni::prof_end(ldni_slot_, (stream));       \
+    } while (0)

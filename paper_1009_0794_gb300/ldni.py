@@ -1,0 +1,277 @@
+"""Python face of the LDNI library: PyTorch supplies device memory and the
+stream, libldni.so does all the work.
+
+    import paper_1009_0794_gb300 as ldni
+    g = ldni.Grid.cube((-0.5, -0.5, -0.5), 1.0, 1024)
+    X, Y, Z = ldni.sample(verts, tris, g)          # Definition 3: three LDNIs
+    U = ldni.boolean(X, X2, "union")               # Section 4.1
+    v = ldni.volume(X)
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Union
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import Grid as _CGrid, Layers as _CLayers
+
+OPS = {"union": _lib.OP_UNION, "inter": _lib.OP_INTER, "intersection": _lib.OP_INTER,
+       "diff": _lib.OP_DIFF, "difference": _lib.OP_DIFF}
+
+
+@dataclass(frozen=True)
+class Grid:
+    """The cube shared by the three images (Definition 3)."""
+    origin: tuple
+    width: float
+    res: int
+
+    @staticmethod
+    def cube(origin, width, res) -> "Grid":
+        return Grid(tuple(float(np.float32(x)) for x in origin), float(np.float32(width)), int(res))
+
+    @staticmethod
+    def from_bbox(bbox, res) -> "Grid":
+        b = np.ascontiguousarray(bbox, dtype=np.float32).reshape(6)
+        g = _CGrid()
+        _lib.check(_lib.load().ldni_grid_from_bbox(b.ctypes.data_as(ctypes.c_void_p), int(res), ctypes.byref(g)),
+                   "ldni_grid_from_bbox")
+        return Grid(tuple(g.origin), float(g.width), int(g.res))
+
+    @property
+    def h(self) -> float:
+        return self.width / self.res
+
+    def c(self) -> _CGrid:
+        g = _CGrid()
+        for k in range(3):
+            g.origin[k] = self.origin[k]
+        g.width = self.width
+        g.res = self.res
+        return g
+
+
+class LDNI:
+    """One layered depth-normal image in CSR form on the device."""
+
+    def __init__(self, grid: Grid, axis: int, offsets, depth, nx, ny, nz, tri, n: int):
+        self.grid, self.axis = grid, axis
+        self.offsets, self.depth, self.nx, self.ny, self.nz, self.tri = offsets, depth, nx, ny, nz, tri
+        self.n = int(n)
+
+    @property
+    def capacity(self) -> int:
+        return int(self.depth.numel())
+
+    def c(self) -> _CLayers:
+        L = _CLayers()
+        L.offsets = self.offsets.data_ptr()
+        L.depth = self.depth.data_ptr() if self.depth.numel() else None
+        L.nx = self.nx.data_ptr() if self.nx.numel() else None
+        L.ny = self.ny.data_ptr() if self.ny.numel() else None
+        L.nz = self.nz.data_ptr() if self.nz.numel() else None
+        L.tri_id = self.tri.data_ptr() if self.tri.numel() else None
+        L.capacity = self.capacity
+        return L
+
+    def counts(self):
+        return self.offsets[1:] - self.offsets[:-1]
+
+    def numpy(self) -> dict:
+        n = self.n
+        return {"offsets": self.offsets.cpu().numpy().astype(np.int64),
+                "depth": self.depth[:n].cpu().numpy(),
+                "nrm": torch.stack([self.nx[:n], self.ny[:n], self.nz[:n]], 1).cpu().numpy(),
+                "tri": self.tri[:n].cpu().numpy()}
+
+
+def _stream_ptr(stream: Optional[torch.cuda.Stream]):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(x, dtype) -> torch.Tensor:
+    if isinstance(x, torch.Tensor):
+        t = x.to(device="cuda", dtype=dtype)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=dtype)
+    return t.contiguous()
+
+
+def _axes(axis) -> List[int]:
+    if axis in ("all", None, _lib.AXIS_ALL):
+        return [0, 1, 2]
+    return [int(axis)]
+
+
+def new_info() -> torch.Tensor:
+    return torch.zeros(_lib.INFO_BYTES // 8, dtype=torch.int64, device="cuda")
+
+
+def info_decode(info: torch.Tensor) -> dict:
+    h = info.cpu().numpy()
+    st = int(h[3]) & 0xFFFFFFFF
+    odd = (int(h[3]) >> 32) & 0xFFFFFFFF
+    return {"n": [int(x) for x in h[:3]], "status": st, "odd_rays": odd}
+
+
+def _raise_status(st: int, what: str):
+    if st & _lib.ST_INDEX:
+        raise _lib.LDNIError(-1, what + " (triangle vertex index out of range)")
+    if st & _lib.ST_RANGE:
+        raise _lib.LDNIError(-8, what)
+    if st & _lib.ST_TOOLARGE:
+        raise _lib.LDNIError(-4, what)
+    if st & _lib.ST_CAPACITY:
+        raise _lib.LDNIError(-9, what)
+    if st & _lib.ST_TIMEOUT:
+        raise _lib.LDNIError(-7, what)
+
+
+def sample_workspace_size(nv: int, nt: int, res: int, axis=_lib.AXIS_ALL) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_sample_workspace_size(int(nv), int(nt), int(res),
+                                                      _lib.AXIS_ALL if axis in ("all", None) else int(axis),
+                                                      ctypes.byref(sz)), "ldni_sample_workspace_size")
+    return int(sz.value)
+
+
+def empty_layers(grid: Grid, axis: int, capacity: int) -> LDNI:
+    N = grid.res * grid.res
+    f = lambda: torch.empty(capacity, dtype=torch.float32, device="cuda")
+    return LDNI(grid, axis, torch.empty(N + 1, dtype=torch.int32, device="cuda"), f(), f(), f(), f(),
+                torch.empty(capacity, dtype=torch.int32, device="cuda"), 0)
+
+
+def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=None,
+           check_odd: bool = False) -> Union[LDNI, List[LDNI]]:
+    """Sample a closed mesh into LDNIs (Section 3, Definitions 1-4).
+
+    Exact sizing: the count pass runs, the sample totals are read back (one
+    device->host read, the only synchronisation), the sample arrays are
+    allocated to size, then the fill pass and per-ray sort run."""
+    lib = _lib.load()
+    v = _dev(verts, torch.float32).reshape(-1, 3)
+    t = _dev(tris, torch.int32).reshape(-1, 3)
+    axes = _axes(axis)
+    cax = _lib.AXIS_ALL if len(axes) == 3 else axes[0]
+    ws = torch.empty(sample_workspace_size(v.shape[0], t.shape[0], grid.res, cax), dtype=torch.uint8, device="cuda")
+    info = new_info()
+    outs = [empty_layers(grid, a, 0) for a in axes]
+    arr = (_CLayers * len(axes))(*[o.c() for o in outs])
+    g = grid.c()
+    sp = _stream_ptr(stream)
+    _lib.check(lib.ldni_sample_count(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
+                                     info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_count")
+    meta = info_decode(info)
+    _raise_status(meta["status"], "ldni_sample_count")
+    res_list = []
+    for k, a in enumerate(axes):
+        n = meta["n"][a]
+        L = empty_layers(grid, a, n)
+        L.offsets = outs[k].offsets
+        L.n = n
+        res_list.append(L)
+    arr = (_CLayers * len(axes))(*[o.c() for o in res_list])
+    _lib.check(lib.ldni_sample_fill(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
+                                    info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_fill")
+    if check_odd:
+        meta = info_decode(info)
+        _raise_status(meta["status"], "ldni_sample_fill")
+        if meta["status"] & _lib.ST_ODD:
+            raise _lib.LDNIError(-3, f"ldni_sample: {meta['odd_rays']} odd rays")
+    return res_list if len(axes) > 1 else res_list[0]
+
+
+class SamplePlan:
+    """Pre-sized buffers for repeated sampling of one mesh size without any
+    host synchronisation (for benchmarks and pipelines).  Capacities come
+    from a first exact call; a later call that needs more sets
+    LDNI_ST_CAPACITY in ``info``."""
+
+    def __init__(self, nv: int, nt: int, grid: Grid, capacities: Sequence[int], axis="all", slack: float = 1.0):
+        self.grid = grid
+        self.axes = _axes(axis)
+        self.cax = _lib.AXIS_ALL if len(self.axes) == 3 else self.axes[0]
+        self.ws = torch.empty(sample_workspace_size(nv, nt, grid.res, self.cax), dtype=torch.uint8, device="cuda")
+        self.info = new_info()
+        self.outs = [empty_layers(grid, a, int(np.ceil(c * slack))) for a, c in zip(self.axes, capacities)]
+        self._arr = (_CLayers * len(self.axes))(*[o.c() for o in self.outs])
+        self._g = grid.c()
+
+    def run(self, verts: torch.Tensor, tris: torch.Tensor, stream=None, mode: int = _lib.MODE_EXACT2):
+        lib = _lib.load()
+        _lib.check(lib.ldni_sample(verts.data_ptr(), verts.shape[0], tris.data_ptr(), tris.shape[0],
+                                   ctypes.byref(self._g), self.cax, mode, self._arr, self.info.data_ptr(),
+                                   self.ws.data_ptr(), self.ws.numel(), _stream_ptr(stream)), "ldni_sample")
+
+    def finish(self) -> List[LDNI]:
+        """Synchronise, check status and set the sample counts."""
+        meta = info_decode(self.info)
+        _raise_status(meta["status"], "ldni_sample")
+        for o in self.outs:
+            o.n = meta["n"][o.axis]
+        return self.outs
+
+
+def boolean_workspace_size(res: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_boolean_workspace_size(int(res), ctypes.byref(sz)), "ldni_boolean_workspace_size")
+    return int(sz.value)
+
+
+def boolean(A: LDNI, B: LDNI, op, eps: float = 0.0, stream=None, out: Optional[LDNI] = None,
+            ws: Optional[torch.Tensor] = None, info: Optional[torch.Tensor] = None, sync: bool = True) -> LDNI:
+    """A op B per ray (Section 4.1) with small-interval removal (Section
+    4.1.1).  Output capacity A.capacity + B.capacity always suffices."""
+    lib = _lib.load()
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    if out is None:
+        out = empty_layers(A.grid, A.axis, A.capacity + B.capacity)
+    if ws is None:
+        ws = torch.empty(boolean_workspace_size(A.grid.res), dtype=torch.uint8, device="cuda")
+    if info is None:
+        info = new_info()
+    la, lb, lo = A.c(), B.c(), out.c()
+    ga, gb = A.grid.c(), B.grid.c()
+    _lib.check(lib.ldni_boolean(ctypes.byref(la), ctypes.byref(ga), ctypes.byref(lb), ctypes.byref(gb), opc,
+                                float(eps), ctypes.byref(lo), info.data_ptr(), ws.data_ptr(), ws.numel(),
+                                _stream_ptr(stream)), "ldni_boolean")
+    if sync:
+        meta = info_decode(info)
+        _raise_status(meta["status"], "ldni_boolean")
+        if meta["status"] & _lib.ST_ODD:
+            raise _lib.LDNIError(-3, "ldni_boolean")
+        out.n = meta["n"][0]
+    return out
+
+
+def volume_workspace_size(res: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_volume_workspace_size(int(res), ctypes.byref(sz)), "ldni_volume_workspace_size")
+    return int(sz.value)
+
+
+def volume(L: LDNI, stream=None, out: Optional[torch.Tensor] = None, ws: Optional[torch.Tensor] = None,
+           info: Optional[torch.Tensor] = None, sync: bool = True):
+    """Enclosed volume seen by one LDNI (odd-to-even ranges inside)."""
+    lib = _lib.load()
+    if out is None:
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = torch.empty(volume_workspace_size(L.grid.res), dtype=torch.uint8, device="cuda")
+    if info is None:
+        info = new_info()
+    lc, g = L.c(), L.grid.c()
+    _lib.check(lib.ldni_volume(ctypes.byref(lc), ctypes.byref(g), out.data_ptr(), info.data_ptr(), ws.data_ptr(),
+                               ws.numel(), _stream_ptr(stream)), "ldni_volume")
+    if not sync:
+        return out
+    meta = info_decode(info)
+    if meta["status"] & _lib.ST_ODD:
+        raise _lib.LDNIError(-3, "ldni_volume")
+    return float(out.item())

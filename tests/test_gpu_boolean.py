@@ -1,0 +1,118 @@
+"""CUDA Boolean and volume through the C ABI against the oracle
+(Section 4.1, 4.1.1; odd-to-even volume).  Both sides read the same FP32
+LDNIs, so the Boolean must match bit for bit: counts, depths, normals, ids."""
+import numpy as np
+import pytest
+
+import meshgen as M
+import oracle
+from ldni_compare import bit_equal
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+O3 = (-0.5, -0.5, -0.5)
+
+
+@pytest.fixture(scope="module")
+def ldni():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1009_0794_gb300 as pkg
+    pkg._lib.load()
+    return pkg
+
+
+def _pairs(ldni, meshA, meshB, res):
+    grid = ldni.Grid.cube(O3, 1.0, res)
+    return ldni.sample(*meshA, grid, "all"), ldni.sample(*meshB, grid, "all")
+
+
+@pytest.mark.parametrize("res", [128, 77])
+@pytest.mark.parametrize("op", ["union", "inter", "diff"])
+@pytest.mark.parametrize("eps", [0.0, 1e-5])
+def test_pr1_boolean_bit_exact(ldni, res, op, eps):
+    A, B = M.pr1_pair()
+    LA, LB = _pairs(ldni, A, B, res)
+    for a in range(3):
+        got = ldni.boolean(LA[a], LB[a], op, eps=eps).numpy()
+        ref = oracle.boolean(LA[a].numpy(), LB[a].numpy(), op, eps=eps)
+        assert bit_equal(got, ref)
+
+
+def test_flower_knot_boolean_bit_exact(ldni):
+    (fv, ft), (kv, kt) = M.flower(128, 128), M.torus_knot(n_ring=128, n_side=16)
+    LA, LB = _pairs(ldni, (fv, ft), (kv, kt), 192)
+    for a in range(3):
+        for op in ("union", "inter", "diff"):
+            got = ldni.boolean(LA[a], LB[a], op, eps=1e-5).numpy()
+            ref = oracle.boolean(LA[a].numpy(), LB[a].numpy(), op, eps=1e-5)
+            assert bit_equal(got, ref)
+
+
+def test_identities_on_gpu(ldni):
+    """A u A = A, A \\ A = empty, (A n B) \\ A = empty (Figure 6), and
+    (A \\ B) u (A n B) = A in depths, all on the device."""
+    A, B = M.pr1_pair()
+    LA, LB = _pairs(ldni, A, B, 128)
+    for a in range(3):
+        X = LA[a].numpy()
+        assert bit_equal(ldni.boolean(LA[a], LA[a], "union").numpy(), X)
+        assert ldni.boolean(LA[a], LA[a], "diff").n == 0
+        I = ldni.boolean(LA[a], LB[a], "inter")
+        assert ldni.boolean(I, LA[a], "diff").n == 0
+        D = ldni.boolean(LA[a], LB[a], "diff")
+        R = ldni.boolean(D, I, "union").numpy()
+        assert np.array_equal(R["offsets"], X["offsets"]) and np.array_equal(R["depth"], X["depth"])
+
+
+def test_empty_operands(ldni):
+    A, _ = M.pr1_pair()
+    grid = ldni.Grid.cube(O3, 1.0, 64)
+    LA = ldni.sample(*A, grid, 0)
+    E = ldni.sample(np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), grid, 0)
+    assert bit_equal(ldni.boolean(LA, E, "union").numpy(), LA.numpy())
+    assert ldni.boolean(LA, E, "inter").n == 0
+    assert bit_equal(ldni.boolean(LA, E, "diff").numpy(), LA.numpy())
+    assert ldni.boolean(E, E, "union").n == 0
+
+
+def test_grid_mismatch_rejected(ldni):
+    A, _ = M.pr1_pair()
+    L1 = ldni.sample(*A, ldni.Grid.cube(O3, 1.0, 64), 0)
+    L2 = ldni.sample(*A, ldni.Grid.cube((-0.5, -0.5, -0.25), 1.0, 64), 0)
+    with pytest.raises(ldni.LDNIError) as e:
+        ldni.boolean(L1, L2, "union")
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("res", [64, 128, 333])
+def test_volume_matches_oracle(ldni, res):
+    A, B = M.pr1_pair()
+    grid = ldni.Grid.cube(O3, 1.0, res)
+    for mesh in (A, B):
+        for L in ldni.sample(*mesh, grid, "all"):
+            v = ldni.volume(L)
+            ref = oracle.volume(L.numpy(), grid.h)
+            assert v == pytest.approx(ref, rel=1e-12)
+
+
+def test_volume_deterministic_and_inclusion_exclusion(ldni):
+    A, B = M.pr1_pair()
+    LA, LB = _pairs(ldni, A, B, 128)
+    for a in range(3):
+        vA, vB = ldni.volume(LA[a]), ldni.volume(LB[a])
+        assert ldni.volume(LA[a]) == vA
+        vU = ldni.volume(ldni.boolean(LA[a], LB[a], "union"))
+        vI = ldni.volume(ldni.boolean(LA[a], LB[a], "inter"))
+        assert vU + vI == pytest.approx(vA + vB, rel=1e-12)
+
+
+def test_odd_operand_rejected(ldni):
+    v, t = M.icosphere(4, r=0.35)
+    grid = ldni.Grid.cube(O3, 1.0, 64)
+    L = ldni.sample(v, t[1:], grid, 2)
+    with pytest.raises(ldni.LDNIError):
+        ldni.boolean(L, L, "union")
+    with pytest.raises(ldni.LDNIError):
+        ldni.volume(L)
