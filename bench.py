@@ -187,6 +187,64 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
     return 0.0
 
 
+def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
+    """The same step through the public API, inputs copied from pinned host
+    memory and the united LDNIs plus volumes copied back, every step."""
+    import torch
+    hv = torch.from_numpy(sv).pin_memory()
+    ht = torch.from_numpy(st).pin_memory()
+    host = None
+    vol_host = torch.empty(3, dtype=torch.float64, pin_memory=True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    d2h = 0
+    for rep in range(2 + e2e_steps):
+        if rep == 2:
+            torch.cuda.synchronize()
+            e0.record()
+            h0 = time.perf_counter()
+        dv = hv.to(dev, non_blocking=True)
+        dt_ = ht.to(dev, non_blocking=True)
+        A = ldni.sample(dv, dt_, grid, "all")
+        vol_dev = torch.zeros(3, dtype=torch.float64, device=dev)
+        res = []
+        for a in range(3):
+            Ua = ldni.boolean(A[a], K[a], "union", ws=bws)
+            ldni.volume(Ua, out=vol_dev[a:a + 1], ws=vws, sync=False)
+            res.append(Ua)
+        if host is None:
+            host = [[torch.empty(Ua.offsets.numel(), dtype=torch.int32, pin_memory=True)]
+                    + [torch.empty(max(Ua.n, 1) * 2, dtype=torch.float32, pin_memory=True) for _ in range(4)]
+                    + [torch.empty(max(Ua.n, 1) * 2, dtype=torch.int32, pin_memory=True)] for Ua in res]
+        d2h = 0
+        for Ua, hb in zip(res, host):
+            n = Ua.n
+            for s_, h_ in zip([Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]], hb):
+                h_[:s_.numel()].copy_(s_, non_blocking=True)
+                d2h += s_.numel() * s_.element_size()
+        vol_host.copy_(vol_dev, non_blocking=True)
+        d2h += vol_dev.numel() * 8
+    e1.record()
+    torch.cuda.synchronize()
+    wall = 1e3 * (time.perf_counter() - h0) / e2e_steps
+    ms = e0.elapsed_time(e1) / e2e_steps
+    return {"value": ws * rays_per_step / (ms * 1e-3), "unit": "rays/s",
+            "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(d2h),
+            "ms_per_step": ms, "wall_ms_per_step": wall, "steps": e2e_steps,
+            "api": "paper_1009_0794_gb300.sample / boolean / volume (exact sizing: one count readback per call)"}
+
+
+def _events(n):
+    """n timing events with their CUDA handles created (torch creates an
+    event lazily at its first record)."""
+    import torch
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+    for e in ev:
+        e.record()
+    torch.cuda.synchronize()
+    return ev
+
+
 def run_ours(args):
     import torch
     import paper_1009_0794_gb300 as ldni
@@ -225,8 +283,8 @@ def run_ours(args):
 
     # per-kernel profile during warm-up: find the dominant kernel
     cap = 64
-    ev_b = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(cap)]
+    ev_b = _events(cap)
+    ev_e = _events(cap)
     import ctypes
     arr_b = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_b])
     arr_e = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_e])
@@ -257,8 +315,8 @@ def run_ours(args):
     # timed region: K steps, per-step events, L2 flushed between steps,
     # dominant kernel timed by its own events
     steps = args.steps
-    dk_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps * launches_per_call[dominant])]
-    dk_e = [torch.cuda.Event(enable_timing=True) for _ in range(len(dk_b))]
+    dk_b = _events(steps * launches_per_call[dominant])
+    dk_e = _events(len(dk_b))
     dk_arr_b = (ctypes.c_void_p * len(dk_b))(*[e.cuda_event for e in dk_b])
     dk_arr_e = (ctypes.c_void_p * len(dk_e))(*[e.cuda_event for e in dk_e])
     st_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -267,7 +325,7 @@ def run_ours(args):
     clocks.start()
     # settle clocks under load before the measured steps
     t_settle = time.perf_counter()
-    while time.perf_counter() - t_settle < 1.0:
+    while time.perf_counter() - t_settle < args.settle:
         flush.zero_()
         step()
         torch.cuda.synchronize()
@@ -301,52 +359,8 @@ def run_ours(args):
     samples_per_s = ws * sum(n_sphere) * steps / (total_ms * 1e-3)
 
     # end to end through the public API from pinned host buffers
-    e2e = None
-    if rank == 0 or True:
-        hv = torch.from_numpy(sv).pin_memory()
-        ht = torch.from_numpy(st).pin_memory()
-        e2e_steps = max(3, min(steps, 20))
-        outs_host = None
-        for rep in range(2 + e2e_steps):
-            if rep == 2:
-                torch.cuda.synchronize()
-                e0 = torch.cuda.Event(enable_timing=True)
-                e0.record()
-                h0 = time.perf_counter()
-            dv = hv.to(dev, non_blocking=True)
-            dt_ = ht.to(dev, non_blocking=True)
-            A = ldni.sample(dv, dt_, grid, "all")
-            res_host = []
-            vol_dev = torch.zeros(3, dtype=torch.float64, device=dev)
-            for a in range(3):
-                Ua = ldni.boolean(A[a], K[a], "union", ws=bws)
-                ldni.volume(Ua, out=vol_dev[a:a + 1], ws=vws, sync=False)
-                res_host.append(Ua)
-            if outs_host is None:
-                outs_host = []
-                for Ua in res_host:
-                    outs_host.append([torch.empty(Ua.offsets.numel(), dtype=torch.int32, pin_memory=True)] +
-                                     [torch.empty(max(Ua.n, 1) * 2, dtype=torch.float32, pin_memory=True)
-                                      for _ in range(4)] +
-                                     [torch.empty(max(Ua.n, 1) * 2, dtype=torch.int32, pin_memory=True)])
-                vol_host = torch.empty(3, dtype=torch.float64, pin_memory=True)
-            d2h = 0
-            for Ua, hb in zip(res_host, outs_host):
-                n = Ua.n
-                srcs = [Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]]
-                for s_, h_ in zip(srcs, hb):
-                    h_[:s_.numel()].copy_(s_, non_blocking=True)
-                    d2h += s_.numel() * s_.element_size()
-            vol_host.copy_(vol_dev, non_blocking=True)
-            d2h += 24
-        e1 = torch.cuda.Event(enable_timing=True)
-        e1.record()
-        torch.cuda.synchronize()
-        e2e_ms = e0.elapsed_time(e1) / e2e_steps
-        e2e = {"value": ws * rays_per_step / (e2e_ms * 1e-3), "unit": "rays/s",
-               "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": e2e_ms, "wall_ms_per_step": 1e3 * (time.perf_counter() - h0) / e2e_steps,
-               "api": "paper_1009_0794_gb300.sample / boolean / volume (exact sizing, one count readback per call)"}
+    e2e = None if args.no_e2e else run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step,
+                                           max(3, min(steps, 20)))
 
     if rank != 0:
         if dist:
@@ -416,6 +430,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed load before the timed steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -46,6 +46,7 @@ inline int prof_begin(int id, cudaStream_t s) {
     ProfState &P = prof_state();
     if (P.cap <= 0 || (P.filter != 0 && P.filter != id)) return -1;
     const int slot = P.next % P.cap;
+    if (!P.begin[slot] || !P.end[slot]) return -1;
     P.next++;
     if (P.ids) P.ids[slot] = id;
     cudaEventRecord(P.begin[slot], s);
