@@ -186,6 +186,27 @@ int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_l
                  int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                  void *stream);
 
+/*
+ * ldni_boolean without a workspace argument, for callers that cannot
+ * allocate device memory where they need a Boolean (code that is handed only
+ * input and output buffers because another framework owns the device
+ * allocator, or a loop where an allocation would synchronise the device).
+ * The paper has no counterpart; this is a deployment variant.
+ * Scratch: one static device array of 4 MiB + 8.5 KiB in the library, held by
+ * every GPU that loads the library until the process exits.  Limit: res <=
+ * 1024, else LDNI_ETOOLARGE.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  No call allocates or frees memory.
+ * All calls share the array: calls whose work overlaps on the GPU (two
+ * streams, or two host threads) race and corrupt each other's results;
+ * serialise them.  Each call writes every scratch word it reads, so the
+ * previous call's leftovers do not matter.  Same arguments, semantics and
+ * results as ldni_boolean otherwise.
+ */
+int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
+                        const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info,
+                        void *stream);
+
 /* ---- volume ----------------------------------------------------------- */
 
 /* Workspace bytes for ldni_volume at resolution res. */

@@ -61,6 +61,7 @@ SIGNATURES = {
     "ldni_sample_fill": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
     "ldni_boolean_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_boolean": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P, _SZ, _P]),
+    "ldni_boolean_static": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P]),
     "ldni_volume_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_volume": (ctypes.c_int, [_PL, _PG, _P, _P, _P, _SZ, _P]),
     "ldni_launch_count": (ctypes.c_uint64, []),

@@ -14,6 +14,7 @@
 //
 // Two passes: count (one output count per ray), scan to CSR offsets, write.
 #include <climits>
+#include <mutex>
 
 #include "ldni_host.h"
 
@@ -190,6 +191,84 @@ extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, c
     Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
     LDNI_LAUNCH(K_BOOL_COUNT, s, bool_pass<false><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
     int rc = cuda_status();
+    if (rc != LDNI_OK) return rc;
+    const int *cnt[1] = {w.count};
+    int *off[1] = {out->offsets};
+    rc = csr_scan(cnt, off, 1, N, w.partials, info, 0, s);
+    if (rc != LDNI_OK) return rc;
+    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_pass<true><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
+    return cuda_status();
+}
+
+// ---- Boolean without a caller workspace -------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they need a
+// Boolean: code running while another framework owns the device allocator
+// (a plugin that is only handed input and output buffers), or a latency-
+// critical loop where an allocation would synchronise the device.  For them
+// ldni_boolean_static keeps its scratch (per-ray output counts and the scan's
+// chunk totals) in one static device array instead of a workspace argument.
+// Every GPU that loads the library holds this array until the process exits.
+namespace ldni {
+namespace {
+
+constexpr int kStaticMaxRes = 1024;  // scratch sized for res <= 1024
+constexpr size_t kStaticScratchBytes =
+    4u * (size_t)kStaticMaxRes * kStaticMaxRes + 8u * 1024u + 2u * kAlign;  // counts + scan chunk totals
+
+static __device__ __align__(256) unsigned char g_bool_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void *g_static_ptr[kMaxDevices] = {nullptr};
+
+// Device address of the static scratch on the current device.  The host-side
+// symbol is only a stand-in, so the address is looked up once per device.
+int static_scratch(void **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LDNI_ECUDA;
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_bool_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return LDNI_ECUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    *out = g_static_ptr[dev];
+    return LDNI_OK;
+}
+
+}  // namespace
+}  // namespace ldni
+
+extern "C" int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
+                                   const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out,
+                                   ldni_info_t *info, void *stream) {
+    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !info || !grid_valid(grid_a) ||
+        !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
+        return LDNI_EINVAL;
+    if (grid_a->res != grid_b->res || grid_a->width != grid_b->width || grid_a->origin[0] != grid_b->origin[0] ||
+        grid_a->origin[1] != grid_b->origin[1] || grid_a->origin[2] != grid_b->origin[2])
+        return LDNI_EGRID_MISMATCH;
+    const int res = grid_a->res;
+    if (res > kStaticMaxRes) return LDNI_ETOOLARGE;
+    void *scratch = nullptr;
+    int rc = static_scratch(&scratch);
+    if (rc != LDNI_OK) return rc;
+    // every scratch word is written before it is read (counts by the count
+    // pass, chunk totals by the scan), so nothing needs clearing
+    Carver c(scratch, kStaticScratchBytes);
+    BoolWs w = carve_bool_ws(c, res);
+    if (!c.fits()) return LDNI_ETOOLARGE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long N = (long long)res * res;
+    Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
+    Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
+    Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
+    LDNI_LAUNCH(K_BOOL_COUNT, s, bool_pass<false><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
+    rc = cuda_status();
     if (rc != LDNI_OK) return rc;
     const int *cnt[1] = {w.count};
     int *off[1] = {out->offsets};
