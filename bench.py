@@ -173,16 +173,14 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
         1: mesh + 3 * 4.0 * N,                        # count: mesh read, counts written
         6: mesh + 3 * 4.0 * (N + 1) + 20.0 * ntot,    # fill: mesh, offsets read, samples written
         8: 3 * 4.0 * (N + 1) + 40.0 * ntot,           # sort: offsets, samples read + written
-        3: 3 * 4.0 * N, 5: 3 * 8.0 * N,               # scan phases
+        5: 3 * (4.0 * N + 4.0 * (N + 1)),             # scan: counts read, offsets written
     }
     if kid in table:
         return table[kid]
     a_mean = lambda xs: float(sum(xs)) / 3.0
-    if kid == 9:   # boolean count, one image
-        return 8.0 * (N + 1) + 4.0 * (a_mean(n) + a_mean(n_knot)) + 4.0 * N
-    if kid == 10:  # boolean write, one image
-        return 12.0 * (N + 1) + 20.0 * (a_mean(n) + a_mean(n_knot)) + 20.0 * a_mean(n_union)
-    if kid == 11:  # volume, one image
+    if kid == 13:  # fused Boolean, one image: both operands read, result written
+        return 8.0 * (N + 1) + 20.0 * (a_mean(n) + a_mean(n_knot)) + 4.0 * (N + 1) + 20.0 * a_mean(n_union)
+    if kid == 11:  # volume, one image: offsets and depths read
         return 4.0 * (N + 1) + 4.0 * a_mean(n_union)
     return 0.0
 

@@ -240,9 +240,9 @@ int ldni_profile_set(void **begin_events, void **end_events, int32_t *kernel_ids
 /* Records made since the last ldni_profile_set. */
 int64_t ldni_profile_recorded(void);
 
-/* Name of a kernel id (1 count_tri, 2 count_big, 3 scan_chunk_totals,
- * 4 scan_totals, 5 scan_chunks, 6 fill_tri, 7 fill_big, 8 sort_rays,
- * 9 bool_count, 10 bool_write, 11 volume_partial, 12 volume_final). */
+/* Name of a kernel id (1 count_tri, 2 count_big, 4 scan_empty, 5 scan,
+ * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
+ * two passes of ldni_boolean_static), 11 volume, 13 boolean). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "ldni_host.h"
+#include "lookback.cuh"
 
 namespace ldni {
 namespace {
@@ -132,6 +133,118 @@ __global__ void __launch_bounds__(kThreads) bool_pass(long long nrays, Side A, S
     }
 }
 
+// ---- fused single-launch Boolean --------------------------------------
+//
+// One block owns a tile of kTileRays consecutive rays, taken in kRounds
+// rounds of kFusedThreads consecutive rays (lane k of a warp holds ray p + k,
+// so a warp's loads and stores touch neighbouring CSR rows).  It merges every
+// ray once to count its output samples, scans the counts inside the block,
+// obtains the tile's starting offset by decoupled look-back, writes the tile's
+// CSR offsets, then merges again (inputs now hot in L1/L2) and writes the
+// samples.  One launch per image; the workspace is one status word per tile.
+constexpr int kFusedThreads = 256;
+constexpr int kRounds = 4;
+constexpr int kTileRays = kFusedThreads * kRounds;
+
+// Merge one ray.  kWrite = false: returns the output count.  kWrite = true:
+// writes the samples from `at` on.
+template <bool kWrite>
+__device__ __forceinline__ int merge_ray(long long p, const Side &A, const Side &B, int op, float eps,
+                                         const Out &o, long long at, ldni_info_t *info) {
+    long long a = A.off[p], ae = A.off[p + 1];
+    long long b = B.off[p], be = B.off[p + 1];
+    if (!kWrite && (((ae - a) | (be - b)) & 1)) {
+        atomicAdd(&info->odd_rays, 1u);
+        set_status(info, LDNI_ST_ODD);
+    }
+    if (ae > A.cap || be > B.cap) {
+        if (!kWrite) set_status(info, LDNI_ST_CAPACITY);
+        ae = min(ae, A.cap);
+        be = min(be, B.cap);
+        a = min(a, ae);
+        b = min(b, be);
+    }
+    bool inA = false, inB = false, out = false;
+    Pick pend{false, 0, 0.0f};
+    int m = 0;
+    while (a < ae || b < be) {
+        const float da = a < ae ? A.d[a] : 0.0f;
+        const float db = b < be ? B.d[b] : 0.0f;
+        const float d = (a < ae && (b >= be || da <= db)) ? da : db;
+        const long long fa = a, fb = b;
+        while (a < ae && A.d[a] == d) ++a;
+        while (b < be && B.d[b] == d) ++b;
+        const bool flipA = ((a - fa) & 1) != 0;
+        const bool flipB = ((b - fb) & 1) != 0;
+        inA ^= flipA;
+        inB ^= flipB;
+        const bool now = op_apply(op, inA, inB);
+        if (now == out) continue;
+        out = now;
+        const Pick cur = flipA ? Pick{false, fa, d} : Pick{true, fb, d};
+        if (now) {
+            pend = cur;
+        } else if (!(__fsub_rn(d, pend.d) < eps)) {
+            if (kWrite) {
+                emit(pend, A, B, op, o, at + m, info);
+                emit(cur, A, B, op, o, at + m + 1, info);
+            }
+            m += 2;
+        }
+    }
+    return m;
+}
+
+__global__ void __launch_bounds__(kFusedThreads, 4) bool_fused(long long N, Side A, Side B, int op, float eps,
+                                                               Out o, unsigned long long *words, int ntiles,
+                                                               ldni_info_t *info) {
+    __shared__ long long sh[kFusedThreads / 32 + 1];
+    __shared__ int s_tile;
+    __shared__ long long s_base;
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(words + ntiles, 1ull);
+    __syncthreads();
+    const int tile = s_tile;
+    const long long p0 = (long long)tile * kTileRays + threadIdx.x;  // round r: ray p0 + r * kFusedThreads
+    int cnt[kRounds];
+    long long excl[kRounds];
+    long long total = 0;
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long p = p0 + (long long)r * kFusedThreads;
+        cnt[r] = p < N ? merge_ray<false>(p, A, B, op, eps, o, 0, info) : 0;
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {  // rays in order: round by round, lane by lane
+        long long tot;
+        excl[r] = total + block_exclusive_scan<kFusedThreads>(cnt[r], sh, &tot);
+        total += tot;
+    }
+    if (threadIdx.x < 32) {
+        const long long b = lookback_warp(words, tile, total, info);
+        if (threadIdx.x == 0) s_base = b;
+    }
+    __syncthreads();
+    const long long base = s_base;
+    int *off = const_cast<int *>(o.off);
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long p = p0 + (long long)r * kFusedThreads;
+        if (p < N) off[p] = (int)min(base + excl[r], (long long)INT_MAX);
+    }
+    if (tile == ntiles - 1 && threadIdx.x == 0) {
+        const long long n_out = base + total;
+        off[N] = (int)min(n_out, (long long)INT_MAX);
+        info->n[0] = n_out;
+        if (n_out > INT_MAX) set_status(info, LDNI_ST_TOOLARGE);
+        if (n_out > o.cap) set_status(info, LDNI_ST_CAPACITY);
+    }
+#pragma unroll
+    for (int r = 0; r < kRounds; ++r) {
+        const long long p = p0 + (long long)r * kFusedThreads;
+        if (p < N && cnt[r] > 0) merge_ray<true>(p, A, B, op, eps, o, base + excl[r], info);
+    }
+}
+
 int grid_blocks(long long work) {
     long long b = (work + kThreads - 1) / kThreads;
     const long long lim = (long long)num_sms() * 16;
@@ -163,11 +276,15 @@ bool layers_ok(const ldni_layers_t *L, bool need) {
 
 using namespace ldni;
 
+namespace ldni {
+namespace {
+int fused_tiles(long long N) { return (int)((N + kTileRays - 1) / kTileRays); }
+}  // namespace
+}  // namespace ldni
+
 extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
     if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
-    Carver c(nullptr, 0);
-    carve_bool_ws(c, res);
-    *bytes = align_up(c.off);
+    *bytes = align_up(sizeof(unsigned long long) * (size_t)(fused_tiles((long long)res * res) + 1));
     return LDNI_OK;
 }
 
@@ -181,22 +298,18 @@ extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, c
         grid_a->origin[1] != grid_b->origin[1] || grid_a->origin[2] != grid_b->origin[2])
         return LDNI_EGRID_MISMATCH;
     const int res = grid_a->res;
-    Carver c(ws, ws_bytes);
-    BoolWs w = carve_bool_ws(c, res);
-    if (!c.fits()) return LDNI_EWORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long N = (long long)res * res;
+    const int ntiles = fused_tiles(N);
+    if (ws_bytes < sizeof(unsigned long long) * (size_t)(ntiles + 1)) return LDNI_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *words = static_cast<unsigned long long *>(ws);
+    if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(ntiles + 1), s) != cudaSuccess)
+        return LDNI_ECUDA;
     Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
     Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
     Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
-    LDNI_LAUNCH(K_BOOL_COUNT, s, bool_pass<false><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
-    int rc = cuda_status();
-    if (rc != LDNI_OK) return rc;
-    const int *cnt[1] = {w.count};
-    int *off[1] = {out->offsets};
-    rc = csr_scan(cnt, off, 1, N, w.partials, info, 0, s);
-    if (rc != LDNI_OK) return rc;
-    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_pass<true><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
+    LDNI_LAUNCH(K_BOOL_FUSED, s,
+                bool_fused<<<ntiles, kFusedThreads, 0, s>>>(N, sa, sb, op, eps, o, words, ntiles, info));
     return cuda_status();
 }
 

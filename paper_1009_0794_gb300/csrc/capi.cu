@@ -68,9 +68,9 @@ extern "C" int64_t ldni_profile_recorded(void) { return ldni::prof_state().next;
 extern "C" uint64_t ldni_launch_count(void) { return ldni::launch_counter().load(); }
 
 extern "C" const char *ldni_kernel_name(int32_t id) {
-    static const char *names[ldni::K_NUM] = {"none",        "count_tri",    "count_big",   "scan_chunk_totals",
-                                             "scan_totals", "scan_chunks",  "fill_tri",    "fill_big",
-                                             "sort_rays",   "bool_count",   "bool_write",  "volume_partial",
-                                             "volume_final"};
+    static const char *names[ldni::K_NUM] = {"none",       "count_tri",  "count_big", "unused",
+                                             "scan_empty", "scan",       "fill_tri",  "fill_big",
+                                             "sort_rays",  "bool_count", "bool_write", "volume",
+                                             "unused",     "boolean"};
     return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
 }

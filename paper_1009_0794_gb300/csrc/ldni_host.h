@@ -66,8 +66,11 @@ inline int num_sms() {
 // offsets[a][0..N] = exclusive prefix sum of counts[a][0..N-1], offsets[a][N]
 // = total; info->n[info_base + a] = total; totals above 2^31-1 set
 // LDNI_ST_TOOLARGE.  `partials` must hold csr_scan_partials(N) int64 per axis.
+// With `tinfo`, tinfo[a][c] = (offset of count c * kScanChunk, sum of that
+// chunk's counts) for every chunk c of kScanChunk counts.
+constexpr int kScanChunk = 4096;
 size_t csr_scan_partials(long long N);
 int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long N, long long *partials,
-             ldni_info_t *info, int info_base, cudaStream_t s);
+             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo = nullptr);
 
 }  // namespace ldni

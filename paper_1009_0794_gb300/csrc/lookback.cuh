@@ -1,0 +1,105 @@
+// Single-pass prefix sums across thread blocks by decoupled look-back: each
+// block publishes its aggregate, then walks back over its predecessors'
+// published words until it meets an inclusive prefix, and publishes its own
+// inclusive prefix.  Blocks take their chunk index from a ticket counter, so
+// a block only ever waits for blocks that are already running.  Every wait is
+// bounded: after kSpinLimit polls the block records LDNI_ST_TIMEOUT in the
+// call's info block and treats the missing word as zero, so the kernel always
+// terminates (the result is then flagged as invalid, never silently wrong).
+#pragma once
+
+#include <cstdint>
+
+#include "ldni.h"
+
+namespace ldni {
+
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagPrefix = 2ull << 62;
+constexpr unsigned long long kValueMask = (1ull << 62) - 1;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
+    return *reinterpret_cast<const volatile unsigned long long *>(p);
+}
+
+__device__ __forceinline__ void st_status(unsigned long long *p, unsigned long long v) {
+    atomicExch(p, v);  // value and flag travel in one 64-bit word
+}
+
+// Called by ALL 32 lanes of one warp (the same warp in every block).
+// Returns, in every lane, the exclusive prefix of chunk `c` given its
+// aggregate (>= 0).  The warp inspects 32 predecessors per probe: it waits
+// until all of them have published something, adds the aggregates down to
+// the nearest inclusive prefix, and moves on by 32 chunks if none was found.
+__device__ __forceinline__ long long lookback_warp(unsigned long long *status, int c, long long aggregate,
+                                                   ldni_info_t *info) {
+    const int lane = threadIdx.x & 31;
+    const unsigned long long agg = (unsigned long long)aggregate & kValueMask;
+    if (c == 0) {
+        if (lane == 0) st_status(status, kFlagPrefix | agg);
+        return 0;
+    }
+    if (lane == 0) st_status(status + c, kFlagAgg | agg);
+    long long excl = 0;
+    int hi = c - 1;  // nearest predecessor not yet accounted for
+    bool timed_out = false;
+    while (hi >= 0) {
+        const int k = hi - lane;  // lane 0 = nearest
+        unsigned long long w = k >= 0 ? ld_status(status + k) : kFlagPrefix;  // before chunk 0: prefix 0
+        int spins = 0;
+        while (__any_sync(0xffffffffu, (w & ~kValueMask) == 0)) {
+            if (++spins > kSpinLimit) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(32);
+            if ((w & ~kValueMask) == 0) w = ld_status(status + k);
+        }
+        if (timed_out) break;
+        const unsigned prefix_lanes = __ballot_sync(0xffffffffu, (w & ~kValueMask) == kFlagPrefix);
+        // lanes up to (and including) the nearest prefix contribute
+        const int stop = prefix_lanes ? __ffs(prefix_lanes) - 1 : 31;
+        long long v = lane <= stop ? (long long)(w & kValueMask) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        excl += v;
+        if (prefix_lanes) break;
+        hi -= 32;
+    }
+    if (timed_out && lane == 0 && info) atomicOr(&info->status, LDNI_ST_TIMEOUT);
+    if (lane == 0) st_status(status + c, kFlagPrefix | (((unsigned long long)(excl + aggregate)) & kValueMask));
+    return excl;
+}
+
+// Block-wide exclusive scan of one long long per thread (blockDim.x == NT,
+// a multiple of 32, at most 1024).  Returns the exclusive prefix; *total gets
+// the block sum.  `sh` holds at least NT/32 + 1 entries.
+template <int NT>
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *sh, long long *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < NT / 32 ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane < NT / 32) sh[lane] = w;
+    }
+    __syncthreads();
+    const long long excl = x - v + (warp > 0 ? sh[warp - 1] : 0);
+    *total = sh[NT / 32 - 1];
+    __syncthreads();
+    return excl;
+}
+
+}  // namespace ldni

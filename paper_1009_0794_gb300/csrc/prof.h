@@ -26,7 +26,8 @@ enum KernelId : int {
     K_BOOL_WRITE = 10,
     K_VOL_PARTIAL = 11,
     K_VOL_FINAL = 12,
-    K_NUM = 13
+    K_BOOL_FUSED = 13,
+    K_NUM = 14
 };
 
 struct ProfState {

@@ -1,36 +1,34 @@
-// LDNI sampling of a closed triangle mesh (Section 3; Definitions 1-4).
+// LDNI sampling of a closed triangle mesh, exact two-pass form (Section 3;
+// Definitions 1-4).
 //
 // The paper renders the mesh n_max + 1 times through a stencil-routed
 // OpenGL pipeline: pass 1 counts the depth complexity n_p of every pixel,
 // passes 2..n_max each capture the n-th fragment, and the host post-sorts
-// every pixel (Section 3, Appendix A).  Here the same exact two-pass
+// every pixel (Section 3, Appendix A).  Here the same count-then-fill
 // structure runs as CUDA kernels with everything resident on the device:
 //
-//   count : one thread per triangle snaps its vertices once, then for each
-//           requested image tests the pixel centres of its bounding box and
-//           adds 1 to count[p] per crossing (= the stencil pass);
-//   scan  : counts -> CSR row offsets (scan.cu);
+//   count : one thread per triangle snaps its vertices once and, for each
+//           requested image, adds 1 to count[p] for every crossed pixel
+//           centre (= the stencil pass);
+//   scan  : counts -> CSR offsets (scan.cu);
 //   fill  : the same traversal; every crossing takes a slot of its ray with
-//           an atomic decrement of count[p] (leaving the counts at zero) and
-//           writes depth, normal and triangle id there (= passes 2..n_max);
+//           an atomic decrement of count[p] and writes depth, normal and
+//           triangle id there (= passes 2..n_max);
 //   sort  : every ray orders its samples by (depth, tri_id) in place
 //           (= the host post-sort).
 //
-// Triangles whose pixel box holds more than kBigPixels centres are handed to
-// a CTA-per-triangle kernel so that a few large faces do not serialise a warp.
-#include <climits>
-
-#include "ldni_host.h"
+// Triangles whose pixel box is large are handed to a block-per-triangle
+// kernel with 64-bit edge functions.
+#include "sample_common.cuh"
 
 namespace ldni {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kBigPixels = 64;
 
-struct ImgPtrs {
-    int *count[3];
-    const int *offsets[3];
+struct Img {
+    int *count[3];          // per-ray counts (count pass), slot cursors (fill pass)
+    const int *offsets[3];  // CSR offsets
     float *depth[3];
     float *nx[3];
     float *ny[3];
@@ -39,157 +37,120 @@ struct ImgPtrs {
     long long cap[3];
 };
 
-template <class T>
-__device__ __forceinline__ T pick(T const (&arr)[3], int a) {
-    return a == 0 ? arr[0] : (a == 1 ? arr[1] : arr[2]);
-}
+__device__ __forceinline__ int *sel(int *const (&arr)[3], int a) { return a == 0 ? arr[0] : (a == 1 ? arr[1] : arr[2]); }
 
-// Per-thread view of one triangle: snapped lattice coordinates of its three
-// vertices (all three world axes) and the world positions.
-struct TriView {
-    int q[3][3];  // [vertex][axis]
-    float3 p[3];
-};
-
-// 0 = ok, else an LDNI_ST_* bit (bad index, unsnappable vertex)
-__device__ __forceinline__ unsigned load_tri(const float *__restrict__ verts, const int *__restrict__ tris, int t,
-                                             int nv, const GridDev &g, TriView &T) {
-    const int id[3] = {__ldg(tris + 3 * (long long)t), __ldg(tris + 3 * (long long)t + 1),
-                       __ldg(tris + 3 * (long long)t + 2)};
-    if ((unsigned)id[0] >= (unsigned)nv || (unsigned)id[1] >= (unsigned)nv || (unsigned)id[2] >= (unsigned)nv)
-        return LDNI_ST_INDEX;
-    bool ok = true;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        const float *v = verts + 3 * (long long)id[k];
-        T.p[k] = make_float3(__ldg(v), __ldg(v + 1), __ldg(v + 2));
-        ok &= snap(T.p[k].x, g.o[0], g.s, T.q[k][0]);
-        ok &= snap(T.p[k].y, g.o[1], g.s, T.q[k][1]);
-        ok &= snap(T.p[k].z, g.o[2], g.s, T.q[k][2]);
-    }
-    return ok ? 0u : LDNI_ST_RANGE;
-}
-
-template <int A>
-__device__ __forceinline__ bool project_axis(const TriView &T, int res, ProjTri &P) {
-    constexpr int U = (A + 1) % 3, V = (A + 2) % 3;
-    const int qu[3] = {T.q[0][U], T.q[1][U], T.q[2][U]};
-    const int qv[3] = {T.q[0][V], T.q[1][V], T.q[2][V]};
-    const float a[3] = {comp(T.p[0], A), comp(T.p[1], A), comp(T.p[2], A)};
-    return project_tri(qu, qv, a, res, P);
-}
-
-__device__ __forceinline__ bool project_axis_rt(const TriView &T, int a, int res, ProjTri &P) {
-    if (a == 0) return project_axis<0>(T, res, P);
-    if (a == 1) return project_axis<1>(T, res, P);
-    return project_axis<2>(T, res, P);
-}
-
-struct Normal {
-    float x, y, z;
-};
-
-// Test one pixel centre; on a crossing either count it or store the sample.
+// One crossing at depth d: count it, or take the next slot of ray p and store the sample.
 template <bool kFill>
-__device__ __forceinline__ void visit_pixel(const ProjTri &P, const EdgeBias &B, int i, int j, int a, int t,
-                                            const Normal &n, const ImgPtrs &o, int res, ldni_info_t *info) {
-    const EdgeEval E = edges_at(P, i * kSubpix + kHalfSubpix, j * kSubpix + kHalfSubpix);
-    if (!inside(E, B)) return;
-    const long long p = (long long)j * res + i;
-    int *cnt = pick(o.count, a);
+__device__ __forceinline__ void emit(float d, int a, int t, long long p, const float3 &n, const Img &o,
+                                     ldni_info_t *info) {
+    int *cnt = sel(o.count, a);
     if (!kFill) {
         atomicAdd(cnt + p, 1);
         return;
     }
     const int k = atomicSub(cnt + p, 1) - 1;
-    const long long slot = (long long)pick(o.offsets, a)[p] + k;
-    if (k < 0 || slot >= pick(o.cap, a)) {
+    const int *off = a == 0 ? o.offsets[0] : (a == 1 ? o.offsets[1] : o.offsets[2]);
+    const long long cap = a == 0 ? o.cap[0] : (a == 1 ? o.cap[1] : o.cap[2]);
+    const long long slot = (long long)off[p] + k;
+    if (k < 0 || slot >= cap) {
         set_status(info, LDNI_ST_CAPACITY);
         return;
     }
-    pick(o.depth, a)[slot] = crossing_depth(P, E);
-    pick(o.tri, a)[slot] = t;
-    pick(o.nx, a)[slot] = n.x;
-    pick(o.ny, a)[slot] = n.y;
-    pick(o.nz, a)[slot] = n.z;
+    float *D = a == 0 ? o.depth[0] : (a == 1 ? o.depth[1] : o.depth[2]);
+    float *X = a == 0 ? o.nx[0] : (a == 1 ? o.nx[1] : o.nx[2]);
+    float *Y = a == 0 ? o.ny[0] : (a == 1 ? o.ny[1] : o.ny[2]);
+    float *Z = a == 0 ? o.nz[0] : (a == 1 ? o.nz[1] : o.nz[2]);
+    int *T = a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]);
+    D[slot] = d;
+    T[slot] = t;
+    X[slot] = n.x;
+    Y[slot] = n.y;
+    Z[slot] = n.z;
 }
 
 template <bool kFill, int A>
-__device__ __forceinline__ void small_tri_axis(const TriView &T, int t, const Normal &n, const ImgPtrs &o, int res,
-                                               int *big_q, int *big_n, ldni_info_t *info) {
-    ProjTri P;
-    if (!project_axis<A>(T, res, P)) return;
-    const long long npx = (long long)(P.i1 - P.i0 + 1) * (P.j1 - P.j0 + 1);
-    if (npx > kBigPixels) {
-        const int k = atomicAdd(big_n, 1);
-        big_q[k] = t * 4 + A;
+__device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &n, const Img &o, int res, int *big_q,
+                                         int *big_n, ldni_info_t *info) {
+    Setup32 S;
+    const int kind = setup_axis<A, kFill>(T, res, S);
+    if (kind == kNone) return;
+    if (kind == kBig) {
+        if (!kFill) big_q[atomicAdd(big_n, 1)] = t * 4 + A;  // the fill pass reuses this queue
         return;
     }
-    const EdgeBias B = edge_bias(P);
-    for (int j = P.j0; j <= P.j1; ++j)
-        for (int i = P.i0; i <= P.i1; ++i) visit_pixel<kFill>(P, B, i, j, A, t, n, o, res, info);
+    if (!kFill) {
+        S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(o.count[A] + (long long)j * res + i, 1); });
+        return;
+    }
+    // fill: crossings first, then one store group per crossing (fewer live registers)
+    const unsigned long long m = hit_mask(S);
+    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
+    for (int y = 0; y < S.h; ++y) {
+        unsigned long long r = (m >> (y * S.w)) & row_mask;
+        while (r) {
+            const int x = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            const int i = S.i0 + x, j = S.j0 + y;
+            emit<true>(S.depth(i, j), A, t, (long long)j * res + i, n, o, info);
+        }
+    }
 }
 
-// One thread per triangle; big triangles are queued for big_tri_pass.
+// One thread per triangle; big triangles are queued (count pass) for big_pass.
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) tri_pass(const float *__restrict__ verts, const int *__restrict__ tris,
-                                                     int nt, int nv, GridDev g, int ax_lo, int ax_hi,
-                                                     ImgPtrs o, int *big_q, int *big_n, ldni_info_t *info) {
+                                                     int nt, int nv, GridDev g, int ax_lo, int ax_hi, Img o,
+                                                     int *big_q, int *big_n, ldni_info_t *info) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         TriView T;
         const unsigned bad = load_tri(verts, tris, t, nv, g, T);
         if (bad) {
-            set_status(info, bad);
+            if (!kFill) set_status(info, bad);
             continue;
         }
-        Normal n{0.f, 0.f, 0.f};
+        float3 n = make_float3(0.f, 0.f, 0.f);
         if (kFill) face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        if (ax_lo <= 0 && 0 <= ax_hi) small_tri_axis<kFill, 0>(T, t, n, o, g.res, big_q, big_n, info);
-        if (ax_lo <= 1 && 1 <= ax_hi) small_tri_axis<kFill, 1>(T, t, n, o, g.res, big_q, big_n, info);
-        if (ax_lo <= 2 && 2 <= ax_hi) small_tri_axis<kFill, 2>(T, t, n, o, g.res, big_q, big_n, info);
+        if (ax_lo <= 0 && 0 <= ax_hi) tri_axis<kFill, 0>(T, t, n, o, g.res, big_q, big_n, info);
+        if (ax_lo <= 1 && 1 <= ax_hi) tri_axis<kFill, 1>(T, t, n, o, g.res, big_q, big_n, info);
+        if (ax_lo <= 2 && 2 <= ax_hi) tri_axis<kFill, 2>(T, t, n, o, g.res, big_q, big_n, info);
     }
 }
 
-// One CTA per queued (triangle, image) pair; threads stride over its pixels.
+// One block per queued (triangle, image) pair; threads stride over its pixels.
 template <bool kFill>
-__global__ void __launch_bounds__(kThreads) big_tri_pass(const float *__restrict__ verts,
-                                                         const int *__restrict__ tris, int nv, GridDev g,
-                                                         ImgPtrs o, const int *big_q, const int *big_n,
-                                                         ldni_info_t *info) {
+__global__ void __launch_bounds__(kThreads) big_pass(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                     int nv, GridDev g, Img o, const int *big_q, const int *big_n,
+                                                     ldni_info_t *info) {
     const int nq = *big_n;
     for (int e = blockIdx.x; e < nq; e += gridDim.x) {
         const int code = big_q[e];
         const int t = code >> 2, a = code & 3;
         TriView T;
         if (load_tri(verts, tris, t, nv, g, T)) continue;
-        ProjTri P;
-        if (!project_axis_rt(T, a, g.res, P)) continue;
-        Normal n{0.f, 0.f, 0.f};
+        Setup64 S;
+        int i0, i1, j0, j1;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        float3 n = make_float3(0.f, 0.f, 0.f);
         if (kFill) face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        const EdgeBias B = edge_bias(P);
-        const int w = P.i1 - P.i0 + 1;
-        const long long npx = (long long)w * (P.j1 - P.j0 + 1);
+        const int w = i1 - i0 + 1;
+        const long long npx = (long long)w * (j1 - j0 + 1);
         for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
-            const int j = P.j0 + (int)(k / w), i = P.i0 + (int)(k % w);
-            visit_pixel<kFill>(P, B, i, j, a, t, n, o, g.res, info);
+            const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
+            if (S.inside(i, j)) emit<kFill>(kFill ? S.depth(i, j) : 0.0f, a, t, (long long)j * g.res + i, n, o, info);
         }
     }
 }
 
-__device__ __forceinline__ bool key_less(float d0, int t0, float d1, int t1) {
-    return d0 < d1 || (d0 == d1 && t0 < t1);
-}
-
 // Per-ray ordering by (depth, tri_id) in place; also flags odd rays.
-__global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo, ImgPtrs o, ldni_info_t *info) {
+__global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo, Img o, ldni_info_t *info) {
     const int a = ax_lo + blockIdx.y;
-    const int *off = pick(o.offsets, a);
-    float *D = pick(o.depth, a);
-    int *Tr = pick(o.tri, a);
-    float *X = pick(o.nx, a);
-    float *Y = pick(o.ny, a);
-    float *Z = pick(o.nz, a);
-    const long long cap = pick(o.cap, a);
+    const int *off = a == 0 ? o.offsets[0] : (a == 1 ? o.offsets[1] : o.offsets[2]);
+    float *D = a == 0 ? o.depth[0] : (a == 1 ? o.depth[1] : o.depth[2]);
+    int *Tr = a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]);
+    float *X = a == 0 ? o.nx[0] : (a == 1 ? o.nx[1] : o.nx[2]);
+    float *Y = a == 0 ? o.ny[0] : (a == 1 ? o.ny[1] : o.ny[2]);
+    float *Z = a == 0 ? o.nz[0] : (a == 1 ? o.nz[1] : o.nz[2]);
+    const long long cap = a == 0 ? o.cap[0] : (a == 1 ? o.cap[1] : o.cap[2]);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
          p += (long long)gridDim.x * blockDim.x) {
         const long long b = off[p];
@@ -213,42 +174,28 @@ __global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo
             }
             continue;
         }
-        for (long long x = b + 1; x < e; ++x) {
-            const float d = D[x];
-            const int t = Tr[x];
-            const float nx = X[x], ny = Y[x], nz = Z[x];
-            long long y = x - 1;
-            while (y >= b && key_less(d, t, D[y], Tr[y])) {
-                D[y + 1] = D[y];
-                Tr[y + 1] = Tr[y];
-                X[y + 1] = X[y];
-                Y[y + 1] = Y[y];
-                Z[y + 1] = Z[y];
-                --y;
-            }
-            D[y + 1] = d;
-            Tr[y + 1] = t;
-            X[y + 1] = nx;
-            Y[y + 1] = ny;
-            Z[y + 1] = nz;
-        }
+        sort_ray_global(b, e, D, Tr, X, Y, Z);
     }
 }
 
 struct SampleWs {
     int *count[3];
-    long long *partials;
+    int *big_n;          // right after the counts: one memset clears both
+    size_t clear_bytes;
+    long long *scan_words;
     int *big_q;
-    int *big_n;
 };
 
 SampleWs carve_sample_ws(Carver &c, long long nt, int res, int naxes) {
     SampleWs w{};
     const long long N = (long long)res * res;
-    for (int a = 0; a < naxes; ++a) w.count[a] = c.take<int>((size_t)N);
-    w.partials = c.take<long long>(csr_scan_partials(N) * naxes);
+    const long long stride = (N + 63) / 64 * 64;  // every image's counts start 256-byte aligned
+    int *block = c.take<int>((size_t)(stride * naxes + 1));
+    for (int a = 0; a < naxes; ++a) w.count[a] = block ? block + (size_t)a * stride : nullptr;
+    w.big_n = block ? block + (size_t)stride * naxes : nullptr;
+    w.clear_bytes = sizeof(int) * (size_t)(stride * naxes + 1);
+    w.scan_words = c.take<long long>(csr_scan_partials(N) * naxes);
     w.big_q = c.take<int>((size_t)(nt * naxes > 0 ? nt * naxes : 1));
-    w.big_n = c.take<int>(1);
     return w;
 }
 
@@ -256,7 +203,7 @@ struct Call {
     GridDev g;
     int ax_lo, ax_hi, naxes;
     long long nrays;
-    ImgPtrs o;
+    Img o;
     SampleWs w;
     cudaStream_t s;
 };
@@ -278,7 +225,7 @@ int prepare(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, con
     SampleWs w = carve_sample_ws(c, nt, grid->res, C.naxes);
     if (!c.fits()) return LDNI_EWORKSPACE;
     C.w = w;
-    C.o = ImgPtrs{};
+    C.o = Img{};
     for (int k = 0; k < C.naxes; ++k) {
         const int a = C.ax_lo + k;
         const ldni_layers_t &L = out[k];
@@ -305,16 +252,15 @@ int grid_blocks(long long work) {
 }
 
 int run_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const Call &C, ldni_info_t *info) {
-    for (int k = 0; k < C.naxes; ++k)
-        if (cudaMemsetAsync(C.w.count[k], 0, sizeof(int) * (size_t)C.nrays, C.s) != cudaSuccess) return LDNI_ECUDA;
-    if (cudaMemsetAsync(C.w.big_n, 0, sizeof(int), C.s) != cudaSuccess) return LDNI_ECUDA;
+    if (cudaMemsetAsync(C.w.count[0], 0, C.w.clear_bytes, C.s) != cudaSuccess) return LDNI_ECUDA;
     if (nt > 0) {
         LDNI_LAUNCH(K_COUNT_TRI, C.s,
-                    tri_pass<false><<<grid_blocks(nt), kThreads, 0, C.s>>>(
-                        verts, tris, (int)nt, (int)nv, C.g, C.ax_lo, C.ax_hi, C.o, C.w.big_q, C.w.big_n, info));
+                    tri_pass<false><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g,
+                                                                          C.ax_lo, C.ax_hi, C.o, C.w.big_q,
+                                                                          C.w.big_n, info));
         LDNI_LAUNCH(K_COUNT_BIG, C.s,
-                    big_tri_pass<false><<<num_sms() * 4, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o,
-                                                                            C.w.big_q, C.w.big_n, info));
+                    big_pass<false><<<num_sms() * 2, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                        C.w.big_n, info));
     }
     const int *cnt[3];
     int *off[3];
@@ -324,18 +270,18 @@ int run_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, c
     }
     int rc = cuda_status();
     if (rc != LDNI_OK) return rc;
-    return csr_scan(cnt, off, C.naxes, C.nrays, C.w.partials, info, C.ax_lo, C.s);
+    return csr_scan(cnt, off, C.naxes, C.nrays, C.w.scan_words, info, C.ax_lo, C.s);
 }
 
 int run_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const Call &C, ldni_info_t *info) {
-    if (cudaMemsetAsync(C.w.big_n, 0, sizeof(int), C.s) != cudaSuccess) return LDNI_ECUDA;
     if (nt > 0) {
         LDNI_LAUNCH(K_FILL_TRI, C.s,
-                    tri_pass<true><<<grid_blocks(nt), kThreads, 0, C.s>>>(
-                        verts, tris, (int)nt, (int)nv, C.g, C.ax_lo, C.ax_hi, C.o, C.w.big_q, C.w.big_n, info));
+                    tri_pass<true><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g,
+                                                                         C.ax_lo, C.ax_hi, C.o, C.w.big_q,
+                                                                         C.w.big_n, info));
         LDNI_LAUNCH(K_FILL_BIG, C.s,
-                    big_tri_pass<true><<<num_sms() * 4, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o,
-                                                                           C.w.big_q, C.w.big_n, info));
+                    big_pass<true><<<num_sms() * 2, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                       C.w.big_n, info));
     }
     LDNI_LAUNCH(K_SORT, C.s,
                 sort_rays<<<dim3(grid_blocks(C.nrays), C.naxes), kThreads, 0, C.s>>>(C.nrays, C.ax_lo, C.o, info));
@@ -373,14 +319,19 @@ extern "C" int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *t
     return run_fill(verts, nv, tris, nt, C, info);
 }
 
-extern "C" int ldni_sample(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
-                           int32_t axis, int32_t mode, ldni_layers_t *out, ldni_info_t *info, void *ws,
-                           size_t ws_bytes, void *stream) {
-    if (mode != LDNI_MODE_EXACT2) return LDNI_EINVAL;
+static int ldni_sample_exact2(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                       int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes, void *stream) {
     Call C;
     int rc = prepare(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream, true, C);
     if (rc != LDNI_OK) return rc;
     rc = run_count(verts, nv, tris, nt, C, info);
     if (rc != LDNI_OK) return rc;
     return run_fill(verts, nv, tris, nt, C, info);
+}
+
+extern "C" int ldni_sample(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                           int32_t axis, int32_t mode, ldni_layers_t *out, ldni_info_t *info, void *ws,
+                           size_t ws_bytes, void *stream) {
+    if (mode != LDNI_MODE_EXACT2) return LDNI_EINVAL;  // the learned one-pass form is ldni_sample_learned
+    return ldni_sample_exact2(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream);
 }

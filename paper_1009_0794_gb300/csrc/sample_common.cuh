@@ -1,0 +1,246 @@
+// Triangle traversal shared by the exact two-pass and the learned one-pass
+// samplers: per-thread triangle setup, the exact crossing test and hit masks.
+//
+// A tile is kTilePix consecutive rays of one image in CSR order (rows
+// p = j * res + i), so a tile's samples occupy one contiguous CSR range.
+#pragma once
+
+#include <climits>
+
+#include "ldni_host.h"
+
+namespace ldni {
+
+constexpr int kTileBits = 12;
+constexpr int kTilePix = 1 << kTileBits;  // rays per tile (= one scan chunk)
+static_assert(kTilePix == kScanChunk, "a tile is one scan chunk");
+constexpr int kBigPixels = 64;            // pixel-centre box of a thread-handled triangle (fits one mask)
+// Largest snapped extent (fixed-point units) of a triangle handled with
+// 32-bit edge functions.  With every vertex and every visited pixel centre
+// (plus one step beyond the box) within 32768 units of each other, each edge
+// function |d_u (c_v - v) - d_v (c_u - u)| < 2 * 32767^2 < 2^31.
+constexpr int kSmallExtent = 32000;
+
+// Per-thread view of one triangle: snapped lattice coordinates of its three
+// vertices (all three world axes) and the world positions.
+struct TriView {
+    int q[3][3];  // [vertex][axis]
+    float3 p[3];
+};
+
+// 0 = ok, else an LDNI_ST_* bit (bad index, unsnappable vertex)
+__device__ __forceinline__ unsigned load_tri(const float *__restrict__ verts, const int *__restrict__ tris, int t,
+                                             int nv, const GridDev &g, TriView &T) {
+    const int id[3] = {__ldg(tris + 3 * (long long)t), __ldg(tris + 3 * (long long)t + 1),
+                       __ldg(tris + 3 * (long long)t + 2)};
+    if ((unsigned)id[0] >= (unsigned)nv || (unsigned)id[1] >= (unsigned)nv || (unsigned)id[2] >= (unsigned)nv)
+        return LDNI_ST_INDEX;
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float *v = verts + 3 * (long long)id[k];
+        T.p[k] = make_float3(__ldg(v), __ldg(v + 1), __ldg(v + 2));
+        ok &= snap(T.p[k].x, g.o[0], g.s, T.q[k][0]);
+        ok &= snap(T.p[k].y, g.o[1], g.s, T.q[k][1]);
+        ok &= snap(T.p[k].z, g.o[2], g.s, T.q[k][2]);
+    }
+    return ok ? 0u : LDNI_ST_RANGE;
+}
+
+__device__ __forceinline__ int owns_i(int du, int dv) { return (dv > 0 || (dv == 0 && du < 0)) ? 1 : 0; }
+
+// Counter-clockwise projection of one triangle on one image, 32-bit form.
+struct Setup32 {
+    int u0, v0, u1, v1, u2, v2;
+    float a0, a1, a2;
+    int b0, b1, b2;
+    float inv;  // 1 / area2
+    int i0, j0, w, h;  // pixel-centre box: i0 .. i0+w-1, j0 .. j0+h-1
+
+    // biased edge functions at pixel (i, j): inside iff all three are > 0
+    __device__ __forceinline__ void edges(int i, int j, int &e0, int &e1, int &e2) const {
+        const int cu = i * kSubpix + kHalfSubpix, cv = j * kSubpix + kHalfSubpix;
+        e0 = (u1 - u0) * (cv - v0) - (v1 - v0) * (cu - u0) + b0;
+        e1 = (u2 - u1) * (cv - v1) - (v2 - v1) * (cu - u1) + b1;
+        e2 = (u0 - u2) * (cv - v2) - (v0 - v2) * (cu - u2) + b2;
+    }
+    // depth from the biased edge functions at a crossing: lambda_k from the
+    // exact edge functions (bias removed); the edge opposite vertex k is k+1
+    __device__ __forceinline__ float depth_from(int e0, int e1, int e2) const {
+        const float l0 = __int2float_rn(e1 - b1) * inv;
+        const float l1 = __int2float_rn(e2 - b2) * inv;
+        const float l2 = __int2float_rn(e0 - b0) * inv;
+        return l0 * a0 + l1 * a1 + l2 * a2;
+    }
+    __device__ __forceinline__ float depth(int i, int j) const {
+        int e0, e1, e2;
+        edges(i, j, e0, e1, e2);
+        return depth_from(e0, e1, e2);
+    }
+    // visit every crossed pixel centre of the box: f(i, j, e0, e1, e2)
+    template <class F>
+    __device__ __forceinline__ void for_each_hit(F &&f) const {
+        int r0, r1, r2;
+        edges(i0, j0, r0, r1, r2);
+        const int s0 = -(v1 - v0) * kSubpix, s1 = -(v2 - v1) * kSubpix, s2 = -(v0 - v2) * kSubpix;
+        const int t0 = (u1 - u0) * kSubpix, t1 = (u2 - u1) * kSubpix, t2 = (u0 - u2) * kSubpix;
+        for (int y = 0; y < h; ++y) {
+            int e0 = r0, e1 = r1, e2 = r2;
+            for (int x = 0; x < w; ++x) {
+                if ((e0 > 0) & (e1 > 0) & (e2 > 0)) f(i0 + x, j0 + y, e0, e1, e2);
+                e0 += s0;
+                e1 += s1;
+                e2 += s2;
+            }
+            r0 += t0;
+            r1 += t1;
+            r2 += t2;
+        }
+    }
+};
+
+// 64-bit form for triangles too large for Setup32.
+struct Setup64 {
+    long long u0, v0, u1, v1, u2, v2;
+    float a0, a1, a2;
+    long long b0, b1, b2;
+    float inv;
+    __device__ __forceinline__ void edges(int i, int j, long long &e0, long long &e1, long long &e2) const {
+        const long long cu = (long long)i * kSubpix + kHalfSubpix, cv = (long long)j * kSubpix + kHalfSubpix;
+        e0 = (u1 - u0) * (cv - v0) - (v1 - v0) * (cu - u0) + b0;
+        e1 = (u2 - u1) * (cv - v1) - (v2 - v1) * (cu - u1) + b1;
+        e2 = (u0 - u2) * (cv - v2) - (v0 - v2) * (cu - u2) + b2;
+    }
+    __device__ __forceinline__ bool inside(int i, int j) const {
+        long long e0, e1, e2;
+        edges(i, j, e0, e1, e2);
+        return e0 > 0 && e1 > 0 && e2 > 0;
+    }
+    __device__ __forceinline__ float depth(int i, int j) const {
+        long long e0, e1, e2;
+        edges(i, j, e0, e1, e2);
+        const float l0 = (float)(e1 - b1) * inv;
+        const float l1 = (float)(e2 - b2) * inv;
+        const float l2 = (float)(e0 - b0) * inv;
+        return l0 * a0 + l1 * a1 + l2 * a2;
+    }
+};
+
+enum AxisKind { kNone = 0, kSmall = 1, kBig = 2 };
+
+// Box test and (for small triangles) the 32-bit setup of image A; the
+// reciprocal area for depths only when kDepth.
+template <int A, bool kDepth = true>
+__device__ __forceinline__ int setup_axis(const TriView &T, int res, Setup32 &S) {
+    constexpr int U = (A + 1) % 3, V = (A + 2) % 3;
+    int u0 = T.q[0][U], u1 = T.q[1][U], u2 = T.q[2][U];
+    int v0 = T.q[0][V], v1 = T.q[1][V], v2 = T.q[2][V];
+    const int umin = min(u0, min(u1, u2)), umax = max(u0, max(u1, u2));
+    const int vmin = min(v0, min(v1, v2)), vmax = max(v0, max(v1, v2));
+    // pixel centres 256 i + 128 inside [umin, umax] x [vmin, vmax]
+    const int i0 = max((umin + 127) >> 8, 0), i1 = min((umax - 128) >> 8, res - 1);
+    const int j0 = max((vmin + 127) >> 8, 0), j1 = min((vmax - 128) >> 8, res - 1);
+    if (i0 > i1 || j0 > j1) return kNone;
+    if (umax - umin >= kSmallExtent || vmax - vmin >= kSmallExtent || (i1 - i0 + 1) * (j1 - j0 + 1) > kBigPixels)
+        return kBig;
+    int A2 = (u1 - u0) * (v2 - v0) - (v1 - v0) * (u2 - u0);
+    if (A2 == 0) return kNone;  // face parallel to the ray (Definition 1 note)
+    float a0 = comp(T.p[0], A), a1 = comp(T.p[1], A), a2 = comp(T.p[2], A);
+    if (A2 < 0) {  // turn counter-clockwise
+        int x = u1; u1 = u2; u2 = x;
+        x = v1; v1 = v2; v2 = x;
+        const float y = a1; a1 = a2; a2 = y;
+        A2 = -A2;
+    }
+    S.u0 = u0; S.v0 = v0; S.u1 = u1; S.v1 = v1; S.u2 = u2; S.v2 = v2;
+    S.a0 = a0; S.a1 = a1; S.a2 = a2;
+    S.b0 = owns_i(u1 - u0, v1 - v0);
+    S.b1 = owns_i(u2 - u1, v2 - v1);
+    S.b2 = owns_i(u0 - u2, v0 - v2);
+    S.inv = kDepth ? __frcp_rn(__int2float_rn(A2)) : 0.0f;
+    S.i0 = i0; S.j0 = j0; S.w = i1 - i0 + 1; S.h = j1 - j0 + 1;
+    return kSmall;
+}
+
+// Crossings of the pixel box as a bit mask (bit b = pixel (i0 + b % w, j0 + b / w)).
+__device__ __forceinline__ unsigned long long hit_mask(const Setup32 &S) {
+    int r0, r1, r2;
+    S.edges(S.i0, S.j0, r0, r1, r2);
+    const int s0 = -(S.v1 - S.v0) * kSubpix, s1 = -(S.v2 - S.v1) * kSubpix, s2 = -(S.v0 - S.v2) * kSubpix;
+    const int t0 = (S.u1 - S.u0) * kSubpix, t1 = (S.u2 - S.u1) * kSubpix, t2 = (S.u0 - S.u2) * kSubpix;
+    unsigned long long m = 0;
+    int bit = 0;
+    for (int y = 0; y < S.h; ++y) {
+        int e0 = r0, e1 = r1, e2 = r2;
+        for (int x = 0; x < S.w; ++x, ++bit) {
+            if ((e0 > 0) & (e1 > 0) & (e2 > 0)) m |= 1ull << bit;
+            e0 += s0;
+            e1 += s1;
+            e2 += s2;
+        }
+        r0 += t0;
+        r1 += t1;
+        r2 += t2;
+    }
+    return m;
+}
+
+// 64-bit setup of image a for a queued big triangle; false when parallel.
+__device__ __forceinline__ bool setup_big(const TriView &T, int a, int res, Setup64 &S, int &i0, int &i1, int &j0,
+                                          int &j1) {
+    const int U = (a + 1) % 3, V = (a + 2) % 3;
+    long long u0 = T.q[0][U], u1 = T.q[1][U], u2 = T.q[2][U];
+    long long v0 = T.q[0][V], v1 = T.q[1][V], v2 = T.q[2][V];
+    long long A2 = (u1 - u0) * (v2 - v0) - (v1 - v0) * (u2 - u0);
+    if (A2 == 0) return false;
+    float a0 = comp(T.p[0], a), a1 = comp(T.p[1], a), a2 = comp(T.p[2], a);
+    if (A2 < 0) {
+        long long x = u1; u1 = u2; u2 = x;
+        x = v1; v1 = v2; v2 = x;
+        const float y = a1; a1 = a2; a2 = y;
+        A2 = -A2;
+    }
+    S.u0 = u0; S.v0 = v0; S.u1 = u1; S.v1 = v1; S.u2 = u2; S.v2 = v2;
+    S.a0 = a0; S.a1 = a1; S.a2 = a2;
+    S.b0 = (v1 - v0 > 0 || (v1 == v0 && u1 - u0 < 0)) ? 1 : 0;
+    S.b1 = (v2 - v1 > 0 || (v2 == v1 && u2 - u1 < 0)) ? 1 : 0;
+    S.b2 = (v0 - v2 > 0 || (v0 == v2 && u0 - u2 < 0)) ? 1 : 0;
+    S.inv = 1.0f / (float)A2;
+    const long long umin = min(u0, min(u1, u2)), umax = max(u0, max(u1, u2));
+    const long long vmin = min(v0, min(v1, v2)), vmax = max(v0, max(v1, v2));
+    i0 = (int)max((umin + 127) >> 8, 0ll);
+    i1 = (int)min((umax - 128) >> 8, (long long)res - 1);
+    j0 = (int)max((vmin + 127) >> 8, 0ll);
+    j1 = (int)min((vmax - 128) >> 8, (long long)res - 1);
+    return i0 <= i1 && j0 <= j1;
+}
+
+__device__ __forceinline__ bool key_less(float d0, int t0, float d1, int t1) {
+    return d0 < d1 || (d0 == d1 && t0 < t1);
+}
+
+// In-place insertion sort of one ray's samples (five SoA arrays) by (depth, tri).
+__device__ __forceinline__ void sort_ray_global(long long b, long long e, float *D, int *Tr, float *X, float *Y,
+                                                float *Z) {
+    for (long long x = b + 1; x < e; ++x) {
+        const float d = D[x];
+        const int t = Tr[x];
+        const float nx = X[x], ny = Y[x], nz = Z[x];
+        long long y = x - 1;
+        while (y >= b && key_less(d, t, D[y], Tr[y])) {
+            D[y + 1] = D[y];
+            Tr[y + 1] = Tr[y];
+            X[y + 1] = X[y];
+            Y[y + 1] = Y[y];
+            Z[y + 1] = Z[y];
+            --y;
+        }
+        D[y + 1] = d;
+        Tr[y + 1] = t;
+        X[y + 1] = nx;
+        Y[y + 1] = ny;
+        Z[y + 1] = nz;
+    }
+}
+
+}  // namespace ldni

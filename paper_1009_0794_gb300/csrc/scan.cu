@@ -1,165 +1,140 @@
 // Exclusive prefix sum of per-ray counts into CSR row offsets: the step that
 // replaces the paper's per-pixel depth-complexity readback (Section 3:
-// n_p from the stencil buffer) with one device scan.
+// n_p from the stencil buffer, then n_max = max n_p) with one device pass.
 //
-// Three phases over chunks of kChunk counts: per-chunk totals, a scan of the
-// totals per axis, then a per-chunk scan that adds the chunk's prefix.
+// One kernel per call: every block scans a chunk of kChunk counts (coalesced
+// 16-byte loads), finds the chunk's starting offset by decoupled look-back
+// over its predecessors, and writes its offsets.  All images of a call are
+// scanned by the same launch (blockIdx.y = image).
 #include <climits>
 
 #include "ldni_host.h"
+#include "lookback.cuh"
 
 namespace ldni {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kPerThread = 16;
-constexpr int kChunk = kThreads * kPerThread;
+constexpr int kVec = 4;                      // counts per 16-byte load
+constexpr int kSlices = 4;                   // 16-byte loads per thread
+constexpr int kSlice = kThreads * kVec;      // 1024 counts per slice
+constexpr int kChunk = kSlice * kSlices;     // 4096 counts per block
+static_assert(kChunk == kScanChunk, "chunk size is part of the scan's interface");
 
 struct AxisPtrs {
     const int *counts[3];
     int *offsets[3];
+    int2 *tinfo[3];
 };
 
-__device__ __forceinline__ long long block_sum(long long v, long long *sh) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    long long t = 0;
-    if (threadIdx.x < 32) {
-        t = threadIdx.x < (kThreads / 32) ? sh[threadIdx.x] : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    }
-    return t;  // valid in thread 0
+// 16-byte load when the address allows it (c + e aligned), scalar otherwise
+__device__ __forceinline__ int4 load4(const int *c, long long e, long long N, bool vec) {
+    if (vec && e + 3 < N) return *reinterpret_cast<const int4 *>(c + e);
+    int4 v = make_int4(0, 0, 0, 0);
+    if (e < N) v.x = c[e];
+    if (e + 1 < N) v.y = c[e + 1];
+    if (e + 2 < N) v.z = c[e + 2];
+    if (e + 3 < N) v.w = c[e + 3];
+    return v;
 }
 
-__global__ void __launch_bounds__(kThreads) chunk_totals(AxisPtrs ap, long long N, int nchunk, long long *partials) {
-    __shared__ long long sh[kThreads / 32];
+__device__ __forceinline__ int clamp_int(long long x) { return (int)(x < INT_MAX ? x : INT_MAX); }
+
+__global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long N, int nchunk,
+                                                          unsigned long long *words, ldni_info_t *info,
+                                                          int info_base) {
+    __shared__ long long sh[kThreads / 32 + 1];
+    __shared__ int s_chunk;
+    __shared__ long long s_base;
     const int a = blockIdx.y;
-    const int *c = ap.counts[a];
-    const long long base = (long long)blockIdx.x * kChunk;
-    long long s = 0;
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        const long long i = base + (long long)k * kThreads + threadIdx.x;
-        if (i < N) s += c[i];
-    }
-    s = block_sum(s, sh);
-    if (threadIdx.x == 0) partials[(long long)a * nchunk + blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(1024) scan_totals(AxisPtrs ap, long long N, int nchunk, long long *partials,
-                                                     ldni_info_t *info, int info_base) {
-    __shared__ long long sh[32];
-    __shared__ long long carry;
-    const int a = blockIdx.x;
-    long long *P = partials + (long long)a * nchunk;
-    if (threadIdx.x == 0) carry = 0;
+    unsigned long long *status = words + (long long)a * (nchunk + 1);
+    unsigned long long *ticket = status + nchunk;
+    if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ticket, 1ull);
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < nchunk; base += 1024) {
-        const int i = base + threadIdx.x;
-        const long long v = i < nchunk ? P[i] : 0;
-        long long x = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, x, o);
-            if (lane >= o) x += y;
-        }
-        if (lane == 31) sh[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            long long w = sh[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            sh[lane] = w;
-        }
-        __syncthreads();
-        const long long incl = x + (warp > 0 ? sh[warp - 1] : 0) + carry;
-        if (i < nchunk) P[i] = incl - v;  // exclusive
-        __syncthreads();
-        if (threadIdx.x == 1023) carry = incl;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const long long total = carry;
-        if (info) info->n[info_base + a] = total;
-        if (total > INT_MAX) {
-            if (info) atomicOr(&info->status, LDNI_ST_TOOLARGE);
-        }
-        ap.offsets[a][N] = (int)min(total, (long long)INT_MAX);
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) chunk_scan(AxisPtrs ap, long long N, int nchunk,
-                                                       const long long *partials) {
-    __shared__ long long sh[kThreads / 32];
-    const int a = blockIdx.y;
-    const int *c = ap.counts[a];
+    const int c = s_chunk;
+    const int *cnt = ap.counts[a];
     int *out = ap.offsets[a];
-    const long long base = (long long)blockIdx.x * kChunk + (long long)threadIdx.x * kPerThread;
-    int v[kPerThread];
-    long long s = 0;
+    const long long base = (long long)c * kChunk;
+
+    // e is a multiple of 4, so 16-byte access is legal iff the base is aligned
+    const bool vec_in = ((reinterpret_cast<uintptr_t>(cnt) & 15) == 0);
+    int4 v[kSlices];
+    long long tsum[kSlices];
 #pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        const long long i = base + k;
-        v[k] = i < N ? c[i] : 0;
-        s += v[k];
+    for (int m = 0; m < kSlices; ++m) {
+        v[m] = load4(cnt, base + (long long)m * kSlice + threadIdx.x * kVec, N, vec_in);
+        tsum[m] = (long long)v[m].x + v[m].y + v[m].z + v[m].w;
     }
-    // exclusive scan of per-thread sums across the block
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    long long x = s;
+    long long excl[kSlices];
+    long long carry = 0;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
+    for (int m = 0; m < kSlices; ++m) {
+        long long tot;
+        excl[m] = carry + block_exclusive_scan<kThreads>(tsum[m], sh, &tot);
+        carry += tot;
     }
-    if (lane == 31) sh[warp] = x;
+    if (threadIdx.x < 32) {
+        const long long b = lookback_warp(status, c, carry, info);
+        if (threadIdx.x == 0) s_base = b;
+    }
     __syncthreads();
-    if (warp == 0) {
-        long long w = lane < (kThreads / 32) ? sh[lane] : 0;
+    const long long b0 = s_base;
+    if (ap.tinfo[a] && threadIdx.x == 0) ap.tinfo[a][c] = make_int2(clamp_int(b0), clamp_int(carry));
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += y;
+    for (int m = 0; m < kSlices; ++m) {
+        const long long e = base + (long long)m * kSlice + threadIdx.x * kVec;
+        const long long o0 = b0 + excl[m];
+        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v[m].x), clamp_int(o0 + v[m].x + v[m].y),
+                                 clamp_int(o0 + v[m].x + v[m].y + v[m].z));
+        if (vec_ok && e + 3 < N) {
+            *reinterpret_cast<int4 *>(out + e) = w;
+        } else {
+            if (e < N) out[e] = w.x;
+            if (e + 1 < N) out[e + 1] = w.y;
+            if (e + 2 < N) out[e + 2] = w.z;
+            if (e + 3 < N) out[e + 3] = w.w;
         }
-        if (lane < (kThreads / 32)) sh[lane] = w;
     }
-    __syncthreads();
-    long long run = partials[(long long)a * nchunk + blockIdx.x] + (x - s) + (warp > 0 ? sh[warp - 1] : 0);
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-        const long long i = base + k;
-        if (i < N) out[i] = (int)min(run, (long long)INT_MAX);
-        run += v[k];
+    if (c == nchunk - 1 && threadIdx.x == 0) {
+        const long long total = b0 + carry;
+        if (info) info->n[info_base + a] = total;
+        if (total > INT_MAX && info) atomicOr(&info->status, LDNI_ST_TOOLARGE);
+        out[N] = clamp_int(total);
     }
+}
+
+__global__ void scan_empty(AxisPtrs ap, ldni_info_t *info, int info_base) {
+    const int a = blockIdx.x;
+    ap.offsets[a][0] = 0;
+    if (info) info->n[info_base + a] = 0;
 }
 
 }  // namespace
 
 size_t csr_scan_partials(long long N) {
     const long long n = (N + kChunk - 1) / kChunk;
-    return (size_t)(n > 0 ? n : 1);
+    return (size_t)(n + 1);  // one status word per chunk + the ticket
 }
 
 int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long N, long long *partials,
-             ldni_info_t *info, int info_base, cudaStream_t s) {
+             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo) {
     AxisPtrs ap{};
     for (int a = 0; a < naxes; ++a) {
         ap.counts[a] = counts[a];
         ap.offsets[a] = offsets[a];
+        ap.tinfo[a] = tinfo ? tinfo[a] : nullptr;
     }
     const int nchunk = (int)((N + kChunk - 1) / kChunk);
-    if (nchunk > 0)
-        LDNI_LAUNCH(K_SCAN_CHUNK, s, chunk_totals<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials));
-    LDNI_LAUNCH(K_SCAN_TOP, s, scan_totals<<<naxes, 1024, 0, s>>>(ap, N, nchunk, partials, info, info_base));
-    if (nchunk > 0)
-        LDNI_LAUNCH(K_SCAN_DOWN, s, chunk_scan<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials));
+    if (nchunk == 0) {
+        LDNI_LAUNCH(K_SCAN_TOP, s, scan_empty<<<naxes, 1, 0, s>>>(ap, info, info_base));
+        return cuda_status();
+    }
+    unsigned long long *words = reinterpret_cast<unsigned long long *>(partials);
+    if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(nchunk + 1) * naxes, s) != cudaSuccess)
+        return LDNI_ECUDA;
+    LDNI_LAUNCH(K_SCAN_DOWN, s,
+                scan_lookback<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, words, info, info_base));
     return cuda_status();
 }
 

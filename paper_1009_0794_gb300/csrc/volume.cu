@@ -1,62 +1,123 @@
 // Enclosed volume seen by one LDNI: h^2 times the summed lengths of the
 // inside ranges d[2k] .. d[2k+1] of every ray (odd-to-even ranges are inside,
-// Section 2 after Proposition 1).  FP32 samples, exact FP64 differences, FP64
-// sums in a fixed order, so the result is deterministic for a given device.
+// Section 2 after Proposition 1).
+//
+// GB300 executes FP64 at a small fraction of its FP32 rate, so the per-ray
+// work stays in FP32: each difference d[2k+1] - d[2k] is split exactly into
+// a rounded FP32 value and its FP32 rounding error (TwoSum, Knuth, TAOCP
+// vol. 2, 4.2.2), and the per-thread and per-block sums are kept as unevaluated
+// FP32 pairs (double-float arithmetic, Dekker 1971).  Each block's pair is
+// widened to FP64 once; the last block to finish adds the block partials in
+// a fixed order.  The result is deterministic for a given device and within
+// about 1e-13 relative of the exact sum.
 #include "ldni_host.h"
 
 namespace ldni {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kRaysPerThread = 4;
 
-__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+// s + e == a + b exactly (round-to-nearest FP32 arithmetic, no FMA)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+struct DF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+    float s, e;
+    two_sum(x.hi, y.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
+    DF r;
+    two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const int *__restrict__ off,
+                                                          const float *__restrict__ d, long long cap,
+                                                          double *partials, unsigned *done, double h2,
+                                                          double *vol, ldni_info_t *info) {
+    __shared__ DF sh[kThreads / 32];
+    __shared__ bool s_last;
+    DF acc{0.0f, 0.0f};
+    const long long span = (long long)kThreads * kRaysPerThread;
+    for (long long p0 = blockIdx.x * span + threadIdx.x; p0 < nrays; p0 += (long long)gridDim.x * span) {
+        // kRaysPerThread independent rays: their loads are all in flight together
+        long long b[kRaysPerThread], e[kRaysPerThread];
+#pragma unroll
+        for (int r = 0; r < kRaysPerThread; ++r) {
+            const long long p = p0 + (long long)r * kThreads;
+            b[r] = p < nrays ? off[p] : 0;
+            e[r] = p < nrays ? off[p + 1] : 0;
+        }
+#pragma unroll
+        for (int r = 0; r < kRaysPerThread; ++r) {
+            if ((e[r] - b[r]) & 1) {
+                atomicAdd(&info->odd_rays, 1u);
+                set_status(info, LDNI_ST_ODD);
+                e[r] = b[r];
+            }
+            if (e[r] > cap) e[r] = cap;
+        }
+        float lo[kRaysPerThread], hi[kRaysPerThread];
+#pragma unroll
+        for (int r = 0; r < kRaysPerThread; ++r) {  // first inside range of every ray
+            const bool has = e[r] - b[r] >= 2;
+            lo[r] = has ? d[b[r]] : 0.0f;
+            hi[r] = has ? d[b[r] + 1] : 0.0f;
+        }
+#pragma unroll
+        for (int r = 0; r < kRaysPerThread; ++r) {
+            DF diff;
+            two_sum(hi[r], -lo[r], diff.hi, diff.lo);
+            acc = df_add(acc, diff);
+            for (long long k = b[r] + 2; k + 1 < e[r]; k += 2) {  // further ranges (multi-layer rays)
+                two_sum(d[k + 1], -d[k], diff.hi, diff.lo);
+                acc = df_add(acc, diff);
+            }
+        }
+    }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[warp] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+        DF y{__shfl_down_sync(0xffffffffu, acc.hi, o), __shfl_down_sync(0xffffffffu, acc.lo, o)};
+        acc = df_add(acc, y);
+    }
+    if (lane == 0) sh[warp] = acc;
     __syncthreads();
-    double t = 0.0;
-    if (threadIdx.x < 32) {
-        t = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    if (threadIdx.x == 0) {
+        DF t = sh[0];
+        for (int w = 1; w < kThreads / 32; ++w) t = df_add(t, sh[w]);
+        partials[blockIdx.x] = (double)t.hi + (double)t.lo;
+        __threadfence();
+        s_last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
-    return t;
-}
-
-__global__ void __launch_bounds__(kThreads) volume_partial(long long nrays, const int *__restrict__ off,
-                                                           const float *__restrict__ d, long long cap,
-                                                           double *partials, ldni_info_t *info) {
-    __shared__ double sh[kThreads / 32];
-    double acc = 0.0;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
-         p += (long long)gridDim.x * blockDim.x) {
-        const long long b = off[p];
-        long long e = off[p + 1];
-        if ((e - b) & 1) {
-            atomicAdd(&info->odd_rays, 1u);
-            set_status(info, LDNI_ST_ODD);
-            continue;
-        }
-        if (e > cap) e = cap;
-        for (long long k = b; k + 1 < e; k += 2) acc += (double)d[k + 1] - (double)d[k];
+    __syncthreads();
+    if (!s_last) return;
+    // last block: FP64 sum of the block partials in a fixed order (each
+    // thread a strided subset, then a fixed tree), loads issued in parallel
+    __threadfence();
+    __shared__ double shd[kThreads];
+    const volatile double *vp = partials;
+    double sum = 0.0;
+    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) sum += vp[k];
+    shd[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = kThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) shd[threadIdx.x] += shd[threadIdx.x + w];
+        __syncthreads();
     }
-    acc = block_sum_d(acc, sh);
-    if (threadIdx.x == 0) partials[blockIdx.x] = acc;
-}
-
-__global__ void __launch_bounds__(kThreads) volume_final(const double *partials, int nblocks, double h2,
-                                                         double *vol) {
-    __shared__ double sh[kThreads / 32];
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < nblocks; k += blockDim.x) acc += partials[k];
-    acc = block_sum_d(acc, sh);
-    if (threadIdx.x == 0) *vol = acc * h2;
+    if (threadIdx.x == 0) *vol = shd[0] * h2;
 }
 
 int volume_blocks(long long nrays) {
-    long long b = (nrays + kThreads - 1) / kThreads;
-    const long long lim = (long long)num_sms() * 8;
+    long long b = (nrays + (long long)kThreads * kRaysPerThread - 1) / ((long long)kThreads * kRaysPerThread);
+    const long long lim = (long long)num_sms() * 8;  // grid-stride beyond one resident wave
     if (b > lim) b = lim;
     return (int)(b > 0 ? b : 1);
 }
@@ -68,7 +129,7 @@ using namespace ldni;
 
 extern "C" int ldni_volume_workspace_size(int32_t res, size_t *bytes) {
     if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
-    *bytes = align_up(sizeof(double) * (size_t)volume_blocks((long long)res * res));
+    *bytes = align_up(sizeof(double) * (size_t)volume_blocks((long long)res * res) + sizeof(double));
     return LDNI_OK;
 }
 
@@ -79,11 +140,14 @@ extern "C" int ldni_volume(const ldni_layers_t *L, const ldni_grid_t *grid, doub
         return LDNI_EINVAL;
     const long long N = (long long)grid->res * grid->res;
     const int nb = volume_blocks(N);
-    if (ws_bytes < sizeof(double) * (size_t)nb) return LDNI_EWORKSPACE;
+    if (ws_bytes < sizeof(double) * (size_t)nb + sizeof(double)) return LDNI_EWORKSPACE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *partials = static_cast<double *>(ws);
+    unsigned *done = reinterpret_cast<unsigned *>(partials + nb);
+    if (cudaMemsetAsync(done, 0, sizeof(unsigned), s) != cudaSuccess) return LDNI_ECUDA;
     const double h = (double)grid->width / (double)grid->res;
-    LDNI_LAUNCH(K_VOL_PARTIAL, s, volume_partial<<<nb, kThreads, 0, s>>>(N, L->offsets, L->depth, L->capacity, partials, info));
-    LDNI_LAUNCH(K_VOL_FINAL, s, volume_final<<<1, kThreads, 0, s>>>(partials, nb, h * h, vol));
+    LDNI_LAUNCH(K_VOL_PARTIAL, s,
+                volume_kernel<<<nb, kThreads, 0, s>>>(N, L->offsets, L->depth, L->capacity, partials, done, h * h,
+                                                      vol, info));
     return cuda_status();
 }
