@@ -32,7 +32,7 @@ import numpy as np  # noqa: E402
 METRIC = "LDNI rays/s & samples/s at 1024²; learned-sized 1-pass vs exact 2-pass speedup"
 RES = 1024
 WORKLOAD = ("noisy geodesic sphere freq 256 (655,362 verts / 1,310,720 tris, r 0.35, 4-octave radial noise 0.05)"
-            " -> 3 LDNIs at 1024^2 (exact two-pass) -> union with resident (2,3) torus-knot LDNIs -> volume")
+            " -> 3 LDNIs at 1024^2 -> union with resident (2,3) torus-knot LDNIs -> volume")
 
 
 def _dist_env():
@@ -232,6 +232,67 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
             "api": "paper_1009_0794_gb300.sample / boolean / volume (exact sizing: one count readback per call)"}
 
 
+def _capacity_net(args):
+    """The per-tile capacity network: loaded from --net if given, else
+    trained here on 200 seeded noisy spheres at 512^2 by the library's own
+    training kernels."""
+    from paper_1009_0794_gb300 import capacity
+    if args.net and os.path.exists(args.net):
+        return capacity.CapacityNet.load(args.net), {"source": args.net}
+    t0 = time.perf_counter()
+    net, meta = capacity.train_default(count=200, res=512, steps=1500)
+    meta["seconds"] = time.perf_counter() - t0
+    meta["source"] = "trained in this run"
+    return net, meta
+
+
+def _capture(lib, fn, warm=3):
+    """Capture fn's launches (all on torch's current stream) into a CUDA
+    graph; returns (graph, library kernels per replay)."""
+    import torch
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(warm):
+            fn()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    c0 = int(lib.ldni_launch_count())
+    with torch.cuda.graph(g):
+        fn()
+    torch.cuda.synchronize()
+    return g, int(lib.ldni_launch_count()) - c0
+
+
+def _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, reps):
+    """Sampling alone, exact two-pass vs learned one-pass, each as one CUDA
+    graph, same mesh and GPU, L2 flushed before every replay; outputs
+    compared bit for bit."""
+    import torch
+    res = {}
+    for name, p in (("exact2", plan), ("learned1", lplan)):
+        g, nl = _capture(lib, lambda: p.run(vt, tt))
+        res[name + "_kernels"] = nl
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        res[name + "_ms"] = float(np.median(ts))
+        p.finish()
+    res["speedup"] = res["exact2_ms"] / res["learned1_ms"]
+    res["overflow_tiles"] = lplan.overflow_tiles()
+    res["tiles"] = 3 * ldni.ntiles(plan.grid.res)
+    res["identical_output"] = all(ldni.identical(a, b) for a, b in zip(plan.outs, lplan.outs))
+    return res
+
+
 def _events(n):
     """n timing events with their CUDA handles created (torch creates an
     event lazily at its first record)."""
@@ -265,6 +326,10 @@ def run_ours(args):
     A0 = ldni.sample(vt, tt, grid, "all", check_odd=True)
     n_sphere = [L.n for L in A0]
     plan = ldni.SamplePlan(len(sv), len(st), grid, n_sphere)
+    net, train_meta = _capacity_net(args)
+    lplan = ldni.LearnedPlan(len(sv), len(st), grid, n_sphere, slab_samples=3 * RES * RES * 4, net=net,
+                             margin=args.margin, feature_stride=32)
+    main_plan = lplan if args.mode == "learned1" else plan
     bws = torch.empty(ldni.boolean_workspace_size(RES), dtype=torch.uint8, device=dev)
     vws = torch.empty(ldni.volume_workspace_size(RES), dtype=torch.uint8, device=dev)
     binfo = ldni.new_info()
@@ -274,83 +339,86 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step():
-        plan.run(vt, tt)
+        main_plan.run(vt, tt)
         for a in range(3):
-            ldni.boolean(plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=False)
+            ldni.boolean(main_plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=False)
             ldni.volume(U[a], out=vol_views[a], ws=vws, info=binfo, sync=False)
 
-    # per-kernel profile during warm-up: find the dominant kernel
-    cap = 64
-    ev_b = _events(cap)
-    ev_e = _events(cap)
     import ctypes
-    arr_b = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_b])
-    arr_e = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_e])
-    ids = (ctypes.c_int32 * cap)()
     for w in range(max(args.warmup, 3)):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    _lib.check(lib.ldni_profile_set(arr_b, arr_e, ids, cap, 0), "ldni_profile_set")
-    flush.zero_()
-    step()
-    torch.cuda.synchronize()
-    nrec = min(int(lib.ldni_profile_recorded()), cap)
-    _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
-    per_kernel = {}
-    for k in range(nrec):
-        per_kernel.setdefault(int(ids[k]), []).append(ev_b[k].elapsed_time(ev_e[k]))
-    totals = {kid: sum(v) for kid, v in per_kernel.items()}
-    dominant = max(totals, key=totals.get)
-    launches_per_call = {kid: len(v) for kid, v in per_kernel.items()}
-    meta = plan.finish()
-    n_union = [int(x) for x in [0, 0, 0]]
+    main_plan.finish()
+    n_union = [0, 0, 0]
     # exact union sizes (one sync, outside the timed region)
     for a in range(3):
-        Ua = ldni.boolean(plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=True)
-        n_union[a] = Ua.n
+        n_union[a] = ldni.boolean(main_plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=True).n
 
-    # timed region: K steps, per-step events, L2 flushed between steps,
-    # dominant kernel timed by its own events
+    # the whole step as one CUDA graph: one launch per step
+    g_step, launches_per_step = _capture(lib, step)
+
+    # per-kernel times: a copy of the step graph with every library kernel
+    # bracketed by events, replayed (synchronised) once per measured step
+    cap = 64
+    ev_b, ev_e = _events(cap), _events(cap)
+    arr_b = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_b])
+    arr_e = (ctypes.c_void_p * cap)(*[e.cuda_event for e in ev_e])
+    ids = (ctypes.c_int32 * cap)()
+    _lib.check(lib.ldni_profile_set(arr_b, arr_e, ids, cap, 0), "ldni_profile_set")
+    g_prof, _ = _capture(lib, step, warm=0)
+    nrec = min(int(lib.ldni_profile_recorded()), cap)
+    _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
+    kid_of = [int(ids[k]) for k in range(nrec)]
+
+    learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)))
+    learned["train"] = train_meta
+
+    # timed region: K graph replays, per-step events, L2 flushed between steps
     steps = args.steps
-    dk_b = _events(steps * launches_per_call[dominant])
-    dk_e = _events(len(dk_b))
-    dk_arr_b = (ctypes.c_void_p * len(dk_b))(*[e.cuda_event for e in dk_b])
-    dk_arr_e = (ctypes.c_void_p * len(dk_e))(*[e.cuda_event for e in dk_e])
     st_b = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     st_e = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     clocks = ClockSampler(local)
     clocks.start()
-    # settle clocks under load before the measured steps
-    t_settle = time.perf_counter()
+    t_settle = time.perf_counter()  # settle clocks under load before the measured steps
     while time.perf_counter() - t_settle < args.settle:
         flush.zero_()
-        step()
+        g_step.replay()
         torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    launches0 = int(lib.ldni_launch_count())
-    _lib.check(lib.ldni_profile_set(dk_arr_b, dk_arr_e, None, len(dk_b), dominant), "ldni_profile_set")
     for k in range(steps):
         flush.zero_()
         st_b[k].record()
-        step()
+        g_step.replay()
         st_e[k].record()
     torch.cuda.synchronize()
-    _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
-    launches = int(lib.ldni_launch_count()) - launches0
     if dist:
         dist.barrier()
     clk = clocks.stop()
+    launches = launches_per_step * steps
     step_ms = [st_b[k].elapsed_time(st_e[k]) for k in range(steps)]
     total_ms = float(sum(step_ms))
-    dk_ms = [dk_b[k].elapsed_time(dk_e[k]) for k in range(len(dk_b))]
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    plan.finish()  # raises if any step overflowed or mis-snapped
+    main_plan.finish()  # raises if any step overflowed or mis-snapped
+
+    # per-kernel averages over the same number of profiled replays
+    per_kernel = {}
+    for k in range(steps):
+        flush.zero_()
+        g_prof.replay()
+        torch.cuda.synchronize()
+        for r, kid in enumerate(kid_of):
+            per_kernel.setdefault(kid, []).append(ev_b[r].elapsed_time(ev_e[r]))
+    reps = float(steps)
+    totals = {kid: sum(v) / reps for kid, v in per_kernel.items()}
+    dominant = max(totals, key=totals.get)
+    launches_per_call = {kid: kid_of.count(kid) for kid in totals}
+    dk_ms = per_kernel[dominant]
 
     rays_per_step = 3 * RES * RES
     value = ws * rays_per_step * steps / (total_ms * 1e-3)
@@ -386,19 +454,21 @@ def run_ours(args):
             traffic = tj[name]["bytes_per_launch"]
     except Exception:
         traffic = None
-    stages = {lib.ldni_kernel_name(k).decode(): {"ms_per_step": float(np.sum(v)), "launches_per_step": len(v)}
-              for k, v in sorted(per_kernel.items())}
+    stages = {lib.ldni_kernel_name(k).decode(): {"ms_per_step": totals[k], "launches_per_step": launches_per_call[k]}
+              for k in sorted(totals)}
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "res": RES, "axes": 3, "verts": len(sv), "tris": len(st),
-                   "mode": "exact2", "partner": "(2,3) torus knot tube, 8,192 verts / 16,384 tris, resident LDNIs",
+                   "mode": args.mode, "partner": "(2,3) torus knot tube, 8,192 verts / 16,384 tris, resident LDNIs",
                    "l2": "flushed between steps (256 MiB write, outside the per-step events)",
+                   "launch": "each step is one CUDA graph replay",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "samples_per_s": samples_per_s,
         "samples_per_step": int(sum(n_sphere)),
-        "learned_speedup": None,
+        "learned_speedup": learned["speedup"],
+        "learned": learned,
         "roofline": {"bound": "hbm", "kernel": lib.ldni_kernel_name(dominant).decode(), "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
@@ -430,6 +500,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed load before the timed steps")
+    ap.add_argument("--mode", default="learned1", choices=["learned1", "exact2"])
+    ap.add_argument("--margin", type=float, default=0.25)
+    ap.add_argument("--net", default="", help="saved capacity network (.npz); trained when absent")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

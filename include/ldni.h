@@ -107,6 +107,25 @@ typedef struct {
     uint32_t odd_rays; /* rays with an odd count seen by the call */
 } ldni_info_t;
 
+/* The per-tile capacity network of the one-pass sampler: 12 tile features
+ * -> 64 -> 64 -> 64 -> 1 with ReLU on the hidden layers.  Weights are BF16,
+ * row-major [out][in], layers concatenated: W0 [64][12] at 0, W1 [64][64] at
+ * 768, W2 [64][64] at 4864, W3 [1][64] at 8960 (9024 values).  Biases are
+ * FP32: b0[64] at 0, b1[64] at 64, b2[64] at 128, b3[1] at 192 (193 values).
+ * Output y predicts log1p(largest ray count in the tile); the tile's layer
+ * capacity is k = ceil(expm1(y) * (1 + margin)) rounded up to even, in
+ * [2, 64]. */
+typedef struct {
+    const uint16_t *w; /* device, 9024 BF16 weights */
+    const float *b;    /* device, 193 FP32 biases */
+    float margin;
+} ldni_mlp_t;
+
+#define LDNI_MLP_IN 12
+#define LDNI_MLP_WEIGHTS 9024
+#define LDNI_MLP_BIASES 193
+#define LDNI_TILE_RAYS 4096 /* a tile = 4096 consecutive rays of one image (CSR order) */
+
 /* ---- helpers ------------------------------------------------------- */
 
 /* Human-readable text for a return code (static storage, never NULL). */
@@ -162,6 +181,67 @@ int ldni_sample_count(const float *verts, int64_t nv, const int32_t *tris, int64
 int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
                      int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                      void *stream);
+
+/* ---- one-pass sampling with learned capacity ------------------------------ */
+
+/* Workspace bytes for ldni_sample_learned with a slab of slab_samples slots. */
+int ldni_sample_learned_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis, int64_t slab_samples,
+                                       size_t *bytes_host);
+
+/*
+ * The LDNIs of ldni_sample (identical output) from ONE traversal of the mesh
+ * instead of the count-then-fill pair.  The paper's count pass exists to size
+ * each pixel's layer list before the layers are captured (Section 3: the
+ * stencil pass, then passes 2..n_max); here a network predicts, per tile of
+ * LDNI_TILE_RAYS rays, the largest layer count k_t of its rays from features
+ * of a 1-in-feature_stride triangle subsample (count, projected area, mean
+ * |n_a|, depth histogram).  Every ray of tile t gets k_t slots of a slab in
+ * the workspace; a crossing that does not fit marks its tile, and marked
+ * tiles are filled again by the exact method, so the output never depends on
+ * the prediction.
+ *   mlp          : host pointer to the network, or NULL to give every tile
+ *                  fixed_layers slots (the baseline without the network).
+ *   slab_samples : slab slots in the workspace; tiles beyond it are redone.
+ *   overflow_tiles: optional device int32, receives the number of redone tiles.
+ * Other arguments, output and status as ldni_sample.
+ */
+int ldni_sample_learned(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                        int32_t axis, const ldni_mlp_t *mlp, int32_t fixed_layers, int32_t feature_stride,
+                        int64_t slab_samples, ldni_layers_t *out, ldni_info_t *info, int32_t *overflow_tiles, void *ws,
+                        size_t ws_bytes, void *stream);
+
+/* Tile features as the network sees them: raw = device scratch of
+ * naxes * ntiles * 11 floats (cleared by the call); X = device output of
+ * naxes * ntiles * 12 floats, rows image-major then tile.  ntiles =
+ * ceil(res^2 / LDNI_TILE_RAYS). */
+int ldni_tile_features(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                       int32_t axis, int32_t feature_stride, float *raw, float *X, void *stream);
+
+/* Training target per tile of one exact LDNI: label[t] = log1p(largest ray
+ * count of tile t), from its CSR offsets (device, res*res+1). */
+int ldni_tile_labels(const int32_t *offsets, int32_t res, float *label, void *stream);
+
+/* Network outputs y[n] (device) for feature rows X[n][12] (device). */
+int ldni_mlp_forward(const ldni_mlp_t *mlp, const float *X, int64_t n, float *y, void *stream);
+
+/* Workspace bytes for ldni_mlp_train_step on n rows. */
+int ldni_mlp_train_workspace_size(int64_t n, size_t *bytes_host);
+
+/*
+ * One Adam step on the capacity network, all on the device.
+ *   master_w [9024], b [193]: FP32 parameters, updated in place;
+ *   w_bf16 [9024]: refreshed BF16 copy used by the forward pass;
+ *   m, v [9024 + 193]: Adam moments (weights first, then biases);
+ *   X [n][12], label [n]: training rows;
+ *   loss: device float, receives the loss before the update;
+ *   grad: optional device [9024 + 193], receives the gradient.
+ * Loss = mean over rows of w * (y - label)^2 with w = under_weight where
+ * y < label (a predicted capacity below the truth costs a redo) and 1
+ * otherwise.  Forward with the BF16 weights, FP32 everywhere else.
+ */
+int ldni_mlp_train_step(float *master_w, float *b, uint16_t *w_bf16, float *m, float *v, const float *X,
+                        const float *label, int64_t n, float lr, int32_t step, float under_weight, float *loss,
+                        float *grad, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- Boolean (Section 4.1, small-interval removal Section 4.1.1) ----- */
 
@@ -242,7 +322,9 @@ int64_t ldni_profile_recorded(void);
 
 /* Name of a kernel id (1 count_tri, 2 count_big, 4 scan_empty, 5 scan,
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
- * two passes of ldni_boolean_static), 11 volume, 13 boolean). */
+ * two passes of ldni_boolean_static), 11 volume, 13 boolean, 14 features,
+ * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
+ * 21 mlp, 22 adjoint). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

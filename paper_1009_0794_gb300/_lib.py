@@ -28,6 +28,13 @@ class Grid(ctypes.Structure):
     _fields_ = [("origin", ctypes.c_float * 3), ("width", ctypes.c_float), ("res", ctypes.c_int32)]
 
 
+class MLP(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("b", ctypes.c_void_p), ("margin", ctypes.c_float)]
+
+
+MLP_IN, MLP_WEIGHTS, MLP_BIASES, TILE_RAYS = 12, 9024, 193, 4096
+
+
 class Layers(ctypes.Structure):
     _fields_ = [("offsets", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("nx", ctypes.c_void_p),
                 ("ny", ctypes.c_void_p), ("nz", ctypes.c_void_p), ("tri_id", ctypes.c_void_p),
@@ -64,6 +71,15 @@ SIGNATURES = {
     "ldni_boolean_static": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P]),
     "ldni_volume_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_volume": (ctypes.c_int, [_PL, _PG, _P, _P, _P, _SZ, _P]),
+    "ldni_sample_learned_workspace_size": (ctypes.c_int, [_I64, _I64, _I32, _I32, _I64, ctypes.POINTER(_SZ)]),
+    "ldni_sample_learned": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _P, _I32, _I32, _I64, _PL, _P, _P, _P,
+                                           _SZ, _P]),
+    "ldni_tile_features": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _I32, _P, _P, _P]),
+    "ldni_tile_labels": (ctypes.c_int, [_P, _I32, _P, _P]),
+    "ldni_mlp_forward": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "ldni_mlp_train_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
+    "ldni_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _I64, ctypes.c_float, _I32, ctypes.c_float,
+                                           _P, _P, _P, _SZ, _P]),
     "ldni_launch_count": (ctypes.c_uint64, []),
     "ldni_profile_set": (ctypes.c_int, [_P, _P, _P, _I32, _I32]),
     "ldni_profile_recorded": (ctypes.c_int64, []),

@@ -71,6 +71,8 @@ extern "C" const char *ldni_kernel_name(int32_t id) {
     static const char *names[ldni::K_NUM] = {"none",       "count_tri",  "count_big", "unused",
                                              "scan_empty", "scan",       "fill_tri",  "fill_big",
                                              "sort_rays",  "bool_count", "bool_write", "volume",
-                                             "unused",     "boolean"};
+                                             "unused",     "boolean",    "features",  "capacity",
+                                             "layout",     "onepass",    "onepass_big", "redo",
+                                             "gather",     "mlp",        "adjoint"};
     return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
 }

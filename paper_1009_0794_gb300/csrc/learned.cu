@@ -1,0 +1,851 @@
+// LDNI sampling in one traversal with a learned per-tile layer capacity.
+//
+// The exact form counts every ray's crossings before it can place them
+// (Section 3: the stencil pass that finds each pixel's depth complexity n_p,
+// then one rendering pass per layer).  Here a small network predicts, for
+// every tile of kTilePix rays, how many layers k_t its rays can have, so the
+// mesh is traversed once:
+//
+//   features : per tile, from a 1-in-`stride` subsample of the triangles:
+//              triangle count, projected area in pixels, mean |n_a|, and an
+//              8-bin histogram of triangle depth (a proxy for layering);
+//   mlp      : features -> log1p(k_t) -> an even capacity k_t (mlp.cuh);
+//   layout   : every ray of tile t owns k_t slab slots;
+//   one pass : every crossing takes the next slot of its ray (the atomic
+//              cursor is also the ray's exact count) and stores (depth, tri)
+//              if it fits, else marks its tile as overflowed; two-layer
+//              tiles place crossings by orientation instead (see onepass_hit);
+//   scan     : exact CSR offsets from the counts;
+//   redo     : tiles that overflowed are filled again by the exact method
+//              (a second traversal restricted to them; no-op when none did);
+//   gather   : every ray is ordered by (depth, tri_id) and written to its CSR
+//              rows, normals from the per-triangle table the pass wrote.
+//
+// Depths, normals and ordering come from the same device functions as the
+// exact two-pass form, so both forms produce identical LDNIs.
+#include <cuda_bf16.h>
+
+#include "mlp.cuh"
+#include "sample_common.cuh"
+
+namespace ldni {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxLayerCap = 64;   // largest k_t the layout hands out
+
+struct LImg {
+    int *count[3];
+    int *exitc[3];               // crossings whose face leaves the solid (two-layer tiles)
+    const int *offsets[3];
+    float *depth[3];
+    float *nx[3];
+    float *ny[3];
+    float *nz[3];
+    int *tri[3];
+    long long cap[3];
+    // per tile
+    float *feat[3];              // [ntiles][kRawFeat]
+    int *kcap[3];                // layers per ray
+    long long *slab_base[3];     // first slab slot of the tile
+    int *over[3];                // 1 = overflowed, redone exactly
+    int2 *slab;                  // (depth bits, tri) per slot
+    float *nrm[3];               // per-triangle unit normal (x, y, z tables)
+    long long slab_cap;
+    int *any_over;
+};
+
+template <class T>
+__device__ __forceinline__ T pick3(T const (&arr)[3], int a) {
+    return a == 0 ? arr[0] : (a == 1 ? arr[1] : arr[2]);
+}
+
+// ---- features --------------------------------------------------------------
+
+// Shared-memory accumulators when all tiles of all images fit in them.
+constexpr int kFeatSmemTiles = 1024;  // tiles x images
+
+// Tile of one triangle on image A and its feature contributions; tile -1
+// when it covers no pixel centre.
+template <int A>
+__device__ __forceinline__ int feature_of(const TriView &T, const GridDev &g, float &area_px, int &bin) {
+    constexpr int U = (A + 1) % 3, V = (A + 2) % 3;
+    const int u0 = T.q[0][U], u1 = T.q[1][U], u2 = T.q[2][U];
+    const int v0 = T.q[0][V], v1 = T.q[1][V], v2 = T.q[2][V];
+    const int umin = min(u0, min(u1, u2)), umax = max(u0, max(u1, u2));
+    const int vmin = min(v0, min(v1, v2)), vmax = max(v0, max(v1, v2));
+    const int i0 = max((umin + 127) >> 8, 0), i1 = min((umax - 128) >> 8, g.res - 1);
+    const int j0 = max((vmin + 127) >> 8, 0), j1 = min((vmax - 128) >> 8, g.res - 1);
+    if (i0 > i1 || j0 > j1) return -1;
+    const long long p = (long long)((j0 + j1) >> 1) * g.res + ((i0 + i1) >> 1);
+    const float du1 = (float)(u1 - u0), dv1 = (float)(v1 - v0), du2 = (float)(u2 - u0), dv2 = (float)(v2 - v0);
+    area_px = fabsf(du1 * dv2 - dv1 * du2) * (0.5f / (kSubpix * kSubpix));
+    const float ca = (comp(T.p[0], A) + comp(T.p[1], A) + comp(T.p[2], A)) * (1.0f / 3.0f);
+    const float rel = (ca - g.o[A]) * g.s / (float)(kSubpix * g.res);  // 0..1 across the cube
+    bin = min(7, max(0, (int)(rel * 8.0f)));
+    return (int)(p >> kTileBits);
+}
+
+// Every lane of the warp calls this.  When all lanes hit the same tile (the
+// usual case: neighbouring triangles), the warp adds its sums with one set of
+// atomics; otherwise each lane adds its own.
+template <int A>
+__device__ __forceinline__ void feature_axis(const TriView &T, bool valid, float w, const GridDev &g, float *acc,
+                                             int ntiles, bool smem, const LImg &o, float absn, int *s_lo, int *s_hi) {
+    float area = 0.0f;
+    int bin = 0;
+    const int tile = valid ? feature_of<A>(T, g, area, bin) : -1;
+    const int t0 = __shfl_sync(0xffffffffu, tile, 0);
+    const bool uniform = __all_sync(0xffffffffu, tile == t0);
+    if (uniform && t0 < 0) return;
+    auto base = [&](int t) {
+        return smem ? acc + ((long long)A * ntiles + t) * kRawFeat : pick3(o.feat, A) + (long long)t * kRawFeat;
+    };
+    if (uniform) {
+        float c = w, ar = area * w, an = absn * w;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+            c += __shfl_xor_sync(0xffffffffu, c, d);
+            ar += __shfl_xor_sync(0xffffffffu, ar, d);
+            an += __shfl_xor_sync(0xffffffffu, an, d);
+        }
+        unsigned bins[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) bins[k] = __popc(__ballot_sync(0xffffffffu, bin == k));
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(s_lo + A, t0);
+            atomicMax(s_hi + A, t0);
+            float *f = base(t0);
+            atomicAdd(f + 0, c);
+            atomicAdd(f + 1, ar);
+            atomicAdd(f + 2, an);
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (bins[k]) atomicAdd(f + 3 + k, (float)bins[k] * w);
+        }
+        return;
+    }
+    if (tile < 0) return;
+    atomicMin(s_lo + A, tile);
+    atomicMax(s_hi + A, tile);
+    float *f = base(tile);
+    atomicAdd(f + 0, w);
+    atomicAdd(f + 1, area * w);
+    atomicAdd(f + 2, absn * w);
+    atomicAdd(f + 3 + bin, w);
+}
+
+__global__ void __launch_bounds__(kThreads) features_kernel(const float *__restrict__ verts,
+                                                            const int *__restrict__ tris, int nt, int nv, GridDev g,
+                                                            int ax_lo, int ax_hi, int stride, int ntiles, LImg o) {
+    extern __shared__ float acc[];
+    __shared__ int s_lo[3], s_hi[3];  // tiles this block touched, per image
+    const int naxes = ax_hi - ax_lo + 1;
+    const bool smem = ntiles * naxes <= kFeatSmemTiles;
+    if (threadIdx.x < 3) {
+        s_lo[threadIdx.x] = ntiles;
+        s_hi[threadIdx.x] = -1;
+    }
+    if (smem) {
+        for (int k = threadIdx.x; k < 3 * ntiles * kRawFeat; k += blockDim.x) acc[k] = 0.0f;
+    }
+    __syncthreads();
+    const long long nsamp = ((long long)nt + stride - 1) / stride;
+    const float w = (float)stride;
+    // uniform loop bound per block: whole warps take part in the collectives
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < nsamp; base += (long long)gridDim.x * blockDim.x) {
+        const long long sidx = base + threadIdx.x;
+        TriView T;
+        bool valid = false;
+        float nx = 0.f, ny = 0.f, nz = 0.f;
+        if (sidx < nsamp) {
+            valid = load_tri(verts, tris, (int)(sidx * stride), nv, g, T) == 0;
+            if (valid) face_normal(T.p[0], T.p[1], T.p[2], nx, ny, nz);
+        }
+        if (ax_lo <= 0 && 0 <= ax_hi) feature_axis<0>(T, valid, w, g, acc, ntiles, smem, o, fabsf(nx), s_lo, s_hi);
+        if (ax_lo <= 1 && 1 <= ax_hi) feature_axis<1>(T, valid, w, g, acc, ntiles, smem, o, fabsf(ny), s_lo, s_hi);
+        if (ax_lo <= 2 && 2 <= ax_hi) feature_axis<2>(T, valid, w, g, acc, ntiles, smem, o, fabsf(nz), s_lo, s_hi);
+    }
+    if (smem) {
+        __syncthreads();
+        for (int a = ax_lo; a <= ax_hi; ++a) {
+            if (s_hi[a] < s_lo[a]) continue;
+            const int k0 = s_lo[a] * kRawFeat, k1 = (s_hi[a] + 1) * kRawFeat;
+            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+                const float v = acc[(long long)a * ntiles * kRawFeat + k];
+                if (v != 0.0f) atomicAdd(pick3(o.feat, a) + k, v);
+            }
+        }
+    }
+}
+
+// ---- capacity: network or fixed ---------------------------------------------
+
+__device__ __forceinline__ int capacity_from(float y, float margin) {
+    const float layers = expm1f(fmaxf(y, 0.0f)) * (1.0f + margin);
+    int k = (int)ceilf(layers - 1e-3f);
+    k = (k + 1) & ~1;  // rays of closed meshes have even counts
+    return min(max(k, 2), kMaxLayerCap);
+}
+
+// One warp per tile; the weights sit in shared memory.  Hidden units are
+// computed two per lane; the output is a warp sum, so predictions agree with
+// ldni_mlp_forward's to FP32 rounding (the capacity is a hint either way).
+constexpr int kCapWarps = 8;
+
+__global__ void __launch_bounds__(kCapWarps * 32) capacity_kernel(int ntiles, long long nrays, int ax_lo, int naxes,
+                                                                  LImg o, const __nv_bfloat16 *__restrict__ W,
+                                                                  const float *__restrict__ b, float margin,
+                                                                  int fixed_k) {
+    // weights transposed to [in][out] so that lane u reads column u: consecutive lanes, no bank conflicts
+    __shared__ __nv_bfloat16 sw[kMlpWeights];
+    __shared__ float sb[kMlpBiases];
+    __shared__ float act[kCapWarps][2][kMlpHidden];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * kCapWarps + warp;
+    if (W) {
+        auto put = [&](int i, __nv_bfloat16 v) {
+            int dst = i;
+            if (i < kW1) {
+                dst = kW0 + (i % kMlpIn) * kMlpHidden + i / kMlpIn;
+            } else if (i < kW3) {
+                const int base = i < kW2 ? kW1 : kW2, r = i - base;
+                dst = base + (r % kMlpHidden) * kMlpHidden + r / kMlpHidden;
+            }
+            sw[dst] = v;
+        };
+        if ((reinterpret_cast<uintptr_t>(W) & 15) == 0) {  // 8 weights per 16-byte load, all loads in flight
+            const uint4 *W4 = reinterpret_cast<const uint4 *>(W);
+            constexpr int n4 = kMlpWeights / 8;
+#pragma unroll 4
+            for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+                const uint4 v = W4[q];
+                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) put(q * 8 + r, h[r]);
+            }
+        } else {
+            for (int i = threadIdx.x; i < kMlpWeights; i += blockDim.x) put(i, W[i]);
+        }
+        for (int i = threadIdx.x; i < kMlpBiases; i += blockDim.x) sb[i] = b[i];
+    }
+    __syncthreads();
+    if (k >= ntiles * naxes) return;
+    const int a = ax_lo + k / ntiles, tile = k % ntiles;
+    if (!W) {
+        if (lane == 0) pick3(o.kcap, a)[tile] = fixed_k;
+        return;
+    }
+    float *x = act[warp][0];
+    float *h = act[warp][1];
+    if (lane == 0) {
+        const long long p0 = (long long)tile << kTileBits;
+        const float frac = (float)min((long long)kTilePix, nrays - p0) / (float)kTilePix;
+        normalise_features(pick3(o.feat, a) + (long long)tile * kRawFeat, frac, x);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int u = lane + 32 * half;
+        float acc = sb[kB0 + u];
+#pragma unroll
+        for (int i = 0; i < kMlpIn; ++i) acc = fmaf(__bfloat162float(sw[kW0 + i * kMlpHidden + u]), x[i], acc);
+        h[u] = fmaxf(acc, 0.0f);
+    }
+    __syncwarp();
+    float *in = h, *out = x;
+#pragma unroll
+    for (int layer = 1; layer < 3; ++layer) {
+        const int woff = layer == 1 ? kW1 : kW2, boff = layer == 1 ? kB1 : kB2;
+        float r[2];
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            const int u = lane + 32 * half;
+            float acc = sb[boff + u];
+#pragma unroll 16
+            for (int i = 0; i < kMlpHidden; ++i) acc = fmaf(__bfloat162float(sw[woff + i * kMlpHidden + u]), in[i], acc);
+            r[half] = fmaxf(acc, 0.0f);
+        }
+        __syncwarp();
+        out[lane] = r[0];
+        out[lane + 32] = r[1];
+        __syncwarp();
+        float *tmp = in;
+        in = out;
+        out = tmp;
+    }
+    float y = __bfloat162float(sw[kW3 + lane]) * in[lane] + __bfloat162float(sw[kW3 + lane + 32]) * in[lane + 32];
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
+    if (lane == 0) pick3(o.kcap, a)[tile] = capacity_from(y + sb[kB3], margin);
+}
+
+// One block lays out the slab: tile t of image a gets npix * k_t slots.
+// Tiles that no longer fit get k_t = 0 (all their crossings go to the redo).
+__global__ void __launch_bounds__(1024) layout_kernel(int ntiles, long long nrays, int ax_lo, int naxes, LImg o) {
+    __shared__ long long sh[33];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const int total = ntiles * naxes;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < total; base += blockDim.x) {
+        const int k = base + threadIdx.x;
+        long long need = 0;
+        int a = ax_lo, tile = 0;
+        if (k < total) {
+            a = ax_lo + k / ntiles;
+            tile = k % ntiles;
+            const long long p0 = (long long)tile << kTileBits;
+            need = min((long long)kTilePix, nrays - p0) * pick3(o.kcap, a)[tile];
+        }
+        long long x = need;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) sh[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, w, d);
+                if (lane >= d) w += y;
+            }
+            sh[lane] = w;
+        }
+        __syncthreads();
+        const long long start = carry + x - need + (warp > 0 ? sh[warp - 1] : 0);
+        if (k < total) {
+            if (start + need > o.slab_cap) pick3(o.kcap, a)[tile] = 0;
+            pick3(o.slab_base, a)[tile] = start;
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = start + need;
+        __syncthreads();
+    }
+}
+
+// ---- one pass ----------------------------------------------------------------
+
+// A tile given two layers per ray takes the shortcut of closed meshes: a ray
+// crossed twice is entered once and left once, so the entering crossing
+// takes slot 0 and the leaving one slot 1 - no returned atomic, only counts.
+// verify_kernel later sends every tile where some ray broke that pattern to
+// the exact redo.
+__device__ __forceinline__ void onepass_hit(int a, long long p, float d, int t, const float3 &n, int exiting,
+                                            const LImg &o) {
+    const int tile = (int)(p >> kTileBits);
+    const int kt = pick3(o.kcap, a)[tile];
+    if (kt == 2) {
+        atomicAdd(pick3(o.count, a) + p, 1);
+        if (exiting) atomicAdd(pick3(o.exitc, a) + p, 1);
+        const long long slot = pick3(o.slab_base, a)[tile] + (p & (kTilePix - 1)) * 2 + exiting;
+        o.slab[slot] = make_int2(__float_as_int(d), t);
+        return;
+    }
+    const int k = atomicAdd(pick3(o.count, a) + p, 1);
+    if (k < kt) {
+        const long long slot = pick3(o.slab_base, a)[tile] + (p & (kTilePix - 1)) * kt + k;
+        o.slab[slot] = make_int2(__float_as_int(d), t);
+    } else {
+        pick3(o.over, a)[tile] = 1;
+        *o.any_over = 1;
+    }
+}
+
+template <int A>
+__device__ __forceinline__ void onepass_axis(const TriView &T, int t, const float3 &n, int res, const LImg &o,
+                                             int *big_q, int *big_n) {
+    Setup32 S;
+    const int kind = setup_axis<A>(T, res, S);
+    if (kind == kNone) return;
+    if (kind == kBig) {
+        big_q[atomicAdd(big_n, 1)] = t * 4 + A;
+        return;
+    }
+    const unsigned long long m = hit_mask(S);
+    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
+    for (int y = 0; y < S.h; ++y) {
+        unsigned long long r = (m >> (y * S.w)) & row_mask;
+        while (r) {
+            const int x = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            const int i = S.i0 + x, j = S.j0 + y;
+            onepass_hit(A, (long long)j * res + i, S.depth(i, j), t, n, S.exiting, o);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restrict__ verts,
+                                                           const int *__restrict__ tris, int nt, int nv, GridDev g,
+                                                           int ax_lo, int ax_hi, LImg o, int *big_q, int *big_n,
+                                                           ldni_info_t *info) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        TriView T;
+        const unsigned bad = load_tri(verts, tris, t, nv, g, T);
+        if (bad) {
+            set_status(info, bad);
+            continue;
+        }
+        float3 n;
+        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
+        o.nrm[0][t] = n.x;  // coalesced: the gather looks normals up by triangle
+        o.nrm[1][t] = n.y;
+        o.nrm[2][t] = n.z;
+        if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, big_n);
+        if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, big_n);
+        if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, big_n);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) onepass_big(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                        int nv, GridDev g, LImg o, const int *big_q,
+                                                        const int *big_n) {
+    const int nq = *big_n;
+    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
+        const int code = big_q[e];
+        const int t = code >> 2, a = code & 3;
+        TriView T;
+        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        Setup64 S;
+        int i0, i1, j0, j1;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        float3 n;
+        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
+        const int w = i1 - i0 + 1;
+        const long long npx = (long long)w * (j1 - j0 + 1);
+        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+            const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
+            if (S.inside(i, j)) onepass_hit(a, (long long)j * g.res + i, S.depth(i, j), t, n, S.exiting, o);
+        }
+    }
+}
+
+// Two-layer tiles: every ray must have 0 crossings, or 2 of which exactly one
+// leaves the solid; anything else (a ray with more layers, an open or
+// self-intersecting mesh) sends the tile to the exact redo.
+__global__ void __launch_bounds__(256) verify_kernel(int ntiles, long long nrays, int ax_lo, LImg o) {
+    const int a = ax_lo + blockIdx.y;
+    const int tile = blockIdx.x;
+    if (pick3(o.kcap, a)[tile] != 2) return;
+    const long long p0 = (long long)tile << kTileBits;
+    const int npix = (int)min((long long)kTilePix, nrays - p0);
+    const int *cnt = pick3(o.count, a) + p0;
+    const int *ex = pick3(o.exitc, a) + p0;
+    bool bad = false;
+    for (int q = threadIdx.x; q < npix; q += blockDim.x) {
+        const int c = cnt[q];
+        bad |= !(c == 0 || (c == 2 && ex[q] == 1));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        pick3(o.over, a)[tile] = 1;
+        *o.any_over = 1;
+    }
+}
+
+// ---- exact redo of overflowed tiles ------------------------------------------
+
+__device__ __forceinline__ void redo_hit(int a, long long p, float d, int t, const LImg &o, const float3 &n,
+                                         ldni_info_t *info) {
+    if (!pick3(o.over, a)[p >> kTileBits]) return;
+    const int k = atomicSub(pick3(o.count, a) + p, 1) - 1;
+    const long long slot = (long long)pick3(o.offsets, a)[p] + k;
+    if (k < 0 || slot >= pick3(o.cap, a)) {
+        set_status(info, LDNI_ST_CAPACITY);
+        return;
+    }
+    pick3(o.depth, a)[slot] = d;
+    pick3(o.tri, a)[slot] = t;
+    pick3(o.nx, a)[slot] = n.x;
+    pick3(o.ny, a)[slot] = n.y;
+    pick3(o.nz, a)[slot] = n.z;
+}
+
+template <int A>
+__device__ __forceinline__ void redo_axis(const TriView &T, int t, const float3 &n, int res, const LImg &o,
+                                          ldni_info_t *info) {
+    Setup32 S;
+    if (setup_axis<A>(T, res, S) != kSmall) return;  // big triangles: redo_big
+    const unsigned long long m = hit_mask(S);
+    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
+    for (int y = 0; y < S.h; ++y) {
+        unsigned long long r = (m >> (y * S.w)) & row_mask;
+        while (r) {
+            const int x = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            const int i = S.i0 + x, j = S.j0 + y;
+            redo_hit(A, (long long)j * res + i, S.depth(i, j), t, o, n, info);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                        int nt, int nv, GridDev g, int ax_lo, int ax_hi, LImg o,
+                                                        ldni_info_t *info) {
+    if (*(volatile int *)o.any_over == 0) return;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        TriView T;
+        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        float3 n;
+        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
+        if (ax_lo <= 0 && 0 <= ax_hi) redo_axis<0>(T, t, n, g.res, o, info);
+        if (ax_lo <= 1 && 1 <= ax_hi) redo_axis<1>(T, t, n, g.res, o, info);
+        if (ax_lo <= 2 && 2 <= ax_hi) redo_axis<2>(T, t, n, g.res, o, info);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) redo_big(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                     int nv, GridDev g, LImg o, const int *big_q, const int *big_n,
+                                                     ldni_info_t *info) {
+    if (*(volatile int *)o.any_over == 0) return;
+    const int nq = *big_n;
+    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
+        const int code = big_q[e];
+        const int t = code >> 2, a = code & 3;
+        TriView T;
+        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        Setup64 S;
+        int i0, i1, j0, j1;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        float3 n;
+        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
+        const int w = i1 - i0 + 1;
+        const long long npx = (long long)w * (j1 - j0 + 1);
+        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+            const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
+            if (S.inside(i, j)) redo_hit(a, (long long)j * g.res + i, S.depth(i, j), t, o, n, info);
+        }
+    }
+}
+
+// ---- gather ----------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info) {
+    const int a = ax_lo + blockIdx.y;
+    const int *off = pick3(o.offsets, a);
+    float *D = pick3(o.depth, a);
+    int *Tr = pick3(o.tri, a);
+    float *X = pick3(o.nx, a);
+    float *Y = pick3(o.ny, a);
+    float *Z = pick3(o.nz, a);
+    const long long cap = pick3(o.cap, a);
+    const int *over = pick3(o.over, a);
+    const int *kc = pick3(o.kcap, a);
+    const long long *sb = pick3(o.slab_base, a);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
+         p += (long long)gridDim.x * blockDim.x) {
+        const long long b = off[p];
+        const long long e = off[p + 1];
+        const int c = (int)(e - b);
+        if (c & 1) {
+            atomicAdd(&info->odd_rays, 1u);
+            set_status(info, LDNI_ST_ODD);
+        }
+        if (c == 0) continue;
+        if (e > cap) {
+            set_status(info, LDNI_ST_CAPACITY);
+            continue;
+        }
+        const int tile = (int)(p >> kTileBits);
+        if (over[tile]) {  // filled exactly by the redo pass: order in place
+            sort_ray_global(b, e, D, Tr, X, Y, Z);
+            continue;
+        }
+        const int kt = kc[tile];
+        if (c > kt) {  // cannot happen for a tile that did not overflow
+            set_status(info, LDNI_ST_CAPACITY);
+            continue;
+        }
+        const long long s0 = sb[tile] + (p & (kTilePix - 1)) * kt;
+        const float *NX = o.nrm[0], *NY = o.nrm[1], *NZ = o.nrm[2];
+        if (c == 2) {  // the common case: everything in registers
+            int2 v0 = o.slab[s0], v1 = o.slab[s0 + 1];
+            if (key_less(__int_as_float(v1.x), v1.y, __int_as_float(v0.x), v0.y)) {
+                const int2 w = v0;
+                v0 = v1;
+                v1 = w;
+            }
+            const float x0 = NX[v0.y], y0 = NY[v0.y], z0 = NZ[v0.y];
+            const float x1 = NX[v1.y], y1 = NY[v1.y], z1 = NZ[v1.y];
+            D[b] = __int_as_float(v0.x);
+            D[b + 1] = __int_as_float(v1.x);
+            Tr[b] = v0.y;
+            Tr[b + 1] = v1.y;
+            X[b] = x0;
+            X[b + 1] = x1;
+            Y[b] = y0;
+            Y[b + 1] = y1;
+            Z[b] = z0;
+            Z[b + 1] = z1;
+            continue;
+        }
+        for (int x = 0; x < c; ++x) {  // copy, then order in place
+            const int2 v = o.slab[s0 + x];
+            D[b + x] = __int_as_float(v.x);
+            Tr[b + x] = v.y;
+            X[b + x] = NX[v.y];
+            Y[b + x] = NY[v.y];
+            Z[b + x] = NZ[v.y];
+        }
+        sort_ray_global(b, e, D, Tr, X, Y, Z);
+    }
+}
+
+__global__ void count_overflow(int ntiles, int ax_lo, int naxes, LImg o, int *n_over) {
+    __shared__ int sh;
+    if (threadIdx.x == 0) sh = 0;
+    __syncthreads();
+    int c = 0;
+    for (int k = threadIdx.x; k < ntiles * naxes; k += blockDim.x) c += pick3(o.over, ax_lo + k / ntiles)[k % ntiles];
+    atomicAdd(&sh, c);
+    __syncthreads();
+    if (threadIdx.x == 0) *n_over = sh;
+}
+
+// per-tile training targets: log1p of the largest ray count in the tile
+__global__ void tile_label_kernel(long long nrays, const int *off, float *label) {
+    __shared__ int mx;
+    if (threadIdx.x == 0) mx = 0;
+    __syncthreads();
+    const long long p0 = (long long)blockIdx.x << kTileBits;
+    int m = 0;
+    for (int q = threadIdx.x; q < kTilePix && p0 + q < nrays; q += blockDim.x) m = max(m, off[p0 + q + 1] - off[p0 + q]);
+    atomicMax(&mx, m);
+    __syncthreads();
+    if (threadIdx.x == 0) label[blockIdx.x] = log1pf((float)mx);
+}
+
+__global__ void normalise_kernel(int ntiles, long long nrays, int naxes, const float *raw, float *X) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ntiles * naxes) return;
+    const int tile = k % ntiles;
+    const long long p0 = (long long)tile << kTileBits;
+    const float frac = (float)min((long long)kTilePix, nrays - p0) / (float)kTilePix;
+    normalise_features(raw + (long long)k * kRawFeat, frac, X + (long long)k * kMlpIn);
+}
+
+// ---- host side -----------------------------------------------------------------
+
+struct LearnedWs {
+    int *count[3];
+    int *exitc[3];
+    int *big_n;
+    int *any_over;
+    float *feat[3];
+    int *over[3];
+    size_t clear_bytes;  // counts, flags, features and overflow marks: one memset
+    long long *scan_words;
+    int *kcap[3];
+    long long *slab_base[3];
+    int *big_q;
+    float *nrm[3];
+    int2 *slab;
+    long long slab_cap;
+};
+
+LearnedWs carve_learned_ws(Carver &c, long long nt, int res, int naxes, long long slab_samples) {
+    LearnedWs w{};
+    const long long N = (long long)res * res;
+    const long long stride = (N + 63) / 64 * 64;
+    const long long ntiles = (N + kTilePix - 1) / kTilePix;
+    const long long tstride = (ntiles + 63) / 64 * 64;
+    // one cleared block: counts | big_n, any_over (64 ints) | features | overflow marks
+    // one cleared block: counts | big_n, any_over (64 ints) | features | overflow marks | exiting counts
+    const size_t ints = (size_t)(stride * naxes + 64 + tstride * naxes * kRawFeat + tstride * naxes + stride * naxes);
+    int *block = c.take<int>(ints);
+    for (int a = 0; a < naxes; ++a) {
+        w.count[a] = block ? block + (size_t)a * stride : nullptr;
+        w.exitc[a] = block ? block + (size_t)stride * naxes + 64 + (size_t)tstride * naxes * kRawFeat +
+                                 (size_t)tstride * naxes + (size_t)a * stride
+                           : nullptr;
+        w.feat[a] = block ? reinterpret_cast<float *>(block + (size_t)stride * naxes + 64) + (size_t)a * tstride * kRawFeat
+                          : nullptr;
+        w.over[a] = block ? block + (size_t)stride * naxes + 64 + (size_t)tstride * naxes * kRawFeat + (size_t)a * tstride
+                          : nullptr;
+    }
+    w.big_n = block ? block + (size_t)stride * naxes : nullptr;
+    w.any_over = block ? block + (size_t)stride * naxes + 1 : nullptr;
+    w.clear_bytes = sizeof(int) * ints;
+    w.scan_words = c.take<long long>(csr_scan_partials(N) * naxes);
+    int *kc = c.take<int>((size_t)(tstride * naxes));
+    long long *sb = c.take<long long>((size_t)(tstride * naxes));
+    for (int a = 0; a < naxes; ++a) {
+        w.kcap[a] = kc ? kc + (size_t)a * tstride : nullptr;
+        w.slab_base[a] = sb ? sb + (size_t)a * tstride : nullptr;
+    }
+    w.big_q = c.take<int>((size_t)(nt * naxes > 0 ? nt * naxes : 1));
+    for (int k = 0; k < 3; ++k) w.nrm[k] = c.take<float>((size_t)(nt > 0 ? nt : 1));
+    w.slab = c.take<int2>((size_t)(slab_samples > 0 ? slab_samples : 1));
+    w.slab_cap = slab_samples;
+    return w;
+}
+
+int feature_blocks(long long nt, int stride) {
+    const long long nsamp = (nt + stride - 1) / stride;
+    long long b = (nsamp + kThreads - 1) / kThreads;
+    const long long lim = (long long)num_sms() * 8;  // one sampled triangle per thread where possible
+    return (int)(b < 1 ? 1 : (b > lim ? lim : b));
+}
+
+int grid_blocks(long long work) {
+    long long b = (work + kThreads - 1) / kThreads;
+    const long long lim = (long long)num_sms() * 16;
+    if (b > lim) b = lim;
+    return (int)(b > 0 ? b : 1);
+}
+
+}  // namespace
+}  // namespace ldni
+
+using namespace ldni;
+
+extern "C" int ldni_sample_learned_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis,
+                                                  int64_t slab_samples, size_t *bytes) {
+    if (!bytes || res < 1 || res > 8192 || nt < 0 || nv < 0 || axis < 0 || axis > LDNI_AXIS_ALL || slab_samples < 0)
+        return LDNI_EINVAL;
+    Carver c(nullptr, 0);
+    carve_learned_ws(c, nt, res, axis == LDNI_AXIS_ALL ? 3 : 1, slab_samples);
+    *bytes = align_up(c.off);
+    return LDNI_OK;
+}
+
+extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                   const ldni_grid_t *grid, int32_t axis, const ldni_mlp_t *mlp, int32_t fixed_layers,
+                                   int32_t feature_stride, int64_t slab_samples, ldni_layers_t *out, ldni_info_t *info,
+                                   int32_t *overflow_tiles, void *ws, size_t ws_bytes, void *stream) {
+    if (!grid_valid(grid) || !out || !info || !ws || axis < 0 || axis > LDNI_AXIS_ALL || nv <= 0 || nt < 0 ||
+        (nt > 0 && (!verts || !tris)) || slab_samples < 0 || feature_stride < 1 ||
+        (!mlp && (fixed_layers < 0 || fixed_layers > kMaxLayerCap)) || (mlp && (!mlp->w || !mlp->b)))
+        return LDNI_EINVAL;
+    if (nt > (INT_MAX / 4) || nv > INT_MAX) return LDNI_ETOOLARGE;
+    const int ax_lo = axis == LDNI_AXIS_ALL ? 0 : axis, ax_hi = axis == LDNI_AXIS_ALL ? 2 : axis;
+    const int naxes = ax_hi - ax_lo + 1;
+    Carver c(ws, ws_bytes);
+    LearnedWs w = carve_learned_ws(c, nt, grid->res, naxes, slab_samples);
+    if (!c.fits()) return LDNI_EWORKSPACE;
+    const GridDev g = make_grid(grid);
+    const long long N = (long long)grid->res * grid->res;
+    const int ntiles = (int)((N + kTilePix - 1) / kTilePix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LImg o{};
+    for (int k = 0; k < naxes; ++k) {
+        const int a = ax_lo + k;
+        const ldni_layers_t &L = out[k];
+        if (!L.offsets || L.capacity < 0 || (L.capacity > 0 && (!L.depth || !L.nx || !L.ny || !L.nz || !L.tri_id)))
+            return LDNI_EINVAL;
+        o.count[a] = w.count[k];
+        o.exitc[a] = w.exitc[k];
+        o.offsets[a] = L.offsets;
+        o.depth[a] = L.depth;
+        o.nx[a] = L.nx;
+        o.ny[a] = L.ny;
+        o.nz[a] = L.nz;
+        o.tri[a] = L.tri_id;
+        o.cap[a] = L.capacity;
+        o.feat[a] = w.feat[k];
+        o.kcap[a] = w.kcap[k];
+        o.slab_base[a] = w.slab_base[k];
+        o.over[a] = w.over[k];
+    }
+    o.slab = w.slab;
+    for (int k = 0; k < 3; ++k) o.nrm[k] = w.nrm[k];
+    o.slab_cap = w.slab_cap;
+    o.any_over = w.any_over;
+
+    static bool smem_set = false;
+    const size_t feat_smem = sizeof(float) * 3 * (size_t)kFeatSmemTiles * kRawFeat;
+    if (!smem_set) {
+        if (cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)feat_smem) !=
+            cudaSuccess)
+            return LDNI_ECUDA;
+        smem_set = true;
+    }
+    if (cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    const bool use_smem = ntiles * naxes <= kFeatSmemTiles;
+    const size_t smem = use_smem ? sizeof(float) * 3 * (size_t)ntiles * kRawFeat : 0;
+    if (mlp && nt > 0)
+        LDNI_LAUNCH(K_FEATURES, s,
+                    features_kernel<<<feature_blocks(nt, feature_stride), kThreads, smem, s>>>(
+                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, feature_stride, ntiles, o));
+    const __nv_bfloat16 *W = mlp ? reinterpret_cast<const __nv_bfloat16 *>(mlp->w) : nullptr;
+    const float *B = mlp ? mlp->b : nullptr;
+    const float margin = mlp ? mlp->margin : 0.0f;
+    LDNI_LAUNCH(K_CAPACITY, s,
+                capacity_kernel<<<(ntiles * naxes + kCapWarps - 1) / kCapWarps, kCapWarps * 32, 0, s>>>(
+                    ntiles, N, ax_lo, naxes, o, W, B, margin, fixed_layers));
+    LDNI_LAUNCH(K_LAYOUT, s, layout_kernel<<<1, 1024, 0, s>>>(ntiles, N, ax_lo, naxes, o));
+    if (nt > 0) {
+        LDNI_LAUNCH(K_ONEPASS, s,
+                    onepass_kernel<<<grid_blocks(nt), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
+                                                                        o, w.big_q, w.big_n, info));
+        LDNI_LAUNCH(K_ONEPASS_BIG, s,
+                    onepass_big<<<num_sms() * 2, kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.big_n));
+    }
+    const int *cnt[3];
+    int *off[3];
+    for (int k = 0; k < naxes; ++k) {
+        cnt[k] = w.count[k];
+        off[k] = const_cast<int *>(o.offsets[ax_lo + k]);
+    }
+    int rc = cuda_status();
+    if (rc != LDNI_OK) return rc;
+    rc = csr_scan(cnt, off, naxes, N, w.scan_words, info, ax_lo, s);
+    if (rc != LDNI_OK) return rc;
+    LDNI_LAUNCH(K_REDO, s, verify_kernel<<<dim3(ntiles, naxes), 256, 0, s>>>(ntiles, N, ax_lo, o));
+    if (nt > 0) {
+        LDNI_LAUNCH(K_REDO, s,
+                    redo_kernel<<<num_sms(), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o,
+                                                               info));
+        LDNI_LAUNCH(K_REDO, s,
+                    redo_big<<<num_sms(), kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.big_n, info));
+    }
+    LDNI_LAUNCH(K_GATHER, s,
+                gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info));
+    if (overflow_tiles) LDNI_LAUNCH(K_GATHER, s, count_overflow<<<1, 256, 0, s>>>(ntiles, ax_lo, naxes, o, overflow_tiles));
+    return cuda_status();
+}
+
+extern "C" int ldni_tile_features(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                  const ldni_grid_t *grid, int32_t axis, int32_t feature_stride, float *raw, float *X,
+                                  void *stream) {
+    if (!grid_valid(grid) || axis < 0 || axis > LDNI_AXIS_ALL || nv <= 0 || nt < 0 || (nt > 0 && (!verts || !tris)) ||
+        feature_stride < 1 || !raw || !X)
+        return LDNI_EINVAL;
+    if (nt > (INT_MAX / 4) || nv > INT_MAX) return LDNI_ETOOLARGE;
+    const int ax_lo = axis == LDNI_AXIS_ALL ? 0 : axis, ax_hi = axis == LDNI_AXIS_ALL ? 2 : axis;
+    const int naxes = ax_hi - ax_lo + 1;
+    const long long N = (long long)grid->res * grid->res;
+    const int ntiles = (int)((N + kTilePix - 1) / kTilePix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LImg o{};
+    for (int k = 0; k < naxes; ++k) o.feat[ax_lo + k] = raw + (size_t)k * ntiles * kRawFeat;
+    if (cudaMemsetAsync(raw, 0, sizeof(float) * (size_t)naxes * ntiles * kRawFeat, s) != cudaSuccess) return LDNI_ECUDA;
+    static bool smem_set = false;
+    if (!smem_set) {
+        if (cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(sizeof(float) * 3 * (size_t)kFeatSmemTiles * kRawFeat)) != cudaSuccess)
+            return LDNI_ECUDA;
+        smem_set = true;
+    }
+    const bool use_smem = ntiles * naxes <= kFeatSmemTiles;
+    const size_t smem = use_smem ? sizeof(float) * 3 * (size_t)ntiles * kRawFeat : 0;
+    if (nt > 0)
+        LDNI_LAUNCH(K_FEATURES, s,
+                    features_kernel<<<feature_blocks(nt, feature_stride), kThreads, smem, s>>>(
+                        verts, tris, (int)nt, (int)nv, make_grid(grid), ax_lo, ax_hi, feature_stride, ntiles, o));
+    LDNI_LAUNCH(K_FEATURES, s,
+                normalise_kernel<<<(ntiles * naxes + 127) / 128, 128, 0, s>>>(ntiles, N, naxes, raw, X));
+    return cuda_status();
+}
+
+extern "C" int ldni_tile_labels(const int32_t *offsets, int32_t res, float *label, void *stream) {
+    if (!offsets || !label || res < 1 || res > 8192) return LDNI_EINVAL;
+    const long long N = (long long)res * res;
+    const int ntiles = (int)((N + kTilePix - 1) / kTilePix);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LDNI_LAUNCH(K_FEATURES, s, tile_label_kernel<<<ntiles, 256, 0, s>>>(N, offsets, label));
+    return cuda_status();
+}

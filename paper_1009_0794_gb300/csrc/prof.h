@@ -27,7 +27,16 @@ enum KernelId : int {
     K_VOL_PARTIAL = 11,
     K_VOL_FINAL = 12,
     K_BOOL_FUSED = 13,
-    K_NUM = 14
+    K_FEATURES = 14,
+    K_CAPACITY = 15,
+    K_LAYOUT = 16,
+    K_ONEPASS = 17,
+    K_ONEPASS_BIG = 18,
+    K_REDO = 19,
+    K_GATHER = 20,
+    K_MLP = 21,
+    K_GRAD = 22,
+    K_NUM = 23
 };
 
 struct ProfState {
@@ -50,13 +59,14 @@ inline int prof_begin(int id, cudaStream_t s) {
     if (!P.begin[slot] || !P.end[slot]) return -1;
     P.next++;
     if (P.ids) P.ids[slot] = id;
-    cudaEventRecord(P.begin[slot], s);
+    // External: inside a stream capture the record becomes a graph node that fires on every replay
+    cudaEventRecordWithFlags(P.begin[slot], s, cudaEventRecordExternal);
     return slot;
 }
 
 inline void prof_end(int slot, cudaStream_t s) {
     if (slot < 0) return;
-    cudaEventRecord(prof_state().end[slot], s);
+    cudaEventRecordWithFlags(prof_state().end[slot], s, cudaEventRecordExternal);
 }
 
 }  // namespace ldni

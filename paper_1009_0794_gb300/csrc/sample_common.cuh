@@ -56,6 +56,7 @@ struct Setup32 {
     int b0, b1, b2;
     float inv;  // 1 / area2
     int i0, j0, w, h;  // pixel-centre box: i0 .. i0+w-1, j0 .. j0+h-1
+    int exiting;       // 1 if the face's projection was counter-clockwise (n_a > 0: the ray leaves the solid)
 
     // biased edge functions at pixel (i, j): inside iff all three are > 0
     __device__ __forceinline__ void edges(int i, int j, int &e0, int &e1, int &e2) const {
@@ -105,6 +106,7 @@ struct Setup64 {
     float a0, a1, a2;
     long long b0, b1, b2;
     float inv;
+    int exiting;
     __device__ __forceinline__ void edges(int i, int j, long long &e0, long long &e1, long long &e2) const {
         const long long cu = (long long)i * kSubpix + kHalfSubpix, cv = (long long)j * kSubpix + kHalfSubpix;
         e0 = (u1 - u0) * (cv - v0) - (v1 - v0) * (cu - u0) + b0;
@@ -146,6 +148,7 @@ __device__ __forceinline__ int setup_axis(const TriView &T, int res, Setup32 &S)
     int A2 = (u1 - u0) * (v2 - v0) - (v1 - v0) * (u2 - u0);
     if (A2 == 0) return kNone;  // face parallel to the ray (Definition 1 note)
     float a0 = comp(T.p[0], A), a1 = comp(T.p[1], A), a2 = comp(T.p[2], A);
+    S.exiting = A2 > 0 ? 1 : 0;
     if (A2 < 0) {  // turn counter-clockwise
         int x = u1; u1 = u2; u2 = x;
         x = v1; v1 = v2; v2 = x;
@@ -194,6 +197,7 @@ __device__ __forceinline__ bool setup_big(const TriView &T, int a, int res, Setu
     long long A2 = (u1 - u0) * (v2 - v0) - (v1 - v0) * (u2 - u0);
     if (A2 == 0) return false;
     float a0 = comp(T.p[0], a), a1 = comp(T.p[1], a), a2 = comp(T.p[2], a);
+    S.exiting = A2 > 0 ? 1 : 0;
     if (A2 < 0) {
         long long x = u1; u1 = u2; u2 = x;
         x = v1; v1 = v2; v2 = x;

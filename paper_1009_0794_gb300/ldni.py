@@ -89,6 +89,17 @@ class LDNI:
                 "tri": self.tri[:n].cpu().numpy()}
 
 
+def identical(A: "LDNI", B: "LDNI") -> bool:
+    """Bit-for-bit equality of two LDNIs (offsets and every sample array)."""
+    if A.n != B.n or A.offsets.numel() != B.offsets.numel():
+        return False
+    n = A.n
+    same = torch.equal(A.offsets, B.offsets) and torch.equal(A.tri[:n], B.tri[:n])
+    for x, y in ((A.depth, B.depth), (A.nx, B.nx), (A.ny, B.ny), (A.nz, B.nz)):
+        same = same and torch.equal(x[:n].view(torch.int32), y[:n].view(torch.int32))
+    return bool(same)
+
+
 def _stream_ptr(stream: Optional[torch.cuda.Stream]):
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
@@ -275,3 +286,83 @@ def volume(L: LDNI, stream=None, out: Optional[torch.Tensor] = None, ws: Optiona
     if meta["status"] & _lib.ST_ODD:
         raise _lib.LDNIError(-3, "ldni_volume")
     return float(out.item())
+
+
+# ---- one-pass sampling with learned capacity -------------------------------------
+
+def auto_stride(nt: int, budget: int = 65536) -> int:
+    """Feature subsample stride: about `budget` triangles feed the features."""
+    return max(1, -(-int(nt) // budget))
+
+
+def ntiles(res: int) -> int:
+    return (res * res + _lib.TILE_RAYS - 1) // _lib.TILE_RAYS
+
+
+def sample_learned_workspace_size(nv: int, nt: int, res: int, axis, slab_samples: int) -> int:
+    sz = ctypes.c_size_t(0)
+    cax = _lib.AXIS_ALL if axis in ("all", None, _lib.AXIS_ALL) else int(axis)
+    _lib.check(_lib.load().ldni_sample_learned_workspace_size(int(nv), int(nt), int(res), cax, int(slab_samples),
+                                                              ctypes.byref(sz)), "ldni_sample_learned_workspace_size")
+    return int(sz.value)
+
+
+class LearnedPlan:
+    """Buffers for repeated one-pass sampling of one mesh size (no host
+    synchronisation per call).  `net` is a capacity.CapacityNet or None for
+    fixed `layers` per ray (the baseline without the network)."""
+
+    def __init__(self, nv: int, nt: int, grid: Grid, capacities, slab_samples: int, axis="all", net=None,
+                 layers: int = 2, margin: float = 0.25, feature_stride: Optional[int] = None):
+        self.grid = grid
+        self.axes = _axes(axis)
+        self.cax = _lib.AXIS_ALL if len(self.axes) == 3 else self.axes[0]
+        self.slab = int(slab_samples)
+        self.ws = torch.empty(sample_learned_workspace_size(nv, nt, grid.res, self.cax, self.slab), dtype=torch.uint8,
+                              device="cuda")
+        self.info = new_info()
+        self.n_over = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.outs = [empty_layers(grid, a, int(c)) for a, c in zip(self.axes, capacities)]
+        self._arr = (_CLayers * len(self.axes))(*[o.c() for o in self.outs])
+        self._g = grid.c()
+        self.net, self.layers = net, int(layers)
+        self.stride = int(feature_stride) if feature_stride else auto_stride(nt)
+        self._mlp = net.c(margin) if net is not None else None
+
+    def run(self, verts: torch.Tensor, tris: torch.Tensor, stream=None):
+        lib = _lib.load()
+        mp = ctypes.byref(self._mlp) if self._mlp is not None else None
+        _lib.check(lib.ldni_sample_learned(verts.data_ptr(), verts.shape[0], tris.data_ptr(), tris.shape[0],
+                                           ctypes.byref(self._g), self.cax, mp, self.layers, self.stride, self.slab,
+                                           self._arr, self.info.data_ptr(), self.n_over.data_ptr(),
+                                           self.ws.data_ptr(), self.ws.numel(), _stream_ptr(stream)),
+                   "ldni_sample_learned")
+
+    def finish(self) -> List[LDNI]:
+        meta = info_decode(self.info)
+        _raise_status(meta["status"], "ldni_sample_learned")
+        for o in self.outs:
+            o.n = meta["n"][o.axis]
+        return self.outs
+
+    def overflow_tiles(self) -> int:
+        return int(self.n_over.item())
+
+
+def sample_learned(verts, tris, grid: Grid, axis="all", net=None, layers: int = 2, margin: float = 0.25,
+                   feature_stride: Optional[int] = None, slab_samples: Optional[int] = None,
+                   capacity_hint: Optional[int] = None,
+                   stream=None):
+    """One-traversal sampling (identical output to sample()).  Output arrays
+    are sized by capacity_hint per image (default: 3 * res^2 / 2); a call
+    that needs more raises LDNIError(LDNI_ECAPACITY)."""
+    v = _dev(verts, torch.float32).reshape(-1, 3)
+    t = _dev(tris, torch.int32).reshape(-1, 3)
+    axes = _axes(axis)
+    n_img = len(axes)
+    cap = capacity_hint if capacity_hint is not None else max(16, 3 * grid.res * grid.res // 2)
+    slab = slab_samples if slab_samples is not None else n_img * grid.res * grid.res * 4
+    plan = LearnedPlan(v.shape[0], t.shape[0], grid, [cap] * n_img, slab, axis, net, layers, margin, feature_stride)
+    plan.run(v, t, stream)
+    outs = plan.finish()
+    return outs if n_img > 1 else outs[0]
