@@ -301,6 +301,34 @@ int ldni_volume_workspace_size(int32_t res, size_t *bytes_host);
 int ldni_volume(const ldni_layers_t *L, const ldni_grid_t *grid, double *vol, ldni_info_t *info, void *ws,
                 size_t ws_bytes, void *stream);
 
+/* ---- adjoint of depth and volume ---------------------------------------- */
+
+/*
+ * Vector-Jacobian product of the sample depths of one LDNI with respect to
+ * the mesh vertices.  A sample of ray (u, v) on triangle t lies on t's plane,
+ * d = sum_k lambda_k a_k (lambda: barycentrics of (u, v) in t's unsnapped
+ * projection), so d(d)/d(V_j) = lambda_j n / n_a with n t's face normal.  The
+ * set of crossings is held fixed (no boundary terms).
+ *   L          : an LDNI sampled from exactly this mesh (tri_id = triangle),
+ *                image `axis` of `grid`.
+ *   grad_depth : device float[L.capacity], dLoss/d(depth) per sample.
+ *   grad_verts : device float[nv][3], ACCUMULATED into (FP32 atomics).
+ */
+int ldni_depth_vjp(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                   int32_t axis, const ldni_layers_t *L, const float *grad_depth, float *grad_verts, ldni_info_t *info,
+                   void *stream);
+
+/*
+ * Gradient of the LDNI volume h^2 sum_rays sum_k (d_{2k+1} - d_{2k}) (the
+ * odd-to-even ranges are inside, Section 2 after Proposition 1) with respect
+ * to the vertices, scaled by grad_volume (host) and ACCUMULATED into
+ * grad_verts (device float[nv][3]).  Same fixed-crossing-set reading as
+ * ldni_depth_vjp.
+ */
+int ldni_volume_grad(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                     int32_t axis, const ldni_layers_t *L, double grad_volume, float *grad_verts, ldni_info_t *info,
+                     void *stream);
+
 /* ---- instrumentation (no counterpart in the paper) ------------------- */
 
 /* Number of kernels this process has launched through the library. */

@@ -80,6 +80,8 @@ SIGNATURES = {
     "ldni_mlp_train_workspace_size": (ctypes.c_int, [_I64, ctypes.POINTER(_SZ)]),
     "ldni_mlp_train_step": (ctypes.c_int, [_P, _P, _P, _P, _P, _P, _P, _I64, ctypes.c_float, _I32, ctypes.c_float,
                                            _P, _P, _P, _SZ, _P]),
+    "ldni_depth_vjp": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _P, _P]),
+    "ldni_volume_grad": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, ctypes.c_double, _P, _P, _P]),
     "ldni_launch_count": (ctypes.c_uint64, []),
     "ldni_profile_set": (ctypes.c_int, [_P, _P, _P, _I32, _I32]),
     "ldni_profile_recorded": (ctypes.c_int64, []),

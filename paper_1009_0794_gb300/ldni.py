@@ -366,3 +366,39 @@ def sample_learned(verts, tris, grid: Grid, axis="all", net=None, layers: int = 
     plan.run(v, t, stream)
     outs = plan.finish()
     return outs if n_img > 1 else outs[0]
+
+
+# ---- adjoint -------------------------------------------------------------------
+
+def depth_vjp(verts: torch.Tensor, tris: torch.Tensor, L: LDNI, grad_depth: torch.Tensor,
+              grad_verts: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """grad_verts += (d depth / d verts)^T grad_depth for the samples of L
+    (fixed crossing set; d(d)/d(V_j) = lambda_j n / n_a)."""
+    v = verts.contiguous()
+    t = tris.contiguous()
+    if grad_verts is None:
+        grad_verts = torch.zeros(v.shape[0], 3, dtype=torch.float32, device="cuda")
+    gd = grad_depth.contiguous().to(torch.float32)
+    if gd.numel() < L.capacity:
+        gd = torch.cat([gd, torch.zeros(L.capacity - gd.numel(), dtype=torch.float32, device="cuda")])
+    info = new_info()
+    lc, g = L.c(), L.grid.c()
+    _lib.check(_lib.load().ldni_depth_vjp(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), L.axis,
+                                          ctypes.byref(lc), gd.data_ptr(), grad_verts.data_ptr(), info.data_ptr(),
+                                          _stream_ptr(stream)), "ldni_depth_vjp")
+    return grad_verts
+
+
+def volume_grad(verts: torch.Tensor, tris: torch.Tensor, L: LDNI, grad_volume: float = 1.0,
+                grad_verts: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """grad_verts += grad_volume * d(volume of L)/d(verts), fixed crossing set."""
+    v = verts.contiguous()
+    t = tris.contiguous()
+    if grad_verts is None:
+        grad_verts = torch.zeros(v.shape[0], 3, dtype=torch.float32, device="cuda")
+    info = new_info()
+    lc, g = L.c(), L.grid.c()
+    _lib.check(_lib.load().ldni_volume_grad(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g),
+                                            L.axis, ctypes.byref(lc), float(grad_volume), grad_verts.data_ptr(),
+                                            info.data_ptr(), _stream_ptr(stream)), "ldni_volume_grad")
+    return grad_verts
