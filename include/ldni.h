@@ -139,6 +139,19 @@ int ldni_version(void);
  * paper uses a working envelope slightly larger than the model, Section 3). */
 int ldni_grid_from_bbox(const float *bbox_host, int32_t res, ldni_grid_t *grid_host);
 
+/* One mesh of a batch (ldni_sample_batch): its three images x, y, z on its
+ * own grid.  The array of items lives in DEVICE memory for the kernels; the
+ * same values are passed as a host copy for validation and sizing. */
+typedef struct {
+    const float *verts;   /* device float[nv][3] */
+    const int32_t *tris;  /* device int32[nt][3] */
+    int64_t nv;
+    int64_t nt;
+    ldni_grid_t grid;
+    int32_t pad_;         /* keeps out[] 8-byte aligned */
+    ldni_layers_t out[3]; /* device buffers of the three images */
+} ldni_batch_item_t;
+
 /* ---- sampling (Section 3; Definitions 1-4; Remark 1) ---------------- */
 
 /* Bytes of device workspace ldni_sample / ldni_sample_count need for a mesh
@@ -181,6 +194,28 @@ int ldni_sample_count(const float *verts, int64_t nv, const int32_t *tris, int64
 int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
                      int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                      void *stream);
+
+/* ---- batches ------------------------------------------------------------ */
+
+/* Workspace bytes for ldni_sample_batch over items_host[count]. */
+int ldni_sample_batch_workspace_size(const ldni_batch_item_t *items_host, int32_t count, size_t *bytes_host);
+
+/*
+ * ldni_sample (exact two-pass, all three images) for `count` meshes of any
+ * sizes and resolutions with one launch per stage for the whole batch:
+ * count, big-triangle count, scan, fill, big-triangle fill, per-ray sort.
+ * Paper's use: repeated solid modelling operations work on LDNIs of many
+ * solids on one grid (Section 1; Section 4.1.1 chains; Section 4.2 sphere
+ * unions).  items_dev: device array of count items (read by the kernels);
+ * items_host: the same items on the host (validation, workspace carving).
+ * infos: device ldni_info_t[count], one per item (n[a] per image); cleared
+ * by the call itself, so replays of a captured call start from zero.  The
+ * output is bit-identical to sampling each item alone.  Makes no host
+ * synchronisation, so a call can be captured in a CUDA graph as long as the
+ * item array and workspace outlive the graph.
+ */
+int ldni_sample_batch(const ldni_batch_item_t *items_dev, const ldni_batch_item_t *items_host, int32_t count,
+                      ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream);
 
 /* ---- one-pass sampling with learned capacity ------------------------------ */
 
@@ -352,7 +387,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * two passes of ldni_boolean_static), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint). */
+ * 21 mlp, 22 adjoint, 23 batch). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

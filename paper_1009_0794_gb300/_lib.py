@@ -41,6 +41,11 @@ class Layers(ctypes.Structure):
                 ("capacity", ctypes.c_int64)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("nv", ctypes.c_int64),
+                ("nt", ctypes.c_int64), ("grid", Grid), ("pad_", ctypes.c_int32), ("out", Layers * 3)]
+
+
 INFO_BYTES = 32  # ldni_info_t: int64 n[3]; uint32 status; uint32 odd_rays
 
 
@@ -82,6 +87,8 @@ SIGNATURES = {
                                            _P, _P, _P, _SZ, _P]),
     "ldni_depth_vjp": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _P, _P]),
     "ldni_volume_grad": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, ctypes.c_double, _P, _P, _P]),
+    "ldni_sample_batch_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_SZ)]),
+    "ldni_sample_batch": (ctypes.c_int, [_P, _P, _I32, _P, _P, _SZ, _P]),
     "ldni_launch_count": (ctypes.c_uint64, []),
     "ldni_profile_set": (ctypes.c_int, [_P, _P, _P, _I32, _I32]),
     "ldni_profile_recorded": (ctypes.c_int64, []),

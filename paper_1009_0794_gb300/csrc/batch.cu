@@ -1,0 +1,335 @@
+// Many meshes, of uneven size and resolution, sampled by ONE launch per stage
+// (count, scan, fill, sort) for the whole batch - the exact two-pass form of
+// sample.cu spread over every triangle, chunk and ray of the batch at once.
+// Each thread finds its mesh by a binary search over prefix tables that a
+// setup kernel builds on the device from the caller's device array of item
+// descriptors, so a batch call needs no host synchronisation and can be
+// captured in a CUDA graph.
+#include "lookback.cuh"
+#include "sample_common.cuh"
+
+namespace ldni {
+namespace {
+
+constexpr int kThreads = 256;
+
+struct Tables {
+    long long *tri_prefix;    // [count + 1]
+    long long *ray_prefix;    // [3 count + 1]  rays of image (m, a) at 3 m + a
+    long long *chunk_prefix;  // [3 count + 1]  scan chunks
+    long long *count_base;    // [3 count]      start of the image's counts
+    long long *big;           // queued big (item, triangle, image): item << 34 | tri << 2 | a
+    int *big_n;
+};
+
+__device__ __forceinline__ int find(const long long *prefix, int n, long long x) {  // prefix[k] <= x < prefix[k+1]
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (prefix[mid] <= x)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ GridDev grid_dev(const ldni_grid_t &g) {
+    GridDev d;
+    d.o[0] = g.origin[0];
+    d.o[1] = g.origin[1];
+    d.o[2] = g.origin[2];
+    d.s = (float)((double)g.res * (double)kSubpix / (double)g.width);  // as the host computes it
+    d.res = g.res;
+    return d;
+}
+
+// one block: prefix tables of the batch
+__global__ void setup_kernel(const ldni_batch_item_t *items, int count, Tables T) {
+    if (threadIdx.x != 0) return;
+    long long tri = 0, ray = 0, chunk = 0, cbase = 0;
+    for (int m = 0; m < count; ++m) {
+        T.tri_prefix[m] = tri;
+        tri += items[m].nt;
+        const long long N = (long long)items[m].grid.res * items[m].grid.res;
+        for (int a = 0; a < 3; ++a) {
+            T.ray_prefix[3 * m + a] = ray;
+            T.chunk_prefix[3 * m + a] = chunk;
+            T.count_base[3 * m + a] = cbase;
+            ray += N;
+            chunk += (N + kScanChunk - 1) / kScanChunk;
+            cbase += (N + 63) / 64 * 64;
+        }
+    }
+    T.tri_prefix[count] = tri;
+    T.ray_prefix[3 * count] = ray;
+    T.chunk_prefix[3 * count] = chunk;
+}
+
+template <bool kFill>
+__device__ __forceinline__ void batch_emit(const ldni_batch_item_t &it, int a, long long p, float d, int t,
+                                           const float3 &n, int *cnt, ldni_info_t *info) {
+    if (!kFill) {
+        atomicAdd(cnt + p, 1);
+        return;
+    }
+    const ldni_layers_t &L = it.out[a];
+    const int k = atomicSub(cnt + p, 1) - 1;
+    const long long slot = (long long)L.offsets[p] + k;
+    if (k < 0 || slot >= L.capacity) {
+        set_status(info, LDNI_ST_CAPACITY);
+        return;
+    }
+    L.depth[slot] = d;
+    L.tri_id[slot] = t;
+    L.nx[slot] = n.x;
+    L.ny[slot] = n.y;
+    L.nz[slot] = n.z;
+}
+
+template <bool kFill, int A>
+__device__ __forceinline__ void batch_axis(const ldni_batch_item_t &it, int m, const TriView &Tv, int t,
+                                           const float3 &n, int res, int *counts, const Tables &T, ldni_info_t *info) {
+    Setup32 S;
+    const int kind = setup_axis<A, kFill>(Tv, res, S);
+    if (kind == kNone) return;
+    if (kind == kBig) {
+        if (!kFill) T.big[atomicAdd(T.big_n, 1)] = ((long long)m << 34) | ((long long)t << 2) | A;
+        return;
+    }
+    int *cnt = counts + T.count_base[3 * m + A];
+    if (!kFill) {
+        S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(cnt + (long long)j * res + i, 1); });
+        return;
+    }
+    const unsigned long long msk = hit_mask(S);
+    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
+    for (int y = 0; y < S.h; ++y) {
+        unsigned long long r = (msk >> (y * S.w)) & row_mask;
+        while (r) {
+            const int x = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            const int i = S.i0 + x, j = S.j0 + y;
+            batch_emit<true>(it, A, (long long)j * res + i, S.depth(i, j), t, n, cnt, info);
+        }
+    }
+}
+
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) batch_tri_pass(const ldni_batch_item_t *items, int count, Tables T,
+                                                           int *counts, ldni_info_t *infos) {
+    const long long total = T.tri_prefix[count];
+    for (long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x; gt < total;
+         gt += (long long)gridDim.x * blockDim.x) {
+        const int m = find(T.tri_prefix, count, gt);
+        const ldni_batch_item_t &it = items[m];
+        const int t = (int)(gt - T.tri_prefix[m]);
+        const GridDev g = grid_dev(it.grid);
+        TriView Tv;
+        const unsigned bad = load_tri(it.verts, it.tris, t, (int)it.nv, g, Tv);
+        if (bad) {
+            if (!kFill) set_status(infos + m, bad);
+            continue;
+        }
+        float3 n = make_float3(0.f, 0.f, 0.f);
+        if (kFill) face_normal(Tv.p[0], Tv.p[1], Tv.p[2], n.x, n.y, n.z);
+        batch_axis<kFill, 0>(it, m, Tv, t, n, g.res, counts, T, infos + m);
+        batch_axis<kFill, 1>(it, m, Tv, t, n, g.res, counts, T, infos + m);
+        batch_axis<kFill, 2>(it, m, Tv, t, n, g.res, counts, T, infos + m);
+    }
+}
+
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) batch_big(const ldni_batch_item_t *items, Tables T, int *counts,
+                                                      ldni_info_t *infos) {
+    const int nq = *T.big_n;
+    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
+        const long long code = T.big[e];
+        const int m = (int)(code >> 34), t = (int)((code >> 2) & 0xFFFFFFFF), a = (int)(code & 3);
+        const ldni_batch_item_t &it = items[m];
+        const GridDev g = grid_dev(it.grid);
+        TriView Tv;
+        if (load_tri(it.verts, it.tris, t, (int)it.nv, g, Tv)) continue;
+        Setup64 S;
+        int i0, i1, j0, j1;
+        if (!setup_big(Tv, a, g.res, S, i0, i1, j0, j1)) continue;
+        float3 n = make_float3(0.f, 0.f, 0.f);
+        if (kFill) face_normal(Tv.p[0], Tv.p[1], Tv.p[2], n.x, n.y, n.z);
+        int *cnt = counts + T.count_base[3 * m + a];
+        const int w = i1 - i0 + 1;
+        const long long npx = (long long)w * (j1 - j0 + 1);
+        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+            const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
+            if (S.inside(i, j))
+                batch_emit<kFill>(it, a, (long long)j * g.res + i, kFill ? S.depth(i, j) : 0.0f, t, n, cnt, infos + m);
+        }
+    }
+}
+
+// Scan of every image's counts: chunks of all images in one launch; the
+// look-back of a chunk stops at the first chunk of its own image.
+__global__ void __launch_bounds__(kThreads) batch_scan(const ldni_batch_item_t *items, int count, Tables T,
+                                                       const int *counts, unsigned long long *words,
+                                                       ldni_info_t *infos) {
+    __shared__ long long sh[kThreads / 32 + 1];
+    __shared__ long long s_chunk, s_base;
+    const long long nchunks = T.chunk_prefix[3 * count];
+    if (threadIdx.x == 0) s_chunk = (long long)atomicAdd(words + nchunks, 1ull);
+    __syncthreads();
+    const long long c = s_chunk;
+    const int img = find(T.chunk_prefix, 3 * count, c);
+    const int m = img / 3, a = img % 3;
+    const long long local = c - T.chunk_prefix[img];
+    const long long N = (long long)items[m].grid.res * items[m].grid.res;
+    const int *cnt = counts + T.count_base[img];
+    int *out = items[m].out[a].offsets;
+    const long long base = local * kScanChunk;
+    constexpr int kPer = kScanChunk / kThreads;  // 16 counts per thread
+    int v[kPer];
+    long long mine = 0;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const long long e = base + (long long)threadIdx.x * kPer + k;
+        v[k] = e < N ? cnt[e] : 0;
+        mine += v[k];
+    }
+    long long total;
+    const long long excl = block_exclusive_scan<kThreads>(mine, sh, &total);
+    if (threadIdx.x < 32) {
+        // image-local status words: chunk 0 of the image starts at prefix 0
+        const long long b = lookback_warp(words + T.chunk_prefix[img], (int)local, total, infos + m);
+        if (threadIdx.x == 0) s_base = b;
+    }
+    __syncthreads();
+    long long run = s_base + excl;
+#pragma unroll
+    for (int k = 0; k < kPer; ++k) {
+        const long long e = base + (long long)threadIdx.x * kPer + k;
+        if (e < N) out[e] = (int)min(run, (long long)INT_MAX);
+        run += v[k];
+    }
+    if (local == T.chunk_prefix[img + 1] - T.chunk_prefix[img] - 1 && threadIdx.x == 0) {
+        const long long n_img = s_base + total;
+        out[N] = (int)min(n_img, (long long)INT_MAX);
+        infos[m].n[a] = n_img;
+        if (n_img > INT_MAX) set_status(infos + m, LDNI_ST_TOOLARGE);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) batch_sort(const ldni_batch_item_t *items, int count, Tables T,
+                                                       ldni_info_t *infos) {
+    const long long total = T.ray_prefix[3 * count];
+    for (long long gr = blockIdx.x * (long long)blockDim.x + threadIdx.x; gr < total;
+         gr += (long long)gridDim.x * blockDim.x) {
+        const int img = find(T.ray_prefix, 3 * count, gr);
+        const int m = img / 3, a = img % 3;
+        const long long p = gr - T.ray_prefix[img];
+        const ldni_layers_t &L = items[m].out[a];
+        const long long b = L.offsets[p];
+        long long e = L.offsets[p + 1];
+        if ((e - b) & 1) {
+            atomicAdd(&infos[m].odd_rays, 1u);
+            set_status(infos + m, LDNI_ST_ODD);
+        }
+        if (e > L.capacity) e = L.capacity;
+        if (e - b >= 2) sort_ray_global(b, e, L.depth, L.tri_id, L.nx, L.ny, L.nz);
+    }
+}
+
+struct BatchWs {
+    Tables T;
+    int *counts;
+    size_t counts_bytes;  // counts and big_n are cleared by one memset
+    unsigned long long *words;
+    size_t words_bytes;
+};
+
+BatchWs carve_batch(Carver &c, const ldni_batch_item_t *items_host, int count) {
+    BatchWs w{};
+    long long cints = 0, chunks = 0, tris = 0;
+    for (int m = 0; m < count; ++m) {
+        const long long N = (long long)items_host[m].grid.res * items_host[m].grid.res;
+        cints += 3 * ((N + 63) / 64 * 64);
+        chunks += 3 * ((N + kScanChunk - 1) / kScanChunk);
+        tris += items_host[m].nt;
+    }
+    w.counts = c.take<int>((size_t)cints + 64);
+    w.T.big_n = w.counts ? w.counts + cints : nullptr;
+    w.counts_bytes = sizeof(int) * ((size_t)cints + 64);
+    w.words = c.take<unsigned long long>((size_t)chunks + 1);
+    w.words_bytes = sizeof(unsigned long long) * ((size_t)chunks + 1);
+    w.T.tri_prefix = c.take<long long>((size_t)count + 1);
+    w.T.ray_prefix = c.take<long long>(3 * (size_t)count + 1);
+    w.T.chunk_prefix = c.take<long long>(3 * (size_t)count + 1);
+    w.T.count_base = c.take<long long>(3 * (size_t)count);
+    w.T.big = c.take<long long>((size_t)(3 * tris > 0 ? 3 * tris : 1));
+    return w;
+}
+
+bool items_ok(const ldni_batch_item_t *items, int count) {
+    for (int m = 0; m < count; ++m) {
+        const ldni_batch_item_t &it = items[m];
+        if (!grid_valid(&it.grid) || it.nv <= 0 || it.nt < 0 || (it.nt > 0 && (!it.verts || !it.tris)) ||
+            it.nt > (1ll << 31) - 1 || it.nv > INT_MAX)
+            return false;
+        for (int a = 0; a < 3; ++a) {
+            const ldni_layers_t &L = it.out[a];
+            if (!L.offsets || L.capacity < 0 || (L.capacity > 0 && (!L.depth || !L.nx || !L.ny || !L.nz || !L.tri_id)))
+                return false;
+        }
+    }
+    return count < (1 << 29);
+}
+
+int blocks_for(long long work) {
+    long long b = (work + kThreads - 1) / kThreads;
+    const long long lim = (long long)num_sms() * 16;
+    return (int)(b < 1 ? 1 : (b > lim ? lim : b));
+}
+
+}  // namespace
+}  // namespace ldni
+
+using namespace ldni;
+
+extern "C" int ldni_sample_batch_workspace_size(const ldni_batch_item_t *items_host, int32_t count, size_t *bytes) {
+    if (!items_host || count < 1 || !bytes || !items_ok(items_host, count)) return LDNI_EINVAL;
+    Carver c(nullptr, 0);
+    carve_batch(c, items_host, count);
+    *bytes = align_up(c.off);
+    return LDNI_OK;
+}
+
+extern "C" int ldni_sample_batch(const ldni_batch_item_t *items_dev, const ldni_batch_item_t *items_host,
+                                 int32_t count, ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
+    if (!items_dev || !items_host || count < 1 || !infos || !ws || !items_ok(items_host, count)) return LDNI_EINVAL;
+    Carver c(ws, ws_bytes);
+    BatchWs w = carve_batch(c, items_host, count);
+    if (!c.fits()) return LDNI_EWORKSPACE;
+    long long tris = 0, rays = 0, chunks = 0;
+    for (int m = 0; m < count; ++m) {
+        const long long N = (long long)items_host[m].grid.res * items_host[m].grid.res;
+        tris += items_host[m].nt;
+        rays += 3 * N;
+        chunks += 3 * ((N + kScanChunk - 1) / kScanChunk);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(w.counts, 0, w.counts_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    if (cudaMemsetAsync(w.words, 0, w.words_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    if (cudaMemsetAsync(infos, 0, sizeof(ldni_info_t) * (size_t)count, s) != cudaSuccess) return LDNI_ECUDA;
+    LDNI_LAUNCH(K_BATCH, s, setup_kernel<<<1, 32, 0, s>>>(items_dev, count, w.T));
+    if (tris > 0) {
+        LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<false><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,
+                                                                                             w.counts, infos));
+        LDNI_LAUNCH(K_BATCH, s, batch_big<false><<<num_sms() * 2, kThreads, 0, s>>>(items_dev, w.T, w.counts, infos));
+    }
+    LDNI_LAUNCH(K_BATCH, s,
+                batch_scan<<<(unsigned)chunks, kThreads, 0, s>>>(items_dev, count, w.T, w.counts, w.words, infos));
+    if (tris > 0) {
+        LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<true><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,
+                                                                                            w.counts, infos));
+        LDNI_LAUNCH(K_BATCH, s, batch_big<true><<<num_sms() * 2, kThreads, 0, s>>>(items_dev, w.T, w.counts, infos));
+    }
+    LDNI_LAUNCH(K_BATCH, s, batch_sort<<<blocks_for(rays), kThreads, 0, s>>>(items_dev, count, w.T, infos));
+    return cuda_status();
+}

@@ -36,7 +36,8 @@ enum KernelId : int {
     K_GATHER = 20,
     K_MLP = 21,
     K_GRAD = 22,
-    K_NUM = 23
+    K_BATCH = 23,
+    K_NUM = 24
 };
 
 struct ProfState {

@@ -402,3 +402,83 @@ def volume_grad(verts: torch.Tensor, tris: torch.Tensor, L: LDNI, grad_volume: f
                                             L.axis, ctypes.byref(lc), float(grad_volume), grad_verts.data_ptr(),
                                             info.data_ptr(), _stream_ptr(stream)), "ldni_volume_grad")
     return grad_verts
+
+
+# ---- batches ---------------------------------------------------------------------
+
+class BatchPlan:
+    """Sampling of many meshes (each on its own grid, three images each) by
+    one launch per stage for the whole batch (ldni_sample_batch).  Buffers
+    are sized from one exact per-mesh count (or given capacities); run() makes
+    no host synchronisation and can be captured in a CUDA graph."""
+
+    def __init__(self, meshes, grids: Sequence[Grid], capacities=None):
+        lib = _lib.load()
+        self.meshes = [(_dev(v, torch.float32).reshape(-1, 3), _dev(t, torch.int32).reshape(-1, 3)) for v, t in meshes]
+        self.grids = list(grids)
+        if capacities is None:
+            capacities = []
+            for (v, t), g in zip(self.meshes, self.grids):
+                capacities.append([L.n for L in sample(v, t, g, "all")])
+        self.outs = [[empty_layers(g, a, int(c[a])) for a in range(3)] for g, c in zip(self.grids, capacities)]
+        count = len(self.meshes)
+        items = (_lib.BatchItem * count)()
+        for m, ((v, t), g) in enumerate(zip(self.meshes, self.grids)):
+            it = items[m]
+            it.verts, it.tris, it.nv, it.nt = v.data_ptr(), t.data_ptr(), v.shape[0], t.shape[0]
+            it.grid = g.c()
+            for a in range(3):
+                it.out[a] = self.outs[m][a].c()
+        self._items_host = items
+        raw = bytes(memoryview(items))
+        self._items_dev = torch.frombuffer(bytearray(raw), dtype=torch.uint8).cuda()
+        sz = ctypes.c_size_t(0)
+        _lib.check(lib.ldni_sample_batch_workspace_size(ctypes.byref(items), count, ctypes.byref(sz)),
+                   "ldni_sample_batch_workspace_size")
+        self.ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+        self.infos = torch.zeros(count, _lib.INFO_BYTES // 8, dtype=torch.int64, device="cuda")
+        self.count = count
+
+    def run(self, stream=None):
+        _lib.check(_lib.load().ldni_sample_batch(self._items_dev.data_ptr(), ctypes.byref(self._items_host),
+                                                 self.count, self.infos.data_ptr(), self.ws.data_ptr(),
+                                                 self.ws.numel(), _stream_ptr(stream)), "ldni_sample_batch")
+
+    def finish(self) -> List[List[LDNI]]:
+        h = self.infos.cpu().numpy()
+        for m in range(self.count):
+            st = int(h[m, 3]) & 0xFFFFFFFF
+            _raise_status(st, f"ldni_sample_batch item {m}")
+            for a in range(3):
+                self.outs[m][a].n = int(h[m, a])
+        return self.outs
+
+
+def union_chain(parts: Sequence[LDNI], eps: float = 0.0, capacity: Optional[int] = None):
+    """acc = parts[0] u parts[1] u ... in order (Section 4.1 unions, the
+    repeated operation of Minkowski sums and sweeps, Section 4.2), all on one
+    grid.  Returns (run, result): run() enqueues the whole chain without host
+    synchronisation (capturable in a CUDA graph); result is the final LDNI
+    once run() has completed (its .n is set by finish())."""
+    grid, axis = parts[0].grid, parts[0].axis
+    cap = capacity if capacity is not None else int(sum(p.capacity for p in parts))
+    bufs = [empty_layers(grid, axis, cap), empty_layers(grid, axis, cap)]
+    ws = torch.empty(boolean_workspace_size(grid.res), dtype=torch.uint8, device="cuda")
+    info = new_info()
+
+    def run(stream=None):
+        cur = parts[0]
+        for k in range(1, len(parts)):
+            out = bufs[k % 2]
+            boolean(cur, parts[k], "union", eps=eps, stream=stream, out=out, ws=ws, info=info, sync=False)
+            cur = out
+
+    final = bufs[(len(parts) - 1) % 2] if len(parts) > 1 else parts[0]
+
+    def finish():
+        meta = info_decode(info)
+        _raise_status(meta["status"], "union_chain")
+        final.n = meta["n"][0] if len(parts) > 1 else parts[0].n
+        return final
+
+    return run, finish
