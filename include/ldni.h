@@ -195,6 +195,28 @@ int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *tris, int64_
                      int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                      void *stream);
 
+/* ---- launch tuning ---------------------------------------------------- */
+
+/* Launch-shape knobs.  They change speed only, never a result: every setting
+ * produces the same bits.  The values are process-wide host state, read when
+ * a call launches its kernels (a captured CUDA graph keeps the shapes it was
+ * captured with).  Setting them while another thread is launching is a race
+ * on the host. */
+typedef struct {
+    int32_t bool_tile_rays;      /* rays per Boolean block: 256, 512, 1024 or 2048 */
+    int32_t bool_stage_samples;  /* samples of a Boolean tile staged in shared memory,
+                                    0 (merge from global memory) .. 16384 */
+    int32_t tri_blocks_per_sm;   /* grid of the per-triangle sampling passes, 1 .. 64 */
+    int32_t bool_split;          /* Boolean as one launch (0), as count / tile scan / write
+                                    launches (1), or chosen by image size (-1) */
+} ldni_tuning_t;
+
+/* Current knobs (defaults: 1024, 4096, 16, -1). */
+int ldni_get_tuning(ldni_tuning_t *tuning_host);
+/* Replace the knobs; LDNI_EINVAL (and no change) when a value is out of range.
+ * NULL restores the defaults. */
+int ldni_set_tuning(const ldni_tuning_t *tuning_host);
+
 /* ---- batches ------------------------------------------------------------ */
 
 /* Workspace bytes for ldni_sample_batch over items_host[count]. */

@@ -41,6 +41,11 @@ class Layers(ctypes.Structure):
                 ("capacity", ctypes.c_int64)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("bool_tile_rays", ctypes.c_int32), ("bool_stage_samples", ctypes.c_int32),
+                ("tri_blocks_per_sm", ctypes.c_int32), ("bool_split", ctypes.c_int32)]
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("verts", ctypes.c_void_p), ("tris", ctypes.c_void_p), ("nv", ctypes.c_int64),
                 ("nt", ctypes.c_int64), ("grid", Grid), ("pad_", ctypes.c_int32), ("out", Layers * 3)]
@@ -87,6 +92,8 @@ SIGNATURES = {
                                            _P, _P, _P, _SZ, _P]),
     "ldni_depth_vjp": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _P, _P]),
     "ldni_volume_grad": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, ctypes.c_double, _P, _P, _P]),
+    "ldni_get_tuning": (ctypes.c_int, [_P]),
+    "ldni_set_tuning": (ctypes.c_int, [_P]),
     "ldni_sample_batch_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_SZ)]),
     "ldni_sample_batch": (ctypes.c_int, [_P, _P, _I32, _P, _P, _SZ, _P]),
     "ldni_launch_count": (ctypes.c_uint64, []),

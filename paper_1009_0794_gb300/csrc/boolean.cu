@@ -12,7 +12,13 @@
 // exit is known, so an interval thinner than eps is dropped without a second
 // pass over the output.
 //
-// Two passes: count (one output count per ray), scan to CSR offsets, write.
+// Three forms share that merge:
+//   - one launch per image (bool_tiled): a block counts its tile of rays,
+//     scans, finds its first output slot by decoupled look-back and writes;
+//   - three launches per image (bool_count, bool_scan_tiles, bool_write):
+//     no block ever waits for another;
+//   - the two-pass form behind ldni_boolean_static (bool_pass + csr_scan).
+// Launch shapes are chosen by the tuning knobs (ldni_set_tuning).
 #include <climits>
 #include <mutex>
 
@@ -23,6 +29,7 @@ namespace ldni {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kBoolThreads = 256;
 
 struct Side {
     long long cap;  // samples beyond capacity are never read
@@ -44,36 +51,137 @@ struct Out {
     long long cap;
 };
 
-__device__ __forceinline__ bool op_apply(int op, bool a, bool b) {
-    return op == LDNI_OP_UNION ? (a || b) : (op == LDNI_OP_INTER ? (a && b) : (a && !b));
+// Truth table of an operation: bit (2 inA + inB) = op(inA, inB).
+__device__ __forceinline__ unsigned op_table(int op) {
+    return op == LDNI_OP_UNION ? 0xEu : (op == LDNI_OP_INTER ? 0x8u : 0x4u);
 }
 
-struct Pick {
-    bool from_b;
-    long long idx;
-    float d;
+// The merge of one ray over index ranges [a, ae) of dA and [b, be) of dB.
+// Every sample is read once.  emit(pend_from_b, pend_idx, cur_from_b,
+// cur_idx, m) is called for every kept interval (entering sample, leaving
+// sample) with m = samples so far.  A depth that equals nothing, itself
+// included (NaN, outside the method's inputs), is consumed on its own so the
+// walk always ends.
+template <class Idx, class PA, class PB, class EmitF>
+__device__ __forceinline__ int merge_core(PA dA, Idx a, Idx ae, PB dB, Idx b, Idx be, int op, float eps,
+                                          EmitF emit) {
+    const unsigned table = op_table(op);
+    unsigned state = 0;  // bit 1: inside A, bit 0: inside B
+    bool out = false;
+    bool pend_b = false;
+    Idx pend_i = 0;
+    float pend_d = 0.0f;
+    int m = 0;
+    float da = a < ae ? dA[a] : 0.0f;
+    float db = b < be ? dB[b] : 0.0f;
+    while (a < ae || b < be) {
+        const bool takeA = a < ae && (b >= be || !(db < da));
+        const float d = takeA ? da : db;
+        const Idx fa = a, fb = b;
+        while (a < ae && da == d) {
+            ++a;
+            da = a < ae ? dA[a] : 0.0f;
+        }
+        while (b < be && db == d) {
+            ++b;
+            db = b < be ? dB[b] : 0.0f;
+        }
+        if (a == fa && b == fb) {  // NaN guard
+            if (takeA) {
+                ++a;
+                da = a < ae ? dA[a] : 0.0f;
+            } else {
+                ++b;
+                db = b < be ? dB[b] : 0.0f;
+            }
+        }
+        const bool flipA = ((a - fa) & 1) != 0;
+        state ^= (flipA ? 2u : 0u) | (((b - fb) & 1) ? 1u : 0u);
+        const bool now = (table >> state) & 1u;
+        if (now == out) continue;
+        out = now;
+        const bool cur_b = !flipA;
+        const Idx cur_i = flipA ? fa : fb;
+        if (now) {
+            pend_b = cur_b;
+            pend_i = cur_i;
+            pend_d = d;
+        } else if (!(__fsub_rn(d, pend_d) < eps)) {
+            emit(pend_b, pend_i, cur_b, cur_i, m);
+            m += 2;
+        }
+    }
+    return m;
+}
+
+struct NoEmit {
+    template <class Idx>
+    __device__ __forceinline__ void operator()(bool, Idx, bool, Idx, int) const {}
 };
 
-__device__ __forceinline__ void emit(const Pick &s, const Side &A, const Side &B, int op, const Out &o,
-                                     long long at, ldni_info_t *info) {
+// One output sample at slot `at` from sample idx of A or B.
+__device__ __forceinline__ void emit_global(bool from_b, long long idx, const Side &A, const Side &B, int op,
+                                            const Out &o, long long at, ldni_info_t *info) {
     if (at >= o.cap) {
         set_status(info, LDNI_ST_CAPACITY);
         return;
     }
-    o.d[at] = s.d;
-    if (!s.from_b) {
-        o.nx[at] = A.nx[s.idx];
-        o.ny[at] = A.ny[s.idx];
-        o.nz[at] = A.nz[s.idx];
-        o.tri[at] = A.tri[s.idx];
+    if (!from_b) {
+        o.d[at] = A.d[idx];
+        o.nx[at] = A.nx[idx];
+        o.ny[at] = A.ny[idx];
+        o.nz[at] = A.nz[idx];
+        o.tri[at] = A.tri[idx];
     } else {
         const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
-        o.nx[at] = sg * B.nx[s.idx];
-        o.ny[at] = sg * B.ny[s.idx];
-        o.nz[at] = sg * B.nz[s.idx];
-        o.tri[at] = (int)((unsigned)B.tri[s.idx] | 0x80000000u);
+        o.d[at] = B.d[idx];
+        o.nx[at] = sg * B.nx[idx];
+        o.ny[at] = sg * B.ny[idx];
+        o.nz[at] = sg * B.nz[idx];
+        o.tri[at] = (int)((unsigned)B.tri[idx] | 0x80000000u);
     }
 }
+
+__device__ __forceinline__ void finish_output(const Out &o, long long N, long long n_out, ldni_info_t *info) {
+    const_cast<int *>(o.off)[N] = (int)min(n_out, (long long)INT_MAX);
+    info->n[0] = n_out;
+    if (n_out > INT_MAX) set_status(info, LDNI_ST_TOOLARGE);
+    if (n_out > o.cap) set_status(info, LDNI_ST_CAPACITY);
+}
+
+// Ray kinds answered without the general merge: 1 = A alone, entering and
+// leaving once; 2 = B alone, likewise.  Their interval is kept unless it is
+// empty (both samples at one depth cancel) or thinner than eps; it belongs to
+// a union, to a difference only from A, and to no intersection.  0 = no
+// samples, 3 = anything else.
+__device__ __forceinline__ int ray_kind(long long na, long long nb) {
+    if ((na | nb) == 0) return 0;
+    if (nb == 0 && na == 2) return 1;
+    if (na == 0 && nb == 2) return 2;
+    return 3;
+}
+
+__device__ __forceinline__ int two_count(int kind, int op, float d0, float d1, float eps) {
+    if (op == LDNI_OP_INTER || (kind == 2 && op == LDNI_OP_DIFF)) return 0;
+    return (d0 == d1 || __fsub_rn(d1, d0) < eps) ? 0 : 2;
+}
+
+// merge_core with kinds 1 and 2 answered directly.
+template <class Idx, class EmitF>
+__device__ __forceinline__ int merge_ray_fast(const float *dA, Idx a, Idx ae, const float *dB, Idx b, Idx be, int op,
+                                              float eps, EmitF emit) {
+    const int kind = ray_kind(ae - a, be - b);
+    if (kind == 1 || kind == 2) {
+        const float *d = kind == 1 ? dA : dB;
+        const Idx i = kind == 1 ? a : b;
+        const int c = two_count(kind, op, d[i], d[i + 1], eps);
+        if (c) emit(kind == 2, i, kind == 2, i + 1, 0);
+        return c;
+    }
+    return merge_core<Idx>(dA, a, ae, dB, b, be, op, eps, emit);
+}
+
+// ---- two-pass form (ldni_boolean_static) ------------------------------------
 
 template <bool kWrite>
 __global__ void __launch_bounds__(kThreads) bool_pass(long long nrays, Side A, Side B, int op, float eps,
@@ -96,154 +204,473 @@ __global__ void __launch_bounds__(kThreads) bool_pass(long long nrays, Side A, S
             a = min(a, ae);
             b = min(b, be);
         }
-        bool inA = false, inB = false, out = false;
-        Pick pend{false, 0, 0.0f};
-        long long m = 0;
-        const long long base = kWrite ? (long long)o.off[p] : 0;
-        while (a < ae || b < be) {
-            float d;
-            if (a < ae && b < be) {
-                const float da = A.d[a], db = B.d[b];
-                d = da < db ? da : db;
-            } else {
-                d = a < ae ? A.d[a] : B.d[b];
-            }
-            const long long fa = a, fb = b;
-            while (a < ae && A.d[a] == d) ++a;
-            while (b < be && B.d[b] == d) ++b;
-            const bool flipA = ((a - fa) & 1) != 0;
-            const bool flipB = ((b - fb) & 1) != 0;
-            inA ^= flipA;
-            inB ^= flipB;
-            const bool now = op_apply(op, inA, inB);
-            if (now == out) continue;
-            out = now;
-            const Pick cur = flipA ? Pick{false, fa, d} : Pick{true, fb, d};
-            if (now) {
-                pend = cur;
-            } else if (!(__fsub_rn(d, pend.d) < eps)) {
-                if (kWrite) {
-                    emit(pend, A, B, op, o, base + m, info);
-                    emit(cur, A, B, op, o, base + m + 1, info);
-                }
-                m += 2;
-            }
+        if (!kWrite) {
+            out_count[p] = merge_ray_fast<long long>(A.d, a, ae, B.d, b, be, op, eps, NoEmit{});
+        } else {
+            const long long base = o.off[p];
+            merge_ray_fast<long long>(A.d, a, ae, B.d, b, be, op, eps,
+                                      [&](bool pb, long long pi, bool cb, long long ci, int m) {
+                                          emit_global(pb, pi, A, B, op, o, base + m, info);
+                                          emit_global(cb, ci, A, B, op, o, base + m + 1, info);
+                                      });
         }
-        if (!kWrite) out_count[p] = (int)m;
     }
 }
 
-// ---- fused single-launch Boolean --------------------------------------
+// ---- one launch per image, tile staged in shared memory ------------------------
 //
-// One block owns a tile of kTileRays consecutive rays, taken in kRounds
-// rounds of kFusedThreads consecutive rays (lane k of a warp holds ray p + k,
-// so a warp's loads and stores touch neighbouring CSR rows).  It merges every
-// ray once to count its output samples, scans the counts inside the block,
-// obtains the tile's starting offset by decoupled look-back, writes the tile's
-// CSR offsets, then merges again (inputs now hot in L1/L2) and writes the
-// samples.  One launch per image; the workspace is one status word per tile.
-constexpr int kFusedThreads = 256;
-constexpr int kRounds = 4;
-constexpr int kTileRays = kFusedThreads * kRounds;
+// One block owns a tile of kR * 256 consecutive rays; thread t owns the kR
+// consecutive rays t*kR .. t*kR + kR - 1, so one block scan orders the tile
+// and offsets move as vectors.  The depths of the tile's samples are
+// contiguous in both operands (CSR rows in ray order): the block copies the
+// two ranges into shared memory with coalesced loads and merges from there.
+// It then
+//   1. counts every ray's output samples,
+//   2. scans the counts, obtains the tile's first output slot by decoupled
+//      look-back and writes the tile's CSR offsets,
+//   3. merges again, recording for each output sample its source (operand
+//      and index) in shared memory,
+//   4. writes the tile's output samples in order: depth from shared memory,
+//      normal and triangle id gathered from the source; consecutive threads
+//      write consecutive samples.
+// A tile whose two ranges exceed the shared-memory budget (or a budget of 0)
+// merges every ray from global memory instead; results are the same.
+constexpr int kStageUnroll = 8;  // staged loads in flight per thread
+constexpr int kGather = 4;       // output samples gathered per thread and step
 
-// Merge one ray.  kWrite = false: returns the output count.  kWrite = true:
-// writes the samples from `at` on.
-template <bool kWrite>
-__device__ __forceinline__ int merge_ray(long long p, const Side &A, const Side &B, int op, float eps,
-                                         const Out &o, long long at, ldni_info_t *info) {
-    long long a = A.off[p], ae = A.off[p + 1];
-    long long b = B.off[p], be = B.off[p + 1];
-    if (!kWrite && (((ae - a) | (be - b)) & 1)) {
-        atomicAdd(&info->odd_rays, 1u);
-        set_status(info, LDNI_ST_ODD);
-    }
-    if (ae > A.cap || be > B.cap) {
-        if (!kWrite) set_status(info, LDNI_ST_CAPACITY);
-        ae = min(ae, A.cap);
-        be = min(be, B.cap);
-        a = min(a, ae);
-        b = min(b, be);
-    }
-    bool inA = false, inB = false, out = false;
-    Pick pend{false, 0, 0.0f};
-    int m = 0;
-    while (a < ae || b < be) {
-        const float da = a < ae ? A.d[a] : 0.0f;
-        const float db = b < be ? B.d[b] : 0.0f;
-        const float d = (a < ae && (b >= be || da <= db)) ? da : db;
-        const long long fa = a, fb = b;
-        while (a < ae && A.d[a] == d) ++a;
-        while (b < be && B.d[b] == d) ++b;
-        const bool flipA = ((a - fa) & 1) != 0;
-        const bool flipB = ((b - fb) & 1) != 0;
-        inA ^= flipA;
-        inB ^= flipB;
-        const bool now = op_apply(op, inA, inB);
-        if (now == out) continue;
-        out = now;
-        const Pick cur = flipA ? Pick{false, fa, d} : Pick{true, fb, d};
-        if (now) {
-            pend = cur;
-        } else if (!(__fsub_rn(d, pend.d) < eps)) {
-            if (kWrite) {
-                emit(pend, A, B, op, o, at + m, info);
-                emit(cur, A, B, op, o, at + m + 1, info);
-            }
-            m += 2;
-        }
-    }
-    return m;
+__device__ __forceinline__ int clamp_local(long long x, long long cap_rel) {  // x >= 0
+    return cap_rel < 0 ? 0 : (int)min(x, cap_rel);
 }
 
-__global__ void __launch_bounds__(kFusedThreads, 4) bool_fused(long long N, Side A, Side B, int op, float eps,
-                                                               Out o, unsigned long long *words, int ntiles,
-                                                               ldni_info_t *info) {
-    __shared__ long long sh[kFusedThreads / 32 + 1];
+// Copy n floats from global to shared memory, kStageUnroll loads in flight per thread.
+__device__ __forceinline__ void stage_range(const float *__restrict__ src, int n, float *dst) {
+    for (int k0 = threadIdx.x; k0 < n; k0 += kBoolThreads * kStageUnroll) {
+        float v[kStageUnroll];
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int k = k0 + u * kBoolThreads;
+            v[u] = k < n ? src[k] : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kStageUnroll; ++u) {
+            const int k = k0 + u * kBoolThreads;
+            if (k < n) dst[k] = v[u];
+        }
+    }
+}
+
+// Rows of rays q .. q + kR (rows past the tile's end repeat its end).
+template <int kR>
+__device__ __forceinline__ void load_rows(const int *off, long long p0, int q, int nr, int (&r)[kR + 1]) {
+    if (kR >= 4 && (reinterpret_cast<uintptr_t>(off) & 15) == 0 && q + kR <= nr) {
+#pragma unroll
+        for (int v = 0; v < kR; v += 4) {
+            const int4 x = *reinterpret_cast<const int4 *>(off + p0 + q + v);
+            r[v] = x.x; r[v + 1] = x.y; r[v + 2] = x.z; r[v + 3] = x.w;
+        }
+        r[kR] = off[p0 + q + kR];
+    } else {
+#pragma unroll
+        for (int k = 0; k <= kR; ++k) r[k] = off[p0 + min(q + k, nr)];
+    }
+}
+
+// kR ints of this thread to a[p0 + q ..], as 16-byte stores when possible.
+template <int kR>
+__device__ __forceinline__ void store_rows(int *dst, long long p0, int q, int nr, const int (&w)[kR]) {
+    if (kR >= 4 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 && q + kR <= nr) {
+#pragma unroll
+        for (int v = 0; v < kR; v += 4)
+            *reinterpret_cast<int4 *>(dst + p0 + q + v) = make_int4(w[v], w[v + 1], w[v + 2], w[v + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kR; ++k)
+            if (q + k < nr) dst[p0 + q + k] = w[k];
+    }
+}
+
+template <int kR>
+struct TileIn {
+    int la[kR + 1], lb[kR + 1];  // rows q0 .. q0 + kR, tile-local and clamped to capacity
+    unsigned odd;                // bit k: ray q0 + k has an odd count in A or B
+    long long ga0, gb0;          // first kept sample of the tile
+    int LA, LB;                  // kept samples of the tile
+    bool staged;
+};
+
+// Rows of this thread's rays, the tile's sample ranges and, if they fit the
+// budget, their depths in shared memory.  Ends with a barrier.
+template <int kR>
+__device__ __forceinline__ void tile_prologue(const Side &A, const Side &B, long long p_begin, int nr, int budget,
+                                              float *sd, long long *sh4, TileIn<kR> &T, ldni_info_t *info) {
+    const int q0 = threadIdx.x * kR;
+    int ra[kR + 1], rb[kR + 1];
+    load_rows<kR>(A.off, p_begin, q0, nr, ra);
+    load_rows<kR>(B.off, p_begin, q0, nr, rb);
+    if (threadIdx.x == 0) {
+        sh4[0] = ra[0];
+        sh4[1] = rb[0];
+    }
+    if (q0 < nr && q0 + kR >= nr) {  // this thread holds the tile's end row
+#pragma unroll
+        for (int k = 1; k <= kR; ++k)
+            if (q0 + k == nr) {
+                sh4[2] = ra[k];
+                sh4[3] = rb[k];
+            }
+    }
+    __syncthreads();
+    const int rawA0 = (int)sh4[0], rawB0 = (int)sh4[1];
+    const int endA = (int)sh4[2], endB = (int)sh4[3];
+    T.ga0 = min((long long)rawA0, A.cap);
+    T.gb0 = min((long long)rawB0, B.cap);
+    const long long capA = A.cap - rawA0, capB = B.cap - rawB0;  // capacities relative to the tile
+    T.LA = clamp_local((long long)(endA - rawA0), capA);
+    T.LB = clamp_local((long long)(endB - rawB0), capB);
+    T.odd = 0;
+#pragma unroll
+    for (int k = 0; k <= kR; ++k) {
+        T.la[k] = clamp_local((long long)(ra[k] - rawA0), capA);
+        T.lb[k] = clamp_local((long long)(rb[k] - rawB0), capB);
+        if (k < kR && q0 + k < nr && (((ra[k + 1] - ra[k]) | (rb[k + 1] - rb[k])) & 1)) T.odd |= 1u << k;
+    }
+    if (threadIdx.x == 0 && (endA > A.cap || endB > B.cap)) set_status(info, LDNI_ST_CAPACITY);
+    T.staged = budget > 0 && (long long)T.LA + T.LB <= budget;
+    if (T.staged) {
+        stage_range(A.d + T.ga0, T.LA, sd);
+        stage_range(B.d + T.gb0, T.LB, sd + T.LA);
+    }
+    __syncthreads();
+}
+
+// Output counts of this thread's rays (and the odd-count check).
+template <int kR>
+__device__ __forceinline__ int tile_counts(const TileIn<kR> &T, const Side &A, const Side &B, int op, float eps,
+                                           int nr, const float *sd, int (&cnt)[kR], ldni_info_t *info) {
+    const int q0 = threadIdx.x * kR;
+    const float *sA = sd, *sB = sd + T.LA;
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        cnt[k] = 0;
+        if (q0 + k >= nr) continue;
+        if (T.odd & (1u << k)) {
+            atomicAdd(&info->odd_rays, 1u);
+            set_status(info, LDNI_ST_ODD);
+        }
+        const int a = T.la[k], ae = T.la[k + 1], b = T.lb[k], be = T.lb[k + 1];
+        if (a == ae && b == be) continue;
+        if (T.staged)
+            cnt[k] = merge_ray_fast<int>(sA, a, ae, sB, b, be, op, eps, NoEmit{});
+        else
+            cnt[k] = merge_ray_fast<long long>(A.d, T.ga0 + a, T.ga0 + ae, B.d, T.gb0 + b, T.gb0 + be, op, eps,
+                                               NoEmit{});
+        mine += cnt[k];
+    }
+    return mine;
+}
+
+// CSR offsets of this thread's rays, then the tile's output samples from
+// output slot `base` on (this thread's first sample is at base + excl).
+template <int kR>
+__device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, const Side &B, int op, float eps,
+                                          const Out &o, long long p_begin, int nr, const int (&cnt)[kR], int excl,
+                                          long long base, long long total, const float *sd, int *pick,
+                                          ldni_info_t *info) {
+    const int q0 = threadIdx.x * kR;
+    {
+        int w[kR];
+        int run = excl;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            w[k] = (int)min(base + run, (long long)INT_MAX);
+            run += cnt[k];
+        }
+        store_rows<kR>(const_cast<int *>(o.off), p_begin, q0, nr, w);
+    }
+    if (!T.staged) {
+        int run = excl;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            if (cnt[k] > 0) {
+                const long long at = base + run;
+                merge_ray_fast<long long>(A.d, T.ga0 + T.la[k], T.ga0 + T.la[k + 1], B.d, T.gb0 + T.lb[k],
+                                          T.gb0 + T.lb[k + 1], op, eps,
+                                          [&](bool pb, long long pi, bool cb, long long ci, int m) {
+                                              emit_global(pb, pi, A, B, op, o, at + m, info);
+                                              emit_global(cb, ci, A, B, op, o, at + m + 1, info);
+                                          });
+            }
+            run += cnt[k];
+        }
+        return;  // block-uniform: no barrier follows on this path
+    }
+    const float *sA = sd, *sB = sd + T.LA;
+    {
+        int run = excl;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            if (cnt[k] > 0) {
+                const int at = run;
+                merge_ray_fast<int>(sA, T.la[k], T.la[k + 1], sB, T.lb[k], T.lb[k + 1], op, eps,
+                                    [&](bool pb, int pi, bool cb, int ci, int m) {
+                                        pick[at + m] = pb ? (int)(0x80000000u | (unsigned)pi) : pi;
+                                        pick[at + m + 1] = cb ? (int)(0x80000000u | (unsigned)ci) : ci;
+                                    });
+            }
+            run += cnt[k];
+        }
+    }
+    __syncthreads();
+    const int tot = (int)total;
+    const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+    for (int k0 = threadIdx.x; k0 < tot; k0 += kBoolThreads * kGather) {
+        float d[kGather], x[kGather], y[kGather], z[kGather];
+        int t[kGather];
+#pragma unroll
+        for (int u = 0; u < kGather; ++u) {
+            const int k = k0 + u * kBoolThreads;
+            if (k < tot) {
+                const int code = pick[k];
+                const int i = code & 0x7fffffff;
+                const bool fb = code < 0;
+                const long long g = (fb ? T.gb0 : T.ga0) + i;
+                d[u] = fb ? sB[i] : sA[i];
+                x[u] = (fb ? B.nx : A.nx)[g];
+                y[u] = (fb ? B.ny : A.ny)[g];
+                z[u] = (fb ? B.nz : A.nz)[g];
+                t[u] = (fb ? B.tri : A.tri)[g];
+                if (fb) {
+                    x[u] *= sg;
+                    y[u] *= sg;
+                    z[u] *= sg;
+                    t[u] = (int)((unsigned)t[u] | 0x80000000u);
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kGather; ++u) {
+            const int k = k0 + u * kBoolThreads;
+            if (k >= tot) continue;
+            const long long at = base + k;
+            if (at >= o.cap) {
+                set_status(info, LDNI_ST_CAPACITY);
+                continue;
+            }
+            o.d[at] = d[u];
+            o.nx[at] = x[u];
+            o.ny[at] = y[u];
+            o.nz[at] = z[u];
+            o.tri[at] = t[u];
+        }
+    }
+}
+
+template <int kR>
+__global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, Side A, Side B, int op, float eps, Out o,
+                                                           unsigned long long *words, int ntiles, int budget,
+                                                           ldni_info_t *info) {
+    constexpr int kRays = kR * kBoolThreads;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sd = reinterpret_cast<float *>(smem_raw);  // [budget] A depths, then B depths
+    int *pick = reinterpret_cast<int *>(sd + budget);  // [budget] source of every output sample
+    __shared__ long long sh[kBoolThreads / 32 + 1];
+    __shared__ long long sh4[4];
     __shared__ int s_tile;
     __shared__ long long s_base;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(words + ntiles, 1ull);
     __syncthreads();
     const int tile = s_tile;
-    const long long p0 = (long long)tile * kTileRays + threadIdx.x;  // round r: ray p0 + r * kFusedThreads
-    int cnt[kRounds];
-    long long excl[kRounds];
-    long long total = 0;
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long p = p0 + (long long)r * kFusedThreads;
-        cnt[r] = p < N ? merge_ray<false>(p, A, B, op, eps, o, 0, info) : 0;
-    }
-#pragma unroll
-    for (int r = 0; r < kRounds; ++r) {  // rays in order: round by round, lane by lane
-        long long tot;
-        excl[r] = total + block_exclusive_scan<kFusedThreads>(cnt[r], sh, &tot);
-        total += tot;
-    }
+    const long long p_begin = (long long)tile * kRays;
+    const int nr = (int)min((long long)kRays, N - p_begin);
+    TileIn<kR> T;
+    tile_prologue<kR>(A, B, p_begin, nr, budget, sd, sh4, T, info);
+    int cnt[kR];
+    const int mine = tile_counts<kR>(T, A, B, op, eps, nr, sd, cnt, info);
+    long long total;
+    const int excl = (int)block_exclusive_scan<kBoolThreads>(mine, sh, &total);
     if (threadIdx.x < 32) {
         const long long b = lookback_warp(words, tile, total, info);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
     const long long base = s_base;
-    int *off = const_cast<int *>(o.off);
+    if (tile == ntiles - 1 && threadIdx.x == 0) finish_output(o, N, base + total, info);
+    tile_emit<kR>(T, A, B, op, eps, o, p_begin, nr, cnt, excl, base, total, sd, pick, info);
+}
+
+// ---- three launches per image -----------------------------------------------
+//
+// No block waits for another.  Each thread owns kR consecutive rays and reads
+// their rows and depths straight from global memory: a ray of kind 1 or 2
+// needs its two depths, issued for all the thread's rays before any is used;
+// every other ray runs the general merge.
+
+// Pass 1: output count of every ray (kept in the output's offset array,
+// which pass 3 overwrites in place) and of every tile (tile_total, cleared
+// before the launch).
+template <int kR>
+__global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side A, Side B, int op, float eps, Out o,
+                                                              unsigned long long *tile_total, ldni_info_t *info) {
+    constexpr int kRays = kR * kBoolThreads;
+    const long long p0 = (long long)blockIdx.x * kRays;
+    const int nr = (int)min((long long)kRays, N - p0);
+    const int q0 = threadIdx.x * kR;
+    int ra[kR + 1], rb[kR + 1];
+    load_rows<kR>(A.off, p0, q0, nr, ra);
+    load_rows<kR>(B.off, p0, q0, nr, rb);
+    const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;  // rows beyond capacity: general (clamping) path
+    if (clamp) set_status(info, LDNI_ST_CAPACITY);
+    int kind[kR];
+    float d0[kR], d1[kR];
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long p = p0 + (long long)r * kFusedThreads;
-        if (p < N) off[p] = (int)min(base + excl[r], (long long)INT_MAX);
+    for (int k = 0; k < kR; ++k) {
+        const int na = ra[k + 1] - ra[k], nb = rb[k + 1] - rb[k];
+        if ((na | nb) & 1) {
+            atomicAdd(&info->odd_rays, 1u);
+            set_status(info, LDNI_ST_ODD);
+        }
+        kind[k] = clamp ? 3 : ray_kind(na, nb);
+        const float *d = kind[k] == 2 ? B.d + rb[k] : A.d + ra[k];
+        d0[k] = d1[k] = 0.0f;
+        if (kind[k] == 1 || kind[k] == 2) {
+            d0[k] = d[0];
+            d1[k] = d[1];
+        }
     }
-    if (tile == ntiles - 1 && threadIdx.x == 0) {
-        const long long n_out = base + total;
-        off[N] = (int)min(n_out, (long long)INT_MAX);
-        info->n[0] = n_out;
-        if (n_out > INT_MAX) set_status(info, LDNI_ST_TOOLARGE);
-        if (n_out > o.cap) set_status(info, LDNI_ST_CAPACITY);
-    }
+    int cnt[kR];
+    int mine = 0;
 #pragma unroll
-    for (int r = 0; r < kRounds; ++r) {
-        const long long p = p0 + (long long)r * kFusedThreads;
-        if (p < N && cnt[r] > 0) merge_ray<true>(p, A, B, op, eps, o, base + excl[r], info);
+    for (int k = 0; k < kR; ++k) {
+        if (kind[k] == 3) {
+            const long long a = min((long long)ra[k], A.cap), b = min((long long)rb[k], B.cap);
+            const int na = (int)(min((long long)ra[k + 1], A.cap) - a), nb = (int)(min((long long)rb[k + 1], B.cap) - b);
+            cnt[k] = merge_core<int>(A.d + a, 0, na, B.d + b, 0, nb, op, eps, NoEmit{});
+        } else {
+            cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
+        }
+        mine += cnt[k];
+    }
+    store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, cnt);
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, w);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(tile_total + blockIdx.x, (unsigned long long)mine);
+}
+
+// Pass 2: exclusive prefix of the tile totals (one block of 1024 threads,
+// kPer consecutive totals per thread and round).
+__global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total, int ntiles,
+                                                        long long *tile_pre, Out o, long long N, ldni_info_t *info) {
+    constexpr int kPer = 4;
+    __shared__ long long sh[1024 / 32 + 1];
+    long long carry = 0;
+    for (int b0 = 0; b0 < ntiles; b0 += 1024 * kPer) {
+        const int k0 = b0 + threadIdx.x * kPer;
+        long long v[kPer], sum = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            v[u] = k0 + u < ntiles ? (long long)tile_total[k0 + u] : 0;
+            sum += v[u];
+        }
+        long long tot;
+        long long run = carry + block_exclusive_scan<1024>(sum, sh, &tot);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+            if (k0 + u < ntiles) tile_pre[k0 + u] = run;
+            run += v[u];
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) finish_output(o, N, carry, info);
+}
+
+__device__ __forceinline__ void put_sample(const Out &o, long long at, float d, float x, float y, float z, int t,
+                                           ldni_info_t *info) {
+    if (at >= o.cap) {
+        set_status(info, LDNI_ST_CAPACITY);
+        return;
+    }
+    o.d[at] = d;
+    o.nx[at] = x;
+    o.ny[at] = y;
+    o.nz[at] = z;
+    o.tri[at] = t;
+}
+
+// Pass 3: offsets from the counts and the tile's prefix, then the samples of
+// every ray at its offset.
+template <int kR>
+__global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, Side A, Side B, int op, float eps, Out o,
+                                                              const long long *tile_pre, ldni_info_t *info) {
+    constexpr int kRays = kR * kBoolThreads;
+    __shared__ long long sh[kBoolThreads / 32 + 1];
+    const long long p0 = (long long)blockIdx.x * kRays;
+    const int nr = (int)min((long long)kRays, N - p0);
+    const int q0 = threadIdx.x * kR;
+    int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
+    load_rows<kR>(A.off, p0, q0, nr, ra);
+    load_rows<kR>(B.off, p0, q0, nr, rb);
+    load_rows<kR>(o.off, p0, q0, nr, cnt);  // pass 1's counts (cnt[kR] unused)
+#pragma unroll
+    for (int k = 0; k < kR; ++k)
+        if (q0 + k >= nr) cnt[k] = 0;
+    const long long tile_base = tile_pre[blockIdx.x];
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) mine += cnt[k];
+    long long total;
+    const long long base = tile_base + block_exclusive_scan<kBoolThreads>(mine, sh, &total);
+    {
+        int w[kR];
+        long long run = base;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            w[k] = (int)min(run, (long long)INT_MAX);
+            run += cnt[k];
+        }
+        store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, w);
+    }
+    const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;
+    const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+    long long at = base;
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        if (cnt[k] > 0) {
+            const int kind = clamp ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k]);
+            if (kind == 3) {
+                const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
+                const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
+                const int nb = (int)(min((long long)rb[k + 1], B.cap) - b0);
+                const long long at0 = at;
+                merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
+                    emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
+                    emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
+                });
+            } else {  // a kept pair of one operand: copy both samples
+                const bool fa = kind == 1;
+                const int i = fa ? ra[k] : rb[k];
+                const float *sd = (fa ? A.d : B.d) + i, *sx = (fa ? A.nx : B.nx) + i;
+                const float *sy = (fa ? A.ny : B.ny) + i, *sz = (fa ? A.nz : B.nz) + i;
+                const int *st = (fa ? A.tri : B.tri) + i;
+                const float e0 = sd[0], e1 = sd[1];
+                const float x0 = sx[0], x1 = sx[1];
+                const float y0 = sy[0], y1 = sy[1];
+                const float z0 = sz[0], z1 = sz[1];
+                int t0 = st[0], t1 = st[1];
+                const float f = fa ? 1.0f : sg;
+                if (!fa) {
+                    t0 = (int)((unsigned)t0 | 0x80000000u);
+                    t1 = (int)((unsigned)t1 | 0x80000000u);
+                }
+                put_sample(o, at, e0, f * x0, f * y0, f * z0, t0, info);
+                put_sample(o, at + 1, e1, f * x1, f * y1, f * z1, t1, info);
+            }
+        }
+        at += cnt[k];
     }
 }
+
+// ---- host side ------------------------------------------------------------------
 
 int grid_blocks(long long work) {
     long long b = (work + kThreads - 1) / kThreads;
@@ -271,20 +698,49 @@ bool layers_ok(const ldni_layers_t *L, bool need) {
     return true;
 }
 
+constexpr int kMinTileRays = 256;  // the workspace is sized for the smallest tile
+
+template <int kR>
+int launch_bool(long long N, const Side &sa, const Side &sb, int op, float eps, const Out &o, void *ws, int budget,
+                bool split, ldni_info_t *info, cudaStream_t s) {
+    constexpr int kRays = kR * kBoolThreads;
+    const int ntiles = (int)((N + kRays - 1) / kRays);
+    if (!split) {
+        unsigned long long *words = static_cast<unsigned long long *>(ws);
+        if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(ntiles + 1), s) != cudaSuccess)
+            return LDNI_ECUDA;
+        const size_t smem = 8 * (size_t)budget;  // staged depths + output sources
+        if (smem > 48 * 1024 &&
+            cudaFuncSetAttribute(bool_tiled<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+            return LDNI_ECUDA;
+        LDNI_LAUNCH(K_BOOL_FUSED, s,
+                    bool_tiled<kR><<<ntiles, kBoolThreads, smem, s>>>(N, sa, sb, op, eps, o, words, ntiles, budget,
+                                                                       info));
+        return cuda_status();
+    }
+    unsigned long long *tile_total = static_cast<unsigned long long *>(ws);
+    long long *tile_pre = reinterpret_cast<long long *>(tile_total + ntiles);
+    if (cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)ntiles, s) != cudaSuccess)
+        return LDNI_ECUDA;
+    LDNI_LAUNCH(K_BOOL_COUNT, s,
+                bool_count<kR><<<ntiles, kBoolThreads, 0, s>>>(N, sa, sb, op, eps, o, tile_total, info));
+    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<1, 1024, 0, s>>>(tile_total, ntiles, tile_pre, o, N, info));
+    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<ntiles, kBoolThreads, 0, s>>>(N, sa, sb, op, eps, o, tile_pre, info));
+    return cuda_status();
+}
+
 }  // namespace
 }  // namespace ldni
 
 using namespace ldni;
 
-namespace ldni {
-namespace {
-int fused_tiles(long long N) { return (int)((N + kTileRays - 1) / kTileRays); }
-}  // namespace
-}  // namespace ldni
-
 extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
     if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
-    *bytes = align_up(sizeof(unsigned long long) * (size_t)(fused_tiles((long long)res * res) + 1));
+    const long long N = (long long)res * res;
+    // look-back words and ticket of the one-launch form, or tile totals and
+    // prefixes of the three-launch form, for the smallest tile
+    *bytes = align_up(2 * sizeof(long long) * (size_t)((N + kMinTileRays - 1) / kMinTileRays + 1));
     return LDNI_OK;
 }
 
@@ -299,18 +755,23 @@ extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, c
         return LDNI_EGRID_MISMATCH;
     const int res = grid_a->res;
     const long long N = (long long)res * res;
-    const int ntiles = fused_tiles(N);
-    if (ws_bytes < sizeof(unsigned long long) * (size_t)(ntiles + 1)) return LDNI_EWORKSPACE;
+    size_t need = 0;
+    ldni_boolean_workspace_size(res, &need);
+    if (ws_bytes < need) return LDNI_EWORKSPACE;
+    const ldni_tuning_t tune = current_tuning();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    unsigned long long *words = static_cast<unsigned long long *>(ws);
-    if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(ntiles + 1), s) != cudaSuccess)
-        return LDNI_ECUDA;
     Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
     Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
     Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
-    LDNI_LAUNCH(K_BOOL_FUSED, s,
-                bool_fused<<<ntiles, kFusedThreads, 0, s>>>(N, sa, sb, op, eps, o, words, ntiles, info));
-    return cuda_status();
+    const int budget = tune.bool_stage_samples;
+    const int rays = tune.bool_tile_rays;
+    const bool split = tune.bool_split < 0 ? N / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
+    switch (rays) {
+        case 256: return launch_bool<1>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
+        case 512: return launch_bool<2>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
+        case 2048: return launch_bool<8>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
+        default: return launch_bool<4>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
+    }
 }
 
 // ---- Boolean without a caller workspace -------------------------------------

@@ -1,5 +1,6 @@
 // Small C-ABI helpers: error strings, version, grid from a bounding box.
 #include <cmath>
+#include <mutex>
 
 #include "ldni_host.h"
 
@@ -75,4 +76,39 @@ extern "C" const char *ldni_kernel_name(int32_t id) {
                                              "layout",     "onepass",    "onepass_big", "redo",
                                              "gather",     "mlp",        "adjoint",   "batch"};
     return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
+}
+
+// ---- launch tuning -----------------------------------------------------------
+namespace ldni {
+namespace {
+constexpr ldni_tuning_t kDefaultTuning = {1024, 4096, 16, -1};
+std::mutex g_tuning_mu;
+ldni_tuning_t g_tuning = kDefaultTuning;
+
+bool tuning_ok(const ldni_tuning_t &t) {
+    const int r = t.bool_tile_rays;
+    return (r == 256 || r == 512 || r == 1024 || r == 2048) && t.bool_stage_samples >= 0 &&
+           t.bool_stage_samples <= 16384 && t.tri_blocks_per_sm >= 1 && t.tri_blocks_per_sm <= 64 &&
+           t.bool_split >= -1 && t.bool_split <= 1;
+}
+}  // namespace
+
+ldni_tuning_t current_tuning() {
+    std::lock_guard<std::mutex> lock(g_tuning_mu);
+    return g_tuning;
+}
+}  // namespace ldni
+
+extern "C" int ldni_get_tuning(ldni_tuning_t *t) {
+    if (!t) return LDNI_EINVAL;
+    *t = ldni::current_tuning();
+    return LDNI_OK;
+}
+
+extern "C" int ldni_set_tuning(const ldni_tuning_t *t) {
+    const ldni_tuning_t v = t ? *t : ldni::kDefaultTuning;
+    if (!ldni::tuning_ok(v)) return LDNI_EINVAL;
+    std::lock_guard<std::mutex> lock(ldni::g_tuning_mu);
+    ldni::g_tuning = v;
+    return LDNI_OK;
 }

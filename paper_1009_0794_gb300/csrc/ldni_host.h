@@ -32,6 +32,9 @@ struct Carver {
     bool fits() const { return off <= cap; }
 };
 
+// Launch knobs (ldni_set_tuning), copied at launch time.
+ldni_tuning_t current_tuning();
+
 inline bool grid_valid(const ldni_grid_t *g) {
     return g && g->res >= 1 && g->res <= 8192 && g->width > 0.0f && g->width < 3.0e38f;
 }

@@ -246,7 +246,7 @@ int prepare(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, con
 
 int grid_blocks(long long work) {
     long long b = (work + kThreads - 1) / kThreads;
-    const long long lim = (long long)num_sms() * 16;
+    const long long lim = (long long)num_sms() * current_tuning().tri_blocks_per_sm;
     if (b > lim) b = lim;
     return (int)(b > 0 ? b : 1);
 }

@@ -64,3 +64,21 @@ def test_grid_mismatch_refused_on_host():
 
 def test_package_import_is_light():
     assert pkg.LDNIError is _lib.LDNIError
+
+
+def test_tuning_knobs_validate_on_host():
+    """ldni_set_tuning rejects out-of-range knobs without changing the
+    current ones, and NULL restores the defaults (no GPU needed)."""
+    from paper_1009_0794_gb300 import _lib
+    lib = _lib.load()
+    t = _lib.Tuning()
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0
+    assert (t.bool_tile_rays, t.bool_stage_samples, t.tri_blocks_per_sm, t.bool_split) == (1024, 4096, 16, -1)
+    for bad in (_lib.Tuning(300, 4096, 16, 0), _lib.Tuning(1024, 20000, 16, 0), _lib.Tuning(1024, 4096, 0, 0),
+                _lib.Tuning(1024, 4096, 16, 2)):
+        assert lib.ldni_set_tuning(ctypes.byref(bad)) == -1
+    good = _lib.Tuning(512, 0, 4, 1)
+    assert lib.ldni_set_tuning(ctypes.byref(good)) == 0
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and (t.bool_tile_rays, t.tri_blocks_per_sm) == (512, 4)
+    assert lib.ldni_set_tuning(None) == 0
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 1024

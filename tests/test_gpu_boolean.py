@@ -116,3 +116,43 @@ def test_odd_operand_rejected(ldni):
         ldni.boolean(L, L, "union")
     with pytest.raises(ldni.LDNIError):
         ldni.volume(L)
+
+
+@pytest.mark.parametrize("tile", [256, 512, 1024, 2048])
+@pytest.mark.parametrize("stage", [0, 64, 4096, 16384])
+@pytest.mark.parametrize("split", [0, 1])
+def test_tuning_does_not_change_results(ldni, tile, stage, split):
+    """Every launch shape of the Boolean (tile rays, samples staged in shared
+    memory; 64 forces a mix of staged and unstaged tiles) gives the oracle's
+    bits, on a ragged grid and on multi-layer rays."""
+    from paper_1009_0794_gb300 import tune
+    prev = tune.set(bool_tile_rays=tile, bool_stage_samples=stage, bool_split=split)
+    try:
+        A, B = M.pr1_pair()
+        for (ma, mb), res in (((A, B), 77), ((M.flower(64, 64), M.torus_knot(n_ring=96, n_side=12)), 150)):
+            LA, LB = _pairs(ldni, ma, mb, res)
+            for a in range(3):
+                for op in ("union", "inter", "diff"):
+                    got = ldni.boolean(LA[a], LB[a], op, eps=1e-5).numpy()
+                    ref = oracle.boolean(LA[a].numpy(), LB[a].numpy(), op, eps=1e-5)
+                    assert bit_equal(got, ref), (op, a)
+    finally:
+        tune.set(**prev)
+
+
+def test_tuner_picks_a_valid_choice(ldni, tmp_path, monkeypatch):
+    from paper_1009_0794_gb300 import tune
+    monkeypatch.setenv(tune.CACHE_ENV, str(tmp_path / "tune.json"))
+    prev = tune.get()
+    try:
+        A, B = M.pr1_pair()
+        LA, LB = _pairs(ldni, A, B, 128)
+        r = tune.tune_boolean(LA[0], LB[0], "union", reps=3, candidates=[(256, 0, 0), (1024, 4096, 1)])
+        assert not r["cached"] and set(r["ms"]) == {"256/0/0", "1024/4096/1"}
+        assert tune.get()["bool_tile_rays"] == r["choice"]["bool_tile_rays"]
+        again = tune.tune_boolean(LA[0], LB[0], "union")
+        assert again["cached"] and again["choice"] == r["choice"]
+        s = tune.tune_sampling(*A, ldni.Grid.cube(O3, 1.0, 64), reps=2, candidates=[4, 16])
+        assert s["choice"]["tri_blocks_per_sm"] in (4, 16)
+    finally:
+        tune.set(**prev)
