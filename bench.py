@@ -164,25 +164,30 @@ def run_reference(args):
 # GPU leg
 # ----------------------------------------------------------------------------
 def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: list, n_union: list) -> float:
-    """Bytes the method must move for one launch of kernel `kid` (all three
-    images where the kernel covers them; per launch)."""
+    """Bytes the method must move for one launch of kernel `kid`; every
+    kernel of the step covers all three images in one launch.  n, n_knot,
+    n_union: samples per image of the sphere, the knot and their union."""
     N = res * res
     mesh = 12.0 * nv + 12.0 * nt
-    ntot = float(sum(n))
+    ns, nk, nu = float(sum(n)), float(sum(n_knot)), float(sum(n_union))
     table = {
-        1: mesh + 3 * 4.0 * N,                        # count: mesh read, counts written
-        6: mesh + 3 * 4.0 * (N + 1) + 20.0 * ntot,    # fill: mesh, offsets read, samples written
-        8: 3 * 4.0 * (N + 1) + 40.0 * ntot,           # sort: offsets, samples read + written
-        5: 3 * (4.0 * N + 4.0 * (N + 1)),             # scan: counts read, offsets written
+        1: mesh + 3 * 4.0 * N,                           # count: mesh read, counts written
+        5: 3 * (4.0 * N + 4.0 * (N + 1)),                # scan: counts read, offsets written
+        6: mesh + 3 * 4.0 * (N + 1) + 20.0 * ns,         # fill: mesh, offsets read, samples written
+        8: 3 * 4.0 * (N + 1) + 40.0 * ns,                # sort: offsets, samples read + written
+        # one-pass sampling: mesh read, ray counts written, (depth, tri) slab records written
+        17: mesh + 3 * 4.0 * N + 8.0 * ns,
+        # gather: counts and slab records read, offsets and CSR samples written
+        20: 3 * 4.0 * N + 8.0 * ns + 3 * 4.0 * (N + 1) + 20.0 * ns,
+        # Boolean, three-launch form: count reads rows and depths, writes counts;
+        # write reads rows, counts and the kept operands' samples, writes the result
+        9: 3 * (8.0 * (N + 1) + 4.0 * N) + 4.0 * (ns + nk),
+        10: 3 * (8.0 * (N + 1) + 4.0 * N + 4.0 * (N + 1)) + 20.0 * (ns + nk) + 20.0 * nu,
+        # Boolean, one-launch form: both operands read, result written
+        13: 3 * (8.0 * (N + 1) + 4.0 * (N + 1)) + 20.0 * (ns + nk) + 20.0 * nu,
+        11: 3 * 4.0 * (N + 1) + 4.0 * nu,                # volume: offsets and depths read
     }
-    if kid in table:
-        return table[kid]
-    a_mean = lambda xs: float(sum(xs)) / 3.0
-    if kid == 13:  # fused Boolean, one image: both operands read, result written
-        return 8.0 * (N + 1) + 20.0 * (a_mean(n) + a_mean(n_knot)) + 4.0 * (N + 1) + 20.0 * a_mean(n_union)
-    if kid == 11:  # volume, one image: offsets and depths read
-        return 4.0 * (N + 1) + 4.0 * a_mean(n_union)
-    return 0.0
+    return table.get(kid, 0.0)
 
 
 def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
@@ -205,11 +210,8 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
         dt_ = ht.to(dev, non_blocking=True)
         A = ldni.sample(dv, dt_, grid, "all")
         vol_dev = torch.zeros(3, dtype=torch.float64, device=dev)
-        res = []
-        for a in range(3):
-            Ua = ldni.boolean(A[a], K[a], "union", ws=bws)
-            ldni.volume(Ua, out=vol_dev[a:a + 1], ws=vws, sync=False)
-            res.append(Ua)
+        res = ldni.boolean_many(A, K, "union", ws=bws)
+        ldni.volume_many(res, out=vol_dev, ws=vws, sync=False)
         if host is None:
             host = [[torch.empty(Ua.offsets.numel(), dtype=torch.int32, pin_memory=True)]
                     + [torch.empty(max(Ua.n, 1) * 2, dtype=torch.float32, pin_memory=True) for _ in range(4)]
@@ -229,7 +231,8 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
     return {"value": ws * rays_per_step / (ms * 1e-3), "unit": "rays/s",
             "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(d2h),
             "ms_per_step": ms, "wall_ms_per_step": wall, "steps": e2e_steps,
-            "api": "paper_1009_0794_gb300.sample / boolean / volume (exact sizing: one count readback per call)"}
+            "api": "paper_1009_0794_gb300.sample / boolean_many / volume_many (exact sizing: one count readback "
+                   "per call)"}
 
 
 def _capacity_net(args):
@@ -330,19 +333,18 @@ def run_ours(args):
     lplan = ldni.LearnedPlan(len(sv), len(st), grid, n_sphere, slab_samples=3 * RES * RES * 4, net=net,
                              margin=args.margin, feature_stride=32)
     main_plan = lplan if args.mode == "learned1" else plan
-    bws = torch.empty(ldni.boolean_workspace_size(RES), dtype=torch.uint8, device=dev)
-    vws = torch.empty(ldni.volume_workspace_size(RES), dtype=torch.uint8, device=dev)
-    binfo = ldni.new_info()
+    bws = torch.empty(ldni.boolean_many_workspace_size(RES, 3), dtype=torch.uint8, device=dev)
+    vws = torch.empty(ldni.volume_many_workspace_size(RES, 3), dtype=torch.uint8, device=dev)
+    binfo = torch.zeros(3, 4, dtype=torch.int64, device=dev)
+    vinfo = torch.zeros(3, 4, dtype=torch.int64, device=dev)
     U = [ldni.empty_layers(grid, a, plan.outs[a].capacity + K[a].capacity) for a in range(3)]
     vols = torch.zeros(3, dtype=torch.float64, device=dev)
-    vol_views = [vols[a:a + 1] for a in range(3)]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step():
         main_plan.run(vt, tt)
-        for a in range(3):
-            ldni.boolean(main_plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=False)
-            ldni.volume(U[a], out=vol_views[a], ws=vws, info=binfo, sync=False)
+        ldni.boolean_many(main_plan.outs, K, "union", outs=U, ws=bws, infos=binfo, sync=False)
+        ldni.volume_many(U, out=vols, ws=vws, infos=vinfo, sync=False)
 
     import ctypes
     for w in range(max(args.warmup, 3)):
@@ -350,10 +352,8 @@ def run_ours(args):
         step()
     torch.cuda.synchronize()
     main_plan.finish()
-    n_union = [0, 0, 0]
     # exact union sizes (one sync, outside the timed region)
-    for a in range(3):
-        n_union[a] = ldni.boolean(main_plan.outs[a], K[a], "union", out=U[a], ws=bws, info=binfo, sync=True).n
+    n_union = [u.n for u in ldni.boolean_many(main_plan.outs, K, "union", outs=U, ws=bws, infos=binfo, sync=True)]
 
     # the whole step as one CUDA graph: one launch per step
     g_step, launches_per_step = _capture(lib, step)
@@ -454,8 +454,15 @@ def run_ours(args):
             traffic = tj[name]["bytes_per_launch"]
     except Exception:
         traffic = None
-    stages = {lib.ldni_kernel_name(k).decode(): {"ms_per_step": totals[k], "launches_per_step": launches_per_call[k]}
-              for k in sorted(totals)}
+    stages = {}
+    for k in sorted(totals):
+        st_ms = totals[k] / launches_per_call[k]  # per launch
+        ab_k = algorithmic_bytes(k, len(sv), len(st), RES, n_sphere, [L.n for L in K], n_union)
+        stages[lib.ldni_kernel_name(k).decode()] = {
+            "ms_per_step": totals[k], "launches_per_step": launches_per_call[k],
+            "algorithmic_bytes_per_launch": ab_k or None,
+            "gbs": (ab_k / (st_ms * 1e-3) / 1e9) if ab_k else None,
+            "frac_of_measured_hbm": (ab_k / (st_ms * 1e-3) / 1e9 / peak) if ab_k else None}
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

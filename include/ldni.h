@@ -61,6 +61,7 @@ extern "C" {
 #define LDNI_AXIS_Y 1
 #define LDNI_AXIS_Z 2
 #define LDNI_AXIS_ALL 3           /* the three images of Definition 3 in one call */
+#define LDNI_MAX_IMAGES 8         /* images per ldni_boolean_many / ldni_volume_many call */
 
 #define LDNI_MODE_EXACT2 0        /* exact two-pass: count, scan, fill, sort */
 #define LDNI_MODE_LEARNED1 1      /* one pass into learned per-tile capacity, exact redo of overflow */
@@ -211,7 +212,7 @@ typedef struct {
                                     launches (1), or chosen by image size (-1) */
 } ldni_tuning_t;
 
-/* Current knobs (defaults: 1024, 4096, 16, -1). */
+/* Current knobs (defaults: 256, 4096, 16, -1). */
 int ldni_get_tuning(ldni_tuning_t *tuning_host);
 /* Replace the knobs; LDNI_EINVAL (and no change) when a value is out of range.
  * NULL restores the defaults. */
@@ -251,8 +252,9 @@ int ldni_sample_learned_workspace_size(int64_t nv, int64_t nt, int32_t res, int3
  * each pixel's layer list before the layers are captured (Section 3: the
  * stencil pass, then passes 2..n_max); here a network predicts, per tile of
  * LDNI_TILE_RAYS rays, the largest layer count k_t of its rays from features
- * of a 1-in-feature_stride triangle subsample (count, projected area, mean
- * |n_a|, depth histogram).  Every ray of tile t gets k_t slots of a slab in
+ * of a 1-in-feature_stride triangle subsample taken as runs of 8
+ * consecutive triangles (count, projected area, mean |n_a|, depth
+ * histogram).  Every ray of tile t gets k_t slots of a slab in
  * the workspace; a crossing that does not fit marks its tile, and marked
  * tiles are filled again by the exact method, so the output never depends on
  * the prediction.
@@ -323,6 +325,20 @@ int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_l
                  int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                  void *stream);
 
+/* Workspace bytes for ldni_boolean_many of `count` images at resolution res. */
+int ldni_boolean_many_workspace_size(int32_t res, int32_t count, size_t *bytes_host);
+
+/*
+ * ldni_boolean for `count` (1 .. LDNI_MAX_IMAGES) image pairs on one grid in
+ * one set of launches: out[j] = A[j] op B[j], typically the three images of
+ * two solids (Definition 3).  A, B, out: host arrays of count layers; infos:
+ * device array of count ldni_info_t.  Each result is the one ldni_boolean
+ * gives for that pair.
+ */
+int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, const ldni_grid_t *grid,
+                      int32_t op, float eps, ldni_layers_t *out, ldni_info_t *infos, void *ws, size_t ws_bytes,
+                      void *stream);
+
 /*
  * ldni_boolean without a workspace argument, for callers that cannot
  * allocate device memory where they need a Boolean (code that is handed only
@@ -357,6 +373,15 @@ int ldni_volume_workspace_size(int32_t res, size_t *bytes_host);
  */
 int ldni_volume(const ldni_layers_t *L, const ldni_grid_t *grid, double *vol, ldni_info_t *info, void *ws,
                 size_t ws_bytes, void *stream);
+
+/* Workspace bytes for ldni_volume_many of `count` images at resolution res. */
+int ldni_volume_many_workspace_size(int32_t res, int32_t count, size_t *bytes_host);
+
+/* ldni_volume of `count` (1 .. LDNI_MAX_IMAGES) images of one grid in one
+ * launch.  L: host array of count layers; vols: device double[count];
+ * infos: device ldni_info_t[count]. */
+int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldni_grid_t *grid, double *vols, ldni_info_t *infos,
+                     void *ws, size_t ws_bytes, void *stream);
 
 /* ---- adjoint of depth and volume ---------------------------------------- */
 
@@ -405,9 +430,9 @@ int ldni_profile_set(void **begin_events, void **end_events, int32_t *kernel_ids
 /* Records made since the last ldni_profile_set. */
 int64_t ldni_profile_recorded(void);
 
-/* Name of a kernel id (1 count_tri, 2 count_big, 4 scan_empty, 5 scan,
+/* Name of a kernel id (1 count_tri, 2 count_big, 4 scan_tiles, 5 scan,
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
- * two passes of ldni_boolean_static), 11 volume, 13 boolean, 14 features,
+ * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
  * 21 mlp, 22 adjoint, 23 batch). */
 const char *ldni_kernel_name(int32_t id);

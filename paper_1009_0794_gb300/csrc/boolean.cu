@@ -51,6 +51,16 @@ struct Out {
     long long cap;
 };
 
+// The images of one call: job j is out[j] = A[j] op B[j], all on one grid.
+// Kernels take it as a __grid_constant__ parameter and index it by job.
+constexpr int kMaxJobs = LDNI_MAX_IMAGES;
+struct BoolJobs {
+    Side A[kMaxJobs];
+    Side B[kMaxJobs];
+    Out o[kMaxJobs];
+    ldni_info_t *info[kMaxJobs];
+};
+
 // Truth table of an operation: bit (2 inA + inB) = op(inA, inB).
 __device__ __forceinline__ unsigned op_table(int op) {
     return op == LDNI_OP_UNION ? 0xEu : (op == LDNI_OP_INTER ? 0x8u : 0x4u);
@@ -152,13 +162,62 @@ __device__ __forceinline__ void finish_output(const Out &o, long long N, long lo
 // Ray kinds answered without the general merge: 1 = A alone, entering and
 // leaving once; 2 = B alone, likewise.  Their interval is kept unless it is
 // empty (both samples at one depth cancel) or thinner than eps; it belongs to
-// a union, to a difference only from A, and to no intersection.  0 = no
-// samples, 3 = anything else.
+// a union, to a difference only from A, and to no intersection.  4 = one
+// interval in each operand (two_two).  0 = no samples, 3 = anything else.
 __device__ __forceinline__ int ray_kind(long long na, long long nb) {
     if ((na | nb) == 0) return 0;
     if (nb == 0 && na == 2) return 1;
     if (na == 0 && nb == 2) return 2;
+    if (na == 2 && nb == 2) return 4;
     return 3;
+}
+
+// merge_core in closed form for one interval [a0, a1] of A and [b0, b1] of B
+// (same events, same tie rules: at a shared depth A's sample is the one
+// emitted, touching intervals of a union merge, a zero-length interval
+// cancels).  Returns the output count; src[k] names output k's source:
+// 0, 1 = A's first, second sample; 2, 3 = B's.
+__device__ __forceinline__ int two_two(int op, float eps, float a0, float a1, float b0, float b1, int (&src)[4]) {
+    int n = 0;
+    auto put = [&](int s0, int s1, float d0, float d1) {
+        if (!(__fsub_rn(d1, d0) < eps)) {
+            src[n] = s0;
+            src[n + 1] = s1;
+            n += 2;
+        }
+    };
+    const bool za = a0 == a1, zb = b0 == b1;
+    if (za || zb) {
+        if (!zb && op == LDNI_OP_UNION) put(2, 3, b0, b1);  // A cancels: B alone
+        if (!za && zb && op != LDNI_OP_INTER) put(0, 1, a0, a1);  // B cancels: A alone
+        return n;
+    }
+    if (op == LDNI_OP_UNION) {
+        if (a1 < b0) {
+            put(0, 1, a0, a1);
+            put(2, 3, b0, b1);
+        } else if (b1 < a0) {
+            put(2, 3, b0, b1);
+            put(0, 1, a0, a1);
+        } else {
+            const bool in_a = !(b0 < a0), out_a = !(a1 < b1);
+            put(in_a ? 0 : 2, out_a ? 1 : 3, in_a ? a0 : b0, out_a ? a1 : b1);
+        }
+    } else if (op == LDNI_OP_INTER) {
+        const bool in_a = !(a0 < b0), out_a = !(b1 < a1);
+        const float lo = in_a ? a0 : b0, hi = out_a ? a1 : b1;
+        if (lo < hi) put(in_a ? 0 : 2, out_a ? 1 : 3, lo, hi);
+    } else {  // A \ B: the parts of A before B and after B
+        if (a0 < b0) {
+            const bool out_a = !(b0 < a1);
+            put(0, out_a ? 1 : 2, a0, out_a ? a1 : b0);
+        }
+        if (b1 < a1) {
+            const bool in_a = !(a0 < b1);
+            put(in_a ? 0 : 3, 1, in_a ? a0 : b1, a1);
+        }
+    }
+    return n;
 }
 
 __device__ __forceinline__ int two_count(int kind, int op, float d0, float d1, float eps) {
@@ -176,6 +235,14 @@ __device__ __forceinline__ int merge_ray_fast(const float *dA, Idx a, Idx ae, co
         const Idx i = kind == 1 ? a : b;
         const int c = two_count(kind, op, d[i], d[i + 1], eps);
         if (c) emit(kind == 2, i, kind == 2, i + 1, 0);
+        return c;
+    }
+    if (kind == 4) {
+        int src[4];
+        const int c = two_two(op, eps, dA[a], dA[a + 1], dB[b], dB[b + 1], src);
+        for (int k = 0; k < c; k += 2)
+            emit(src[k] >= 2, (src[k] >= 2 ? b : a) + (src[k] & 1), src[k + 1] >= 2,
+                 (src[k + 1] >= 2 ? b : a) + (src[k + 1] & 1), k);
         return c;
     }
     return merge_core<Idx>(dA, a, ae, dB, b, be, op, eps, emit);
@@ -466,10 +533,12 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
     }
 }
 
+// Tickets run over all jobs' tiles in order: ticket t is tile t % tpj of job
+// t / tpj; each job has its own look-back words (words + job * tpj).
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, Side A, Side B, int op, float eps, Out o,
-                                                           unsigned long long *words, int ntiles, int budget,
-                                                           ldni_info_t *info) {
+__global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __grid_constant__ BoolJobs J, int op,
+                                                           float eps, unsigned long long *words, int tpj, int njobs,
+                                                           int budget) {
     constexpr int kRays = kR * kBoolThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *sd = reinterpret_cast<float *>(smem_raw);  // [budget] A depths, then B depths
@@ -478,9 +547,13 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, Side A, 
     __shared__ long long sh4[4];
     __shared__ int s_tile;
     __shared__ long long s_base;
-    if (threadIdx.x == 0) s_tile = (int)atomicAdd(words + ntiles, 1ull);
+    if (threadIdx.x == 0) s_tile = (int)atomicAdd(words + (size_t)tpj * njobs, 1ull);
     __syncthreads();
-    const int tile = s_tile;
+    const int job = s_tile / tpj, tile = s_tile - job * tpj;
+    const Side &A = J.A[job];
+    const Side &B = J.B[job];
+    const Out &o = J.o[job];
+    ldni_info_t *info = J.info[job];
     const long long p_begin = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p_begin);
     TileIn<kR> T;
@@ -490,12 +563,12 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, Side A, 
     long long total;
     const int excl = (int)block_exclusive_scan<kBoolThreads>(mine, sh, &total);
     if (threadIdx.x < 32) {
-        const long long b = lookback_warp(words, tile, total, info);
+        const long long b = lookback_warp(words + (size_t)job * tpj, tile, total, info);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
     const long long base = s_base;
-    if (tile == ntiles - 1 && threadIdx.x == 0) finish_output(o, N, base + total, info);
+    if (tile == tpj - 1 && threadIdx.x == 0) finish_output(o, N, base + total, info);
     tile_emit<kR>(T, A, B, op, eps, o, p_begin, nr, cnt, excl, base, total, sd, pick, info);
 }
 
@@ -510,10 +583,15 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, Side A, 
 // which pass 3 overwrites in place) and of every tile (tile_total, cleared
 // before the launch).
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side A, Side B, int op, float eps, Out o,
-                                                              unsigned long long *tile_total, ldni_info_t *info) {
+__global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const __grid_constant__ BoolJobs J, int op,
+                                                              float eps, unsigned long long *tile_total, int tpj) {
     constexpr int kRays = kR * kBoolThreads;
-    const long long p0 = (long long)blockIdx.x * kRays;
+    const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
+    const Side &A = J.A[job];
+    const Side &B = J.B[job];
+    const Out &o = J.o[job];
+    ldni_info_t *info = J.info[job];
+    const long long p0 = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p0);
     const int q0 = threadIdx.x * kR;
     int ra[kR + 1], rb[kR + 1];
@@ -522,7 +600,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side 
     const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;  // rows beyond capacity: general (clamping) path
     if (clamp) set_status(info, LDNI_ST_CAPACITY);
     int kind[kR];
-    float d0[kR], d1[kR];
+    float d0[kR], d1[kR], e0[kR], e1[kR];
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         const int na = ra[k + 1] - ra[k], nb = rb[k + 1] - rb[k];
@@ -532,10 +610,14 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side 
         }
         kind[k] = clamp ? 3 : ray_kind(na, nb);
         const float *d = kind[k] == 2 ? B.d + rb[k] : A.d + ra[k];
-        d0[k] = d1[k] = 0.0f;
-        if (kind[k] == 1 || kind[k] == 2) {
+        d0[k] = d1[k] = e0[k] = e1[k] = 0.0f;
+        if (kind[k] == 1 || kind[k] == 2 || kind[k] == 4) {
             d0[k] = d[0];
             d1[k] = d[1];
+        }
+        if (kind[k] == 4) {
+            e0[k] = B.d[rb[k]];
+            e1[k] = B.d[rb[k] + 1];
         }
     }
     int cnt[kR];
@@ -546,6 +628,9 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side 
             const long long a = min((long long)ra[k], A.cap), b = min((long long)rb[k], B.cap);
             const int na = (int)(min((long long)ra[k + 1], A.cap) - a), nb = (int)(min((long long)rb[k + 1], B.cap) - b);
             cnt[k] = merge_core<int>(A.d + a, 0, na, B.d + b, 0, nb, op, eps, NoEmit{});
+        } else if (kind[k] == 4) {
+            int src[4];
+            cnt[k] = two_two(op, eps, d0[k], d1[k], e0[k], e1[k], src);
         } else {
             cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
         }
@@ -554,14 +639,18 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, Side 
     store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, cnt);
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, w);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(tile_total + blockIdx.x, (unsigned long long)mine);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(tile_total + blockIdx.x, (unsigned long long)mine);  // job * tpj + tile
 }
 
 // Pass 2: exclusive prefix of the tile totals (one block of 1024 threads,
 // kPer consecutive totals per thread and round).
-__global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total, int ntiles,
-                                                        long long *tile_pre, Out o, long long N, ldni_info_t *info) {
+__global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total_all, int ntiles,
+                                                        long long *tile_pre_all, long long N,
+                                                        const __grid_constant__ BoolJobs J) {
     constexpr int kPer = 4;
+    const int job = blockIdx.x;  // one block per job
+    const unsigned long long *tile_total = tile_total_all + (size_t)job * ntiles;
+    long long *tile_pre = tile_pre_all + (size_t)job * ntiles;
     __shared__ long long sh[1024 / 32 + 1];
     long long carry = 0;
     for (int b0 = 0; b0 < ntiles; b0 += 1024 * kPer) {
@@ -581,7 +670,7 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
         }
         carry += tot;
     }
-    if (threadIdx.x == 0) finish_output(o, N, carry, info);
+    if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
 }
 
 __device__ __forceinline__ void put_sample(const Out &o, long long at, float d, float x, float y, float z, int t,
@@ -600,11 +689,16 @@ __device__ __forceinline__ void put_sample(const Out &o, long long at, float d, 
 // Pass 3: offsets from the counts and the tile's prefix, then the samples of
 // every ray at its offset.
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, Side A, Side B, int op, float eps, Out o,
-                                                              const long long *tile_pre, ldni_info_t *info) {
+__global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const __grid_constant__ BoolJobs J, int op,
+                                                              float eps, const long long *tile_pre, int tpj) {
     constexpr int kRays = kR * kBoolThreads;
     __shared__ long long sh[kBoolThreads / 32 + 1];
-    const long long p0 = (long long)blockIdx.x * kRays;
+    const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
+    const Side &A = J.A[job];
+    const Side &B = J.B[job];
+    const Out &o = J.o[job];
+    ldni_info_t *info = J.info[job];
+    const long long p0 = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p0);
     const int q0 = threadIdx.x * kR;
     int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
@@ -614,7 +708,7 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, Side 
 #pragma unroll
     for (int k = 0; k < kR; ++k)
         if (q0 + k >= nr) cnt[k] = 0;
-    const long long tile_base = tile_pre[blockIdx.x];
+    const long long tile_base = tile_pre[blockIdx.x];  // = job * tpj + tile
     int mine = 0;
 #pragma unroll
     for (int k = 0; k < kR; ++k) mine += cnt[k];
@@ -637,7 +731,15 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, Side 
     for (int k = 0; k < kR; ++k) {
         if (cnt[k] > 0) {
             const int kind = clamp ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k]);
-            if (kind == 3) {
+            if (kind == 4) {
+                const long long a0 = ra[k], b0 = rb[k];
+                int src[4];
+                const int c = two_two(op, eps, A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1], src);
+                for (int m = 0; m < c; ++m) {
+                    const bool fb = src[m] >= 2;
+                    emit_global(fb, (fb ? b0 : a0) + (src[m] & 1), A, B, op, o, at + m, info);
+                }
+            } else if (kind == 3) {
                 const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
                 const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
                 const int nb = (int)(min((long long)rb[k + 1], B.cap) - b0);
@@ -700,14 +802,17 @@ bool layers_ok(const ldni_layers_t *L, bool need) {
 
 constexpr int kMinTileRays = 256;  // the workspace is sized for the smallest tile
 
+size_t bool_ws_words(long long N) { return (size_t)((N + kMinTileRays - 1) / kMinTileRays); }
+
 template <int kR>
-int launch_bool(long long N, const Side &sa, const Side &sb, int op, float eps, const Out &o, void *ws, int budget,
-                bool split, ldni_info_t *info, cudaStream_t s) {
+int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, void *ws, int budget, bool split,
+                cudaStream_t s) {
     constexpr int kRays = kR * kBoolThreads;
-    const int ntiles = (int)((N + kRays - 1) / kRays);
+    const int tpj = (int)((N + kRays - 1) / kRays);
+    const int nblocks = tpj * njobs;
     if (!split) {
         unsigned long long *words = static_cast<unsigned long long *>(ws);
-        if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(ntiles + 1), s) != cudaSuccess)
+        if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * ((size_t)nblocks + 1), s) != cudaSuccess)
             return LDNI_ECUDA;
         const size_t smem = 8 * (size_t)budget;  // staged depths + output sources
         if (smem > 48 * 1024 &&
@@ -715,19 +820,52 @@ int launch_bool(long long N, const Side &sa, const Side &sb, int op, float eps, 
                 cudaSuccess)
             return LDNI_ECUDA;
         LDNI_LAUNCH(K_BOOL_FUSED, s,
-                    bool_tiled<kR><<<ntiles, kBoolThreads, smem, s>>>(N, sa, sb, op, eps, o, words, ntiles, budget,
-                                                                       info));
+                    bool_tiled<kR><<<nblocks, kBoolThreads, smem, s>>>(N, J, op, eps, words, tpj, njobs, budget));
         return cuda_status();
     }
     unsigned long long *tile_total = static_cast<unsigned long long *>(ws);
-    long long *tile_pre = reinterpret_cast<long long *>(tile_total + ntiles);
-    if (cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)ntiles, s) != cudaSuccess)
+    long long *tile_pre = reinterpret_cast<long long *>(tile_total + nblocks);
+    if (cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s) != cudaSuccess)
         return LDNI_ECUDA;
-    LDNI_LAUNCH(K_BOOL_COUNT, s,
-                bool_count<kR><<<ntiles, kBoolThreads, 0, s>>>(N, sa, sb, op, eps, o, tile_total, info));
-    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<1, 1024, 0, s>>>(tile_total, ntiles, tile_pre, o, N, info));
-    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<ntiles, kBoolThreads, 0, s>>>(N, sa, sb, op, eps, o, tile_pre, info));
+    LDNI_LAUNCH(K_BOOL_COUNT, s, bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj));
+    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J));
+    LDNI_LAUNCH(K_BOOL_WRITE, s,
+                bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
     return cuda_status();
+}
+
+bool same_grid(const ldni_grid_t *a, const ldni_grid_t *b) {
+    return a->res == b->res && a->width == b->width && a->origin[0] == b->origin[0] &&
+           a->origin[1] == b->origin[1] && a->origin[2] == b->origin[2];
+}
+
+int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, const ldni_grid_t *grid, int32_t op,
+                 float eps, ldni_layers_t *out, ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
+    if (count < 1 || count > kMaxJobs || !A || !B || !out || !infos || !ws || !grid_valid(grid) ||
+        op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
+        return LDNI_EINVAL;
+    BoolJobs J{};
+    for (int j = 0; j < count; ++j) {
+        if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true)) return LDNI_EINVAL;
+        J.A[j] = Side{A[j].capacity, A[j].offsets, A[j].depth, A[j].nx, A[j].ny, A[j].nz, A[j].tri_id};
+        J.B[j] = Side{B[j].capacity, B[j].offsets, B[j].depth, B[j].nx, B[j].ny, B[j].nz, B[j].tri_id};
+        J.o[j] = Out{out[j].offsets, out[j].depth, out[j].nx, out[j].ny, out[j].nz, out[j].tri_id, out[j].capacity};
+        J.info[j] = infos + j;
+    }
+    const long long N = (long long)grid->res * grid->res;
+    if (ws_bytes < 2 * sizeof(long long) * (bool_ws_words(N) * count + 1)) return LDNI_EWORKSPACE;
+    const ldni_tuning_t tune = current_tuning();
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int budget = tune.bool_stage_samples;
+    const int rays = tune.bool_tile_rays;
+    const bool split =
+        tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
+    switch (rays) {
+        case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, split, s);
+        case 512: return launch_bool<2>(N, J, count, op, eps, ws, budget, split, s);
+        case 2048: return launch_bool<8>(N, J, count, op, eps, ws, budget, split, s);
+        default: return launch_bool<4>(N, J, count, op, eps, ws, budget, split, s);
+    }
 }
 
 }  // namespace
@@ -736,42 +874,29 @@ int launch_bool(long long N, const Side &sa, const Side &sb, int op, float eps, 
 using namespace ldni;
 
 extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
-    if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
-    const long long N = (long long)res * res;
+    return ldni_boolean_many_workspace_size(res, 1, bytes);
+}
+
+extern "C" int ldni_boolean_many_workspace_size(int32_t res, int32_t count, size_t *bytes) {
+    if (!bytes || res < 1 || res > 8192 || count < 1 || count > kMaxJobs) return LDNI_EINVAL;
     // look-back words and ticket of the one-launch form, or tile totals and
     // prefixes of the three-launch form, for the smallest tile
-    *bytes = align_up(2 * sizeof(long long) * (size_t)((N + kMinTileRays - 1) / kMinTileRays + 1));
+    *bytes = align_up(2 * sizeof(long long) * (bool_ws_words((long long)res * res) * count + 1));
     return LDNI_OK;
 }
 
 extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
                             const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info,
                             void *ws, size_t ws_bytes, void *stream) {
-    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !info || !ws ||
-        !grid_valid(grid_a) || !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
-        return LDNI_EINVAL;
-    if (grid_a->res != grid_b->res || grid_a->width != grid_b->width || grid_a->origin[0] != grid_b->origin[0] ||
-        grid_a->origin[1] != grid_b->origin[1] || grid_a->origin[2] != grid_b->origin[2])
-        return LDNI_EGRID_MISMATCH;
-    const int res = grid_a->res;
-    const long long N = (long long)res * res;
-    size_t need = 0;
-    ldni_boolean_workspace_size(res, &need);
-    if (ws_bytes < need) return LDNI_EWORKSPACE;
-    const ldni_tuning_t tune = current_tuning();
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
-    Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
-    Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
-    const int budget = tune.bool_stage_samples;
-    const int rays = tune.bool_tile_rays;
-    const bool split = tune.bool_split < 0 ? N / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
-    switch (rays) {
-        case 256: return launch_bool<1>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
-        case 512: return launch_bool<2>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
-        case 2048: return launch_bool<8>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
-        default: return launch_bool<4>(N, sa, sb, op, eps, o, ws, budget, split, info, s);
-    }
+    if (!grid_valid(grid_a) || !grid_valid(grid_b)) return LDNI_EINVAL;
+    if (!same_grid(grid_a, grid_b)) return LDNI_EGRID_MISMATCH;
+    return boolean_jobs(1, A, B, grid_a, op, eps, out, info, ws, ws_bytes, stream);
+}
+
+extern "C" int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B,
+                                 const ldni_grid_t *grid, int32_t op, float eps, ldni_layers_t *out,
+                                 ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
+    return boolean_jobs(count, A, B, grid, op, eps, out, infos, ws, ws_bytes, stream);
 }
 
 // ---- Boolean without a caller workspace -------------------------------------
@@ -823,9 +948,7 @@ extern "C" int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *gr
     if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !info || !grid_valid(grid_a) ||
         !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
         return LDNI_EINVAL;
-    if (grid_a->res != grid_b->res || grid_a->width != grid_b->width || grid_a->origin[0] != grid_b->origin[0] ||
-        grid_a->origin[1] != grid_b->origin[1] || grid_a->origin[2] != grid_b->origin[2])
-        return LDNI_EGRID_MISMATCH;
+    if (!same_grid(grid_a, grid_b)) return LDNI_EGRID_MISMATCH;
     const int res = grid_a->res;
     if (res > kStaticMaxRes) return LDNI_ETOOLARGE;
     void *scratch = nullptr;

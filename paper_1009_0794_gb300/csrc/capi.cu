@@ -70,7 +70,7 @@ extern "C" uint64_t ldni_launch_count(void) { return ldni::launch_counter().load
 
 extern "C" const char *ldni_kernel_name(int32_t id) {
     static const char *names[ldni::K_NUM] = {"none",       "count_tri",  "count_big", "unused",
-                                             "scan_empty", "scan",       "fill_tri",  "fill_big",
+                                             "scan_tiles", "scan",       "fill_tri",  "fill_big",
                                              "sort_rays",  "bool_count", "bool_write", "volume",
                                              "unused",     "boolean",    "features",  "capacity",
                                              "layout",     "onepass",    "onepass_big", "redo",
@@ -81,7 +81,7 @@ extern "C" const char *ldni_kernel_name(int32_t id) {
 // ---- launch tuning -----------------------------------------------------------
 namespace ldni {
 namespace {
-constexpr ldni_tuning_t kDefaultTuning = {1024, 4096, 16, -1};
+constexpr ldni_tuning_t kDefaultTuning = {256, 4096, 16, -1};
 std::mutex g_tuning_mu;
 ldni_tuning_t g_tuning = kDefaultTuning;
 

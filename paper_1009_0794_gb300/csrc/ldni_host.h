@@ -71,9 +71,20 @@ inline int num_sms() {
 // LDNI_ST_TOOLARGE.  `partials` must hold csr_scan_partials(N) int64 per axis.
 // With `tinfo`, tinfo[a][c] = (offset of count c * kScanChunk, sum of that
 // chunk's counts) for every chunk c of kScanChunk counts.
+// With `verify` (one-pass sampling), chunk c of image k whose tile has
+// kcap[k][c] == 2 layers is also checked: every ray must have 0 crossings,
+// or 2 of which exitc says exactly one leaves; otherwise over[k][c] and
+// *any_over are set to 1 (the tile is redone exactly).
 constexpr int kScanChunk = 4096;
+struct ScanVerify {
+    const int *exitc[3];
+    const int *kcap[3];
+    int *over[3];
+    int *any_over;
+};
 size_t csr_scan_partials(long long N);
 int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long N, long long *partials,
-             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo = nullptr);
+             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo = nullptr,
+             const ScanVerify *verify = nullptr);
 
 }  // namespace ldni

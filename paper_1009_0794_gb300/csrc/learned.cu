@@ -10,12 +10,14 @@
 //              triangle count, projected area in pixels, mean |n_a|, and an
 //              8-bin histogram of triangle depth (a proxy for layering);
 //   mlp      : features -> log1p(k_t) -> an even capacity k_t (mlp.cuh);
-//   layout   : every ray of tile t owns k_t slab slots;
+//   layout   : every ray of tile t owns k_t slab slots (reserved by the
+//              mlp launch with one atomic per tile);
 //   one pass : every crossing takes the next slot of its ray (the atomic
 //              cursor is also the ray's exact count) and stores (depth, tri)
 //              if it fits, else marks its tile as overflowed; two-layer
 //              tiles place crossings by orientation instead (see onepass_hit);
-//   scan     : exact CSR offsets from the counts;
+//   scan     : exact CSR offsets from the counts; two-layer tiles are
+//              checked in the same pass;
 //   redo     : tiles that overflowed are filled again by the exact method
 //              (a second traversal restricted to them; no-op when none did);
 //   gather   : every ray is ordered by (depth, tri_id) and written to its CSR
@@ -50,7 +52,7 @@ struct LImg {
     long long *slab_base[3];     // first slab slot of the tile
     int *over[3];                // 1 = overflowed, redone exactly
     int2 *slab;                  // (depth bits, tri) per slot
-    float *nrm[3];               // per-triangle unit normal (x, y, z tables)
+    float4 *nrm;                 // per-triangle unit normal (x, y, z, 0): one 16-byte load per sample
     long long slab_cap;
     int *any_over;
 };
@@ -61,9 +63,6 @@ __device__ __forceinline__ T pick3(T const (&arr)[3], int a) {
 }
 
 // ---- features --------------------------------------------------------------
-
-// Shared-memory accumulators when all tiles of all images fit in them.
-constexpr int kFeatSmemTiles = 1024;  // tiles x images
 
 // Tile of one triangle on image A and its feature contributions; tile -1
 // when it covers no pixel centre.
@@ -86,71 +85,59 @@ __device__ __forceinline__ int feature_of(const TriView &T, const GridDev &g, fl
     return (int)(p >> kTileBits);
 }
 
-// Every lane of the warp calls this.  When all lanes hit the same tile (the
-// usual case: neighbouring triangles), the warp adds its sums with one set of
-// atomics; otherwise each lane adds its own.
+// Every lane of the warp calls this.  The warp walks the distinct tiles its
+// lanes hit (usually one or two: neighbouring triangles) and adds each
+// tile's sums with one set of atomics.
 template <int A>
-__device__ __forceinline__ void feature_axis(const TriView &T, bool valid, float w, const GridDev &g, float *acc,
-                                             int ntiles, bool smem, const LImg &o, float absn, int *s_lo, int *s_hi) {
+__device__ __forceinline__ void feature_axis(const TriView &T, bool valid, float w, const GridDev &g, const LImg &o,
+                                             float absn) {
     float area = 0.0f;
     int bin = 0;
     const int tile = valid ? feature_of<A>(T, g, area, bin) : -1;
-    const int t0 = __shfl_sync(0xffffffffu, tile, 0);
-    const bool uniform = __all_sync(0xffffffffu, tile == t0);
-    if (uniform && t0 < 0) return;
-    auto base = [&](int t) {
-        return smem ? acc + ((long long)A * ntiles + t) * kRawFeat : pick3(o.feat, A) + (long long)t * kRawFeat;
-    };
-    if (uniform) {
-        float c = w, ar = area * w, an = absn * w;
+    unsigned todo = __ballot_sync(0xffffffffu, tile >= 0);
+    while (todo) {
+        const int t = __shfl_sync(0xffffffffu, tile, __ffs(todo) - 1);
+        const bool mine = tile == t;
+        const unsigned grp = __ballot_sync(0xffffffffu, mine);
+        todo &= ~grp;
+        float ar = mine ? area * w : 0.0f, an = mine ? absn * w : 0.0f;
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) {
-            c += __shfl_xor_sync(0xffffffffu, c, d);
             ar += __shfl_xor_sync(0xffffffffu, ar, d);
             an += __shfl_xor_sync(0xffffffffu, an, d);
         }
         unsigned bins[8];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) bins[k] = __popc(__ballot_sync(0xffffffffu, bin == k));
+        for (int k = 0; k < 8; ++k) bins[k] = __popc(__ballot_sync(0xffffffffu, mine && bin == k));
         if ((threadIdx.x & 31) == 0) {
-            atomicMin(s_lo + A, t0);
-            atomicMax(s_hi + A, t0);
-            float *f = base(t0);
-            atomicAdd(f + 0, c);
+            float *f = pick3(o.feat, A) + (long long)t * kRawFeat;
+            atomicAdd(f + 0, (float)__popc(grp) * w);
             atomicAdd(f + 1, ar);
             atomicAdd(f + 2, an);
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (bins[k]) atomicAdd(f + 3 + k, (float)bins[k] * w);
         }
-        return;
     }
-    if (tile < 0) return;
-    atomicMin(s_lo + A, tile);
-    atomicMax(s_hi + A, tile);
-    float *f = base(tile);
-    atomicAdd(f + 0, w);
-    atomicAdd(f + 1, area * w);
-    atomicAdd(f + 2, absn * w);
-    atomicAdd(f + 3 + bin, w);
+}
+
+// Thread = (sampled triangle, image): blockIdx.y is the image, so each
+// thread's chain of dependent work is one triangle on one image.  The sample
+// is 1 in `stride` triangles taken as runs of kFeatRun consecutive ones
+// (sample s is triangle (s / kFeatRun) * kFeatRun * stride + s % kFeatRun): a
+// warp's lanes then hold a few groups of neighbouring triangles, which mostly
+// share a tile, while the runs still spread over the whole mesh.
+constexpr int kFeatRun = 8;
+__device__ __host__ __forceinline__ long long feature_samples(long long nt, int stride) {
+    const long long run = (long long)kFeatRun * stride;
+    return (nt + run - 1) / run * kFeatRun;
 }
 
 __global__ void __launch_bounds__(kThreads) features_kernel(const float *__restrict__ verts,
                                                             const int *__restrict__ tris, int nt, int nv, GridDev g,
-                                                            int ax_lo, int ax_hi, int stride, int ntiles, LImg o) {
-    extern __shared__ float acc[];
-    __shared__ int s_lo[3], s_hi[3];  // tiles this block touched, per image
-    const int naxes = ax_hi - ax_lo + 1;
-    const bool smem = ntiles * naxes <= kFeatSmemTiles;
-    if (threadIdx.x < 3) {
-        s_lo[threadIdx.x] = ntiles;
-        s_hi[threadIdx.x] = -1;
-    }
-    if (smem) {
-        for (int k = threadIdx.x; k < 3 * ntiles * kRawFeat; k += blockDim.x) acc[k] = 0.0f;
-    }
-    __syncthreads();
-    const long long nsamp = ((long long)nt + stride - 1) / stride;
+                                                            int ax_lo, int stride, LImg o) {
+    const int a = ax_lo + blockIdx.y;
+    const long long nsamp = feature_samples(nt, stride);
     const float w = (float)stride;
     // uniform loop bound per block: whole warps take part in the collectives
     for (long long base = (long long)blockIdx.x * blockDim.x; base < nsamp; base += (long long)gridDim.x * blockDim.x) {
@@ -158,24 +145,17 @@ __global__ void __launch_bounds__(kThreads) features_kernel(const float *__restr
         TriView T;
         bool valid = false;
         float nx = 0.f, ny = 0.f, nz = 0.f;
-        if (sidx < nsamp) {
-            valid = load_tri(verts, tris, (int)(sidx * stride), nv, g, T) == 0;
+        const long long t = (sidx / kFeatRun) * kFeatRun * stride + sidx % kFeatRun;
+        if (sidx < nsamp && t < nt) {
+            valid = load_tri(verts, tris, (int)t, nv, g, T) == 0;
             if (valid) face_normal(T.p[0], T.p[1], T.p[2], nx, ny, nz);
         }
-        if (ax_lo <= 0 && 0 <= ax_hi) feature_axis<0>(T, valid, w, g, acc, ntiles, smem, o, fabsf(nx), s_lo, s_hi);
-        if (ax_lo <= 1 && 1 <= ax_hi) feature_axis<1>(T, valid, w, g, acc, ntiles, smem, o, fabsf(ny), s_lo, s_hi);
-        if (ax_lo <= 2 && 2 <= ax_hi) feature_axis<2>(T, valid, w, g, acc, ntiles, smem, o, fabsf(nz), s_lo, s_hi);
-    }
-    if (smem) {
-        __syncthreads();
-        for (int a = ax_lo; a <= ax_hi; ++a) {
-            if (s_hi[a] < s_lo[a]) continue;
-            const int k0 = s_lo[a] * kRawFeat, k1 = (s_hi[a] + 1) * kRawFeat;
-            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-                const float v = acc[(long long)a * ntiles * kRawFeat + k];
-                if (v != 0.0f) atomicAdd(pick3(o.feat, a) + k, v);
-            }
-        }
+        if (a == 0)  // block-uniform
+            feature_axis<0>(T, valid, w, g, o, fabsf(nx));
+        else if (a == 1)
+            feature_axis<1>(T, valid, w, g, o, fabsf(ny));
+        else
+            feature_axis<2>(T, valid, w, g, o, fabsf(nz));
     }
 }
 
@@ -188,143 +168,106 @@ __device__ __forceinline__ int capacity_from(float y, float margin) {
     return min(max(k, 2), kMaxLayerCap);
 }
 
-// One warp per tile; the weights sit in shared memory.  Hidden units are
-// computed two per lane; the output is a warp sum, so predictions agree with
-// ldni_mlp_forward's to FP32 rounding (the capacity is a hint either way).
+// Two warps per tile, one hidden unit per lane (warp h of the pair owns units
+// 32 h .. 32 h + 31); the weights sit in shared memory and the activations of
+// the pair's tile in a shared buffer, four inputs per load.  Each unit sums
+// its inputs in order with FP32 FMAs on the BF16 weights, so predictions
+// agree with ldni_mlp_forward's to FP32 rounding (the capacity is a hint
+// either way).  Each tile then reserves its npix * k_t slab slots with one
+// atomic on the slab cursor (any order is a valid layout: the gather reads a
+// tile's base, and a tile that no longer fits gets k_t = 0, i.e. its
+// crossings all go to the exact redo).
 constexpr int kCapWarps = 8;
+constexpr int kCapTiles = kCapWarps / 2;
+
+__device__ __forceinline__ void reserve_slab(const LImg &o, int a, int tile, long long nrays, int kt,
+                                             unsigned long long *cursor) {
+    const long long npix = min((long long)kTilePix, nrays - ((long long)tile << kTileBits));
+    const unsigned long long need = (unsigned long long)(npix * kt);
+    const unsigned long long start = atomicAdd(cursor, need);
+    const bool fits = start + need <= (unsigned long long)o.slab_cap;
+    pick3(o.kcap, a)[tile] = fits ? kt : 0;
+    pick3(o.slab_base, a)[tile] = fits ? (long long)start : 0;
+}
 
 __global__ void __launch_bounds__(kCapWarps * 32) capacity_kernel(int ntiles, long long nrays, int ax_lo, int naxes,
                                                                   LImg o, const __nv_bfloat16 *__restrict__ W,
                                                                   const float *__restrict__ b, float margin,
-                                                                  int fixed_k) {
-    // weights transposed to [in][out] so that lane u reads column u: consecutive lanes, no bank conflicts
-    __shared__ __nv_bfloat16 sw[kMlpWeights];
+                                                                  int fixed_k, unsigned long long *cursor) {
+    // weights row-major [unit][in] as given, rows padded to an odd number of 32-bit words so that the
+    // 32 lanes (32 units) reading the same input pair hit 32 different banks
+    constexpr int kRow0 = kMlpIn / 2 + 1, kRowH = kMlpHidden / 2 + 1;  // words per padded row
+    constexpr int kS1 = kMlpHidden * kRow0, kS2 = kS1 + kMlpHidden * kRowH, kS3 = kS2 + kMlpHidden * kRowH;
+    __shared__ unsigned sw[kS3 + kMlpHidden / 2];
     __shared__ float sb[kMlpBiases];
-    __shared__ float act[kCapWarps][2][kMlpHidden];
+    __shared__ __align__(16) float act[kCapTiles][2][kMlpHidden];
+    __shared__ float part[kCapTiles];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int k = blockIdx.x * kCapWarps + warp;
+    const int pr = warp >> 1, half = warp & 1;
+    const int k = blockIdx.x * kCapTiles + pr;
+    const bool valid = k < ntiles * naxes;
+    const int a = ax_lo + (valid ? k / ntiles : 0), tile = valid ? k % ntiles : 0;
     if (W) {
-        auto put = [&](int i, __nv_bfloat16 v) {
-            int dst = i;
+        // copy in 32-bit words (pairs of inputs of one unit; rows have an even length)
+        const bool w_aligned = (reinterpret_cast<uintptr_t>(W) & 3) == 0;
+        const unsigned *W2 = reinterpret_cast<const unsigned *>(W);
+        const unsigned short *W1 = reinterpret_cast<const unsigned short *>(W);
+        for (int q = threadIdx.x; q < kMlpWeights / 2; q += blockDim.x) {
+            const unsigned v = w_aligned ? W2[q] : ((unsigned)W1[2 * q] | ((unsigned)W1[2 * q + 1] << 16));
+            const int i = 2 * q;
+            int dst;
             if (i < kW1) {
-                dst = kW0 + (i % kMlpIn) * kMlpHidden + i / kMlpIn;
+                dst = (i / kMlpIn) * kRow0 + (i % kMlpIn) / 2;
             } else if (i < kW3) {
                 const int base = i < kW2 ? kW1 : kW2, r = i - base;
-                dst = base + (r % kMlpHidden) * kMlpHidden + r / kMlpHidden;
+                dst = (i < kW2 ? kS1 : kS2) + (r / kMlpHidden) * kRowH + (r % kMlpHidden) / 2;
+            } else {
+                dst = kS3 + (i - kW3) / 2;
             }
             sw[dst] = v;
-        };
-        if ((reinterpret_cast<uintptr_t>(W) & 15) == 0) {  // 8 weights per 16-byte load, all loads in flight
-            const uint4 *W4 = reinterpret_cast<const uint4 *>(W);
-            constexpr int n4 = kMlpWeights / 8;
-#pragma unroll 4
-            for (int q = threadIdx.x; q < n4; q += blockDim.x) {
-                const uint4 v = W4[q];
-                const __nv_bfloat16 *h = reinterpret_cast<const __nv_bfloat16 *>(&v);
-#pragma unroll
-                for (int r = 0; r < 8; ++r) put(q * 8 + r, h[r]);
-            }
-        } else {
-            for (int i = threadIdx.x; i < kMlpWeights; i += blockDim.x) put(i, W[i]);
         }
         for (int i = threadIdx.x; i < kMlpBiases; i += blockDim.x) sb[i] = b[i];
-    }
-    __syncthreads();
-    if (k >= ntiles * naxes) return;
-    const int a = ax_lo + k / ntiles, tile = k % ntiles;
-    if (!W) {
-        if (lane == 0) pick3(o.kcap, a)[tile] = fixed_k;
-        return;
-    }
-    float *x = act[warp][0];
-    float *h = act[warp][1];
-    if (lane == 0) {
-        const long long p0 = (long long)tile << kTileBits;
-        const float frac = (float)min((long long)kTilePix, nrays - p0) / (float)kTilePix;
-        normalise_features(pick3(o.feat, a) + (long long)tile * kRawFeat, frac, x);
-    }
-    __syncwarp();
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int u = lane + 32 * half;
-        float acc = sb[kB0 + u];
-#pragma unroll
-        for (int i = 0; i < kMlpIn; ++i) acc = fmaf(__bfloat162float(sw[kW0 + i * kMlpHidden + u]), x[i], acc);
-        h[u] = fmaxf(acc, 0.0f);
-    }
-    __syncwarp();
-    float *in = h, *out = x;
-#pragma unroll
-    for (int layer = 1; layer < 3; ++layer) {
-        const int woff = layer == 1 ? kW1 : kW2, boff = layer == 1 ? kB1 : kB2;
-        float r[2];
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-            const int u = lane + 32 * half;
-            float acc = sb[boff + u];
-#pragma unroll 16
-            for (int i = 0; i < kMlpHidden; ++i) acc = fmaf(__bfloat162float(sw[woff + i * kMlpHidden + u]), in[i], acc);
-            r[half] = fmaxf(acc, 0.0f);
-        }
-        __syncwarp();
-        out[lane] = r[0];
-        out[lane + 32] = r[1];
-        __syncwarp();
-        float *tmp = in;
-        in = out;
-        out = tmp;
-    }
-    float y = __bfloat162float(sw[kW3 + lane]) * in[lane] + __bfloat162float(sw[kW3 + lane + 32]) * in[lane + 32];
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
-    if (lane == 0) pick3(o.kcap, a)[tile] = capacity_from(y + sb[kB3], margin);
-}
-
-// One block lays out the slab: tile t of image a gets npix * k_t slots.
-// Tiles that no longer fit get k_t = 0 (all their crossings go to the redo).
-__global__ void __launch_bounds__(1024) layout_kernel(int ntiles, long long nrays, int ax_lo, int naxes, LImg o) {
-    __shared__ long long sh[33];
-    __shared__ long long carry;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    const int total = ntiles * naxes;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int base = 0; base < total; base += blockDim.x) {
-        const int k = base + threadIdx.x;
-        long long need = 0;
-        int a = ax_lo, tile = 0;
-        if (k < total) {
-            a = ax_lo + k / ntiles;
-            tile = k % ntiles;
+        float *x = act[pr][0];
+        if (valid && half == 0 && lane == 0) {
             const long long p0 = (long long)tile << kTileBits;
-            need = min((long long)kTilePix, nrays - p0) * pick3(o.kcap, a)[tile];
+            const float frac = (float)min((long long)kTilePix, nrays - p0) / (float)kTilePix;
+            normalise_features(pick3(o.feat, a) + (long long)tile * kRawFeat, frac, x);
         }
-        long long x = need;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, x, d);
-            if (lane >= d) x += y;
-        }
-        if (lane == 31) sh[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            long long w = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, w, d);
-                if (lane >= d) w += y;
+    }
+    __syncthreads();
+    if (!W) {
+        if (valid && half == 0 && lane == 0) reserve_slab(o, a, tile, nrays, fixed_k, cursor);
+    } else {
+        const int u = 32 * half + lane;
+        // unit u of a layer: inputs in order, two weights per shared load, four inputs per activation load
+        auto unit = [&](const float *in, int n_in, const unsigned *row, int boff) {
+            float acc = sb[boff + u];
+            const float4 *in4 = reinterpret_cast<const float4 *>(in);
+            for (int q = 0; q < n_in / 4; ++q) {
+                const float4 v = in4[q];
+                const unsigned w01 = row[2 * q], w23 = row[2 * q + 1];
+                acc = fmaf(__uint_as_float(w01 << 16), v.x, acc);
+                acc = fmaf(__uint_as_float(w01 & 0xffff0000u), v.y, acc);
+                acc = fmaf(__uint_as_float(w23 << 16), v.z, acc);
+                acc = fmaf(__uint_as_float(w23 & 0xffff0000u), v.w, acc);
             }
-            sh[lane] = w;
-        }
+            return fmaxf(acc, 0.0f);
+        };
+        float *b0 = act[pr][0], *b1 = act[pr][1];
+        b1[u] = unit(b0, kMlpIn, sw + u * kRow0, kB0);
         __syncthreads();
-        const long long start = carry + x - need + (warp > 0 ? sh[warp - 1] : 0);
-        if (k < total) {
-            if (start + need > o.slab_cap) pick3(o.kcap, a)[tile] = 0;
-            pick3(o.slab_base, a)[tile] = start;
-        }
+        b0[u] = unit(b1, kMlpHidden, sw + kS1 + u * kRowH, kB1);  // every read of b0 (layer 0) is before the barrier
         __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = start + need;
+        b1[u] = unit(b0, kMlpHidden, sw + kS2 + u * kRowH, kB2);
         __syncthreads();
+        const unsigned w3 = sw[kS3 + u / 2];
+        float y = __uint_as_float((u & 1) ? (w3 & 0xffff0000u) : (w3 << 16)) * b1[u];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) y += __shfl_xor_sync(0xffffffffu, y, d);
+        if (half == 1 && lane == 0) part[pr] = y;
+        __syncthreads();
+        if (valid && half == 0 && lane == 0)
+            reserve_slab(o, a, tile, nrays, capacity_from(y + part[pr] + sb[kB3], margin), cursor);
     }
 }
 
@@ -333,8 +276,8 @@ __global__ void __launch_bounds__(1024) layout_kernel(int ntiles, long long nray
 // A tile given two layers per ray takes the shortcut of closed meshes: a ray
 // crossed twice is entered once and left once, so the entering crossing
 // takes slot 0 and the leaving one slot 1 - no returned atomic, only counts.
-// verify_kernel later sends every tile where some ray broke that pattern to
-// the exact redo.
+// The scan (csr_scan with ScanVerify) later sends every tile where some ray
+// broke that pattern to the exact redo.
 __device__ __forceinline__ void onepass_hit(int a, long long p, float d, int t, const float3 &n, int exiting,
                                             const LImg &o) {
     const int tile = (int)(p >> kTileBits);
@@ -392,9 +335,7 @@ __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restri
         }
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        o.nrm[0][t] = n.x;  // coalesced: the gather looks normals up by triangle
-        o.nrm[1][t] = n.y;
-        o.nrm[2][t] = n.z;
+        o.nrm[t] = make_float4(n.x, n.y, n.z, 0.0f);  // coalesced: the gather looks normals up by triangle
         if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, big_n);
         if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, big_n);
         if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, big_n);
@@ -424,28 +365,6 @@ __global__ void __launch_bounds__(kThreads) onepass_big(const float *__restrict_
     }
 }
 
-// Two-layer tiles: every ray must have 0 crossings, or 2 of which exactly one
-// leaves the solid; anything else (a ray with more layers, an open or
-// self-intersecting mesh) sends the tile to the exact redo.
-__global__ void __launch_bounds__(256) verify_kernel(int ntiles, long long nrays, int ax_lo, LImg o) {
-    const int a = ax_lo + blockIdx.y;
-    const int tile = blockIdx.x;
-    if (pick3(o.kcap, a)[tile] != 2) return;
-    const long long p0 = (long long)tile << kTileBits;
-    const int npix = (int)min((long long)kTilePix, nrays - p0);
-    const int *cnt = pick3(o.count, a) + p0;
-    const int *ex = pick3(o.exitc, a) + p0;
-    bool bad = false;
-    for (int q = threadIdx.x; q < npix; q += blockDim.x) {
-        const int c = cnt[q];
-        bad |= !(c == 0 || (c == 2 && ex[q] == 1));
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) {
-        pick3(o.over, a)[tile] = 1;
-        *o.any_over = 1;
-    }
-}
-
 // ---- exact redo of overflowed tiles ------------------------------------------
 
 __device__ __forceinline__ void redo_hit(int a, long long p, float d, int t, const LImg &o, const float3 &n,
@@ -467,6 +386,22 @@ __device__ __forceinline__ void redo_hit(int a, long long p, float d, int t, con
 template <int A>
 __device__ __forceinline__ void redo_axis(const TriView &T, int t, const float3 &n, int res, const LImg &o,
                                           ldni_info_t *info) {
+    {  // skip the edge setup unless the triangle's pixel box reaches a redone tile
+        constexpr int U = (A + 1) % 3, V = (A + 2) % 3;
+        const int umin = min(T.q[0][U], min(T.q[1][U], T.q[2][U])), umax = max(T.q[0][U], max(T.q[1][U], T.q[2][U]));
+        const int vmin = min(T.q[0][V], min(T.q[1][V], T.q[2][V])), vmax = max(T.q[0][V], max(T.q[1][V], T.q[2][V]));
+        const int i0 = max((umin + 127) >> 8, 0), i1 = min((umax - 128) >> 8, res - 1);
+        const int j0 = max((vmin + 127) >> 8, 0), j1 = min((vmax - 128) >> 8, res - 1);
+        if (i0 > i1 || j0 > j1) return;
+        const int t0 = (int)(((long long)j0 * res + i0) >> kTileBits);
+        const int t1 = (int)(((long long)j1 * res + i1) >> kTileBits);
+        if (t1 - t0 < 4) {
+            const int *over = pick3(o.over, A);
+            bool any = false;
+            for (int t = t0; t <= t1; ++t) any |= over[t] != 0;
+            if (!any) return;
+        }
+    }
     Setup32 S;
     if (setup_axis<A>(T, res, S) != kSmall) return;  // big triangles: redo_big
     const unsigned long long m = hit_mask(S);
@@ -482,27 +417,11 @@ __device__ __forceinline__ void redo_axis(const TriView &T, int t, const float3 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict__ verts, const int *__restrict__ tris,
-                                                        int nt, int nv, GridDev g, int ax_lo, int ax_hi, LImg o,
-                                                        ldni_info_t *info) {
-    if (*(volatile int *)o.any_over == 0) return;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
-        TriView T;
-        if (load_tri(verts, tris, t, nv, g, T)) continue;
-        float3 n;
-        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        if (ax_lo <= 0 && 0 <= ax_hi) redo_axis<0>(T, t, n, g.res, o, info);
-        if (ax_lo <= 1 && 1 <= ax_hi) redo_axis<1>(T, t, n, g.res, o, info);
-        if (ax_lo <= 2 && 2 <= ax_hi) redo_axis<2>(T, t, n, g.res, o, info);
-    }
-}
-
-__global__ void __launch_bounds__(kThreads) redo_big(const float *__restrict__ verts, const int *__restrict__ tris,
-                                                     int nv, GridDev g, LImg o, const int *big_q, const int *big_n,
-                                                     ldni_info_t *info) {
-    if (*(volatile int *)o.any_over == 0) return;
+__device__ __forceinline__ void redo_big_block(const float *__restrict__ verts, const int *__restrict__ tris, int nv,
+                                               const GridDev &g, const LImg &o, const int *big_q, const int *big_n,
+                                               int blk, int nblk, ldni_info_t *info) {
     const int nq = *big_n;
-    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
+    for (int e = blk; e < nq; e += nblk) {
         const int code = big_q[e];
         const int t = code >> 2, a = code & 3;
         TriView T;
@@ -520,6 +439,30 @@ __global__ void __launch_bounds__(kThreads) redo_big(const float *__restrict__ v
         }
     }
 }
+
+// One launch for both redo traversals: blocks below tri_blocks walk the
+// triangles, the others the big-triangle queue.  Nothing to do (the usual
+// case) costs one load per block.
+__global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                        int nt, int nv, GridDev g, int ax_lo, int ax_hi, LImg o,
+                                                        const int *big_q, const int *big_n, int tri_blocks,
+                                                        ldni_info_t *info) {
+    if (*(volatile int *)o.any_over == 0) return;
+    if (blockIdx.x >= tri_blocks) {
+        redo_big_block(verts, tris, nv, g, o, big_q, big_n, blockIdx.x - tri_blocks, gridDim.x - tri_blocks, info);
+        return;
+    }
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += tri_blocks * blockDim.x) {
+        TriView T;
+        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        float3 n;
+        face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
+        if (ax_lo <= 0 && 0 <= ax_hi) redo_axis<0>(T, t, n, g.res, o, info);
+        if (ax_lo <= 1 && 1 <= ax_hi) redo_axis<1>(T, t, n, g.res, o, info);
+        if (ax_lo <= 2 && 2 <= ax_hi) redo_axis<2>(T, t, n, g.res, o, info);
+    }
+}
+
 
 // ---- gather ----------------------------------------------------------------------
 
@@ -560,7 +503,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             continue;
         }
         const long long s0 = sb[tile] + (p & (kTilePix - 1)) * kt;
-        const float *NX = o.nrm[0], *NY = o.nrm[1], *NZ = o.nrm[2];
+        const float4 *NRM = o.nrm;
         if (c == 2) {  // the common case: everything in registers
             int2 v0 = o.slab[s0], v1 = o.slab[s0 + 1];
             if (key_less(__int_as_float(v1.x), v1.y, __int_as_float(v0.x), v0.y)) {
@@ -568,8 +511,9 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
                 v0 = v1;
                 v1 = w;
             }
-            const float x0 = NX[v0.y], y0 = NY[v0.y], z0 = NZ[v0.y];
-            const float x1 = NX[v1.y], y1 = NY[v1.y], z1 = NZ[v1.y];
+            const float4 q0 = NRM[v0.y], q1 = NRM[v1.y];
+            const float x0 = q0.x, y0 = q0.y, z0 = q0.z;
+            const float x1 = q1.x, y1 = q1.y, z1 = q1.z;
             D[b] = __int_as_float(v0.x);
             D[b + 1] = __int_as_float(v1.x);
             Tr[b] = v0.y;
@@ -586,9 +530,10 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             const int2 v = o.slab[s0 + x];
             D[b + x] = __int_as_float(v.x);
             Tr[b + x] = v.y;
-            X[b + x] = NX[v.y];
-            Y[b + x] = NY[v.y];
-            Z[b + x] = NZ[v.y];
+            const float4 q = NRM[v.y];
+            X[b + x] = q.x;
+            Y[b + x] = q.y;
+            Z[b + x] = q.z;
         }
         sort_ray_global(b, e, D, Tr, X, Y, Z);
     }
@@ -641,7 +586,7 @@ struct LearnedWs {
     int *kcap[3];
     long long *slab_base[3];
     int *big_q;
-    float *nrm[3];
+    float4 *nrm;
     int2 *slab;
     long long slab_cap;
 };
@@ -677,14 +622,14 @@ LearnedWs carve_learned_ws(Carver &c, long long nt, int res, int naxes, long lon
         w.slab_base[a] = sb ? sb + (size_t)a * tstride : nullptr;
     }
     w.big_q = c.take<int>((size_t)(nt * naxes > 0 ? nt * naxes : 1));
-    for (int k = 0; k < 3; ++k) w.nrm[k] = c.take<float>((size_t)(nt > 0 ? nt : 1));
+    w.nrm = c.take<float4>((size_t)(nt > 0 ? nt : 1));
     w.slab = c.take<int2>((size_t)(slab_samples > 0 ? slab_samples : 1));
     w.slab_cap = slab_samples;
     return w;
 }
 
 int feature_blocks(long long nt, int stride) {
-    const long long nsamp = (nt + stride - 1) / stride;
+    const long long nsamp = feature_samples(nt, stride);
     long long b = (nsamp + kThreads - 1) / kThreads;
     const long long lim = (long long)num_sms() * 8;  // one sampled triangle per thread where possible
     return (int)(b < 1 ? 1 : (b > lim ? lim : b));
@@ -751,32 +696,22 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
         o.over[a] = w.over[k];
     }
     o.slab = w.slab;
-    for (int k = 0; k < 3; ++k) o.nrm[k] = w.nrm[k];
+    o.nrm = w.nrm;
     o.slab_cap = w.slab_cap;
     o.any_over = w.any_over;
 
-    static bool smem_set = false;
-    const size_t feat_smem = sizeof(float) * 3 * (size_t)kFeatSmemTiles * kRawFeat;
-    if (!smem_set) {
-        if (cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)feat_smem) !=
-            cudaSuccess)
-            return LDNI_ECUDA;
-        smem_set = true;
-    }
     if (cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
-    const bool use_smem = ntiles * naxes <= kFeatSmemTiles;
-    const size_t smem = use_smem ? sizeof(float) * 3 * (size_t)ntiles * kRawFeat : 0;
     if (mlp && nt > 0)
         LDNI_LAUNCH(K_FEATURES, s,
-                    features_kernel<<<feature_blocks(nt, feature_stride), kThreads, smem, s>>>(
-                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, feature_stride, ntiles, o));
+                    features_kernel<<<dim3(feature_blocks(nt, feature_stride), naxes), kThreads, 0, s>>>(
+                        verts, tris, (int)nt, (int)nv, g, ax_lo, feature_stride, o));
     const __nv_bfloat16 *W = mlp ? reinterpret_cast<const __nv_bfloat16 *>(mlp->w) : nullptr;
     const float *B = mlp ? mlp->b : nullptr;
     const float margin = mlp ? mlp->margin : 0.0f;
     LDNI_LAUNCH(K_CAPACITY, s,
-                capacity_kernel<<<(ntiles * naxes + kCapWarps - 1) / kCapWarps, kCapWarps * 32, 0, s>>>(
-                    ntiles, N, ax_lo, naxes, o, W, B, margin, fixed_layers));
-    LDNI_LAUNCH(K_LAYOUT, s, layout_kernel<<<1, 1024, 0, s>>>(ntiles, N, ax_lo, naxes, o));
+                capacity_kernel<<<(ntiles * naxes + kCapTiles - 1) / kCapTiles, kCapWarps * 32, 0, s>>>(
+                    ntiles, N, ax_lo, naxes, o, W, B, margin, fixed_layers,
+                    reinterpret_cast<unsigned long long *>(w.any_over + 1)));  // 8-byte aligned, cleared
     if (nt > 0) {
         LDNI_LAUNCH(K_ONEPASS, s,
                     onepass_kernel<<<grid_blocks(nt), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
@@ -792,15 +727,19 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     }
     int rc = cuda_status();
     if (rc != LDNI_OK) return rc;
-    rc = csr_scan(cnt, off, naxes, N, w.scan_words, info, ax_lo, s);
+    ScanVerify ver{};
+    for (int k = 0; k < naxes; ++k) {
+        ver.exitc[k] = w.exitc[k];
+        ver.kcap[k] = w.kcap[k];
+        ver.over[k] = w.over[k];
+    }
+    ver.any_over = w.any_over;
+    rc = csr_scan(cnt, off, naxes, N, w.scan_words, info, ax_lo, s, nullptr, &ver);
     if (rc != LDNI_OK) return rc;
-    LDNI_LAUNCH(K_REDO, s, verify_kernel<<<dim3(ntiles, naxes), 256, 0, s>>>(ntiles, N, ax_lo, o));
     if (nt > 0) {
         LDNI_LAUNCH(K_REDO, s,
-                    redo_kernel<<<num_sms(), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o,
-                                                               info));
-        LDNI_LAUNCH(K_REDO, s,
-                    redo_big<<<num_sms(), kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.big_n, info));
+                    redo_kernel<<<4 * num_sms(), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o,
+                                                                   w.big_q, w.big_n, 3 * num_sms(), info));
     }
     LDNI_LAUNCH(K_GATHER, s,
                 gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info));
@@ -823,19 +762,10 @@ extern "C" int ldni_tile_features(const float *verts, int64_t nv, const int32_t 
     LImg o{};
     for (int k = 0; k < naxes; ++k) o.feat[ax_lo + k] = raw + (size_t)k * ntiles * kRawFeat;
     if (cudaMemsetAsync(raw, 0, sizeof(float) * (size_t)naxes * ntiles * kRawFeat, s) != cudaSuccess) return LDNI_ECUDA;
-    static bool smem_set = false;
-    if (!smem_set) {
-        if (cudaFuncSetAttribute(features_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(sizeof(float) * 3 * (size_t)kFeatSmemTiles * kRawFeat)) != cudaSuccess)
-            return LDNI_ECUDA;
-        smem_set = true;
-    }
-    const bool use_smem = ntiles * naxes <= kFeatSmemTiles;
-    const size_t smem = use_smem ? sizeof(float) * 3 * (size_t)ntiles * kRawFeat : 0;
     if (nt > 0)
         LDNI_LAUNCH(K_FEATURES, s,
-                    features_kernel<<<feature_blocks(nt, feature_stride), kThreads, smem, s>>>(
-                        verts, tris, (int)nt, (int)nv, make_grid(grid), ax_lo, ax_hi, feature_stride, ntiles, o));
+                    features_kernel<<<dim3(feature_blocks(nt, feature_stride), naxes), kThreads, 0, s>>>(
+                        verts, tris, (int)nt, (int)nv, make_grid(grid), ax_lo, feature_stride, o));
     LDNI_LAUNCH(K_FEATURES, s,
                 normalise_kernel<<<(ntiles * naxes + 127) / 128, 128, 0, s>>>(ntiles, N, naxes, raw, X));
     return cuda_status();

@@ -2,10 +2,13 @@
 // replaces the paper's per-pixel depth-complexity readback (Section 3:
 // n_p from the stencil buffer, then n_max = max n_p) with one device pass.
 //
-// One kernel per call: every block scans a chunk of kChunk counts (coalesced
-// 16-byte loads), finds the chunk's starting offset by decoupled look-back
-// over its predecessors, and writes its offsets.  All images of a call are
-// scanned by the same launch (blockIdx.y = image).
+// Every block scans a chunk of kChunk counts (coalesced 16-byte loads) and
+// writes its offsets; all images of a call share each launch (blockIdx.y =
+// image).  A chunk's starting offset comes either from a first launch that
+// sums every chunk (the second launch then adds the sums before its chunk,
+// read directly: no block waits for another; used up to kMaxSumChunks chunks
+// per image) or, for larger images, from decoupled look-back over its
+// predecessors in one launch.
 #include <climits>
 
 #include "ldni_host.h"
@@ -25,6 +28,8 @@ struct AxisPtrs {
     const int *counts[3];
     int *offsets[3];
     int2 *tinfo[3];
+    ScanVerify ver;
+    bool verify;
 };
 
 // 16-byte load when the address allows it (c + e aligned), scalar otherwise
@@ -39,6 +44,45 @@ __device__ __forceinline__ int4 load4(const int *c, long long e, long long N, bo
 }
 
 __device__ __forceinline__ int clamp_int(long long x) { return (int)(x < INT_MAX ? x : INT_MAX); }
+
+// ---- two-launch form (at most kMaxSumChunks chunks per image) -----------------
+//
+// Pass 1 sums every chunk; pass 2 gives every chunk the sum of the sums before
+// it by reading them directly, so no block ever waits for another.
+constexpr int kMaxSumChunks = 1024;
+
+__device__ __forceinline__ void load_chunk(const int *cnt, long long base, long long N, int4 (&v)[kSlices],
+                                           long long (&tsum)[kSlices]) {
+    const bool vec_in = ((reinterpret_cast<uintptr_t>(cnt) & 15) == 0);
+#pragma unroll
+    for (int m = 0; m < kSlices; ++m) {
+        v[m] = load4(cnt, base + (long long)m * kSlice + threadIdx.x * kVec, N, vec_in);
+        tsum[m] = (long long)v[m].x + v[m].y + v[m].z + v[m].w;
+    }
+}
+
+// Two-layer check of one-pass sampling (ScanVerify) for chunk c of image a.
+__device__ __forceinline__ void verify_chunk(const AxisPtrs &ap, int a, int c, long long base, long long N,
+                                             const int4 (&v)[kSlices]) {
+    if (!ap.verify || ap.ver.kcap[a][c] != 2) return;  // block-uniform
+    const int *ex = ap.ver.exitc[a];
+    const bool vec_ex = ((reinterpret_cast<uintptr_t>(ex) & 15) == 0);
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < kSlices; ++m) {
+        const int4 x = load4(ex, base + (long long)m * kSlice + threadIdx.x * kVec, N, vec_ex);
+        bad |= !(v[m].x == 0 || (v[m].x == 2 && x.x == 1));
+        bad |= !(v[m].y == 0 || (v[m].y == 2 && x.y == 1));
+        bad |= !(v[m].z == 0 || (v[m].z == 2 && x.z == 1));
+        bad |= !(v[m].w == 0 || (v[m].w == 2 && x.w == 1));
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) {
+        ap.ver.over[a][c] = 1;
+        *ap.ver.any_over = 1;
+    }
+}
+
+// ---- one-launch form: decoupled look-back ---------------------------------------
 
 __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long N, int nchunk,
                                                           unsigned long long *words, ldni_info_t *info,
@@ -65,6 +109,7 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
         v[m] = load4(cnt, base + (long long)m * kSlice + threadIdx.x * kVec, N, vec_in);
         tsum[m] = (long long)v[m].x + v[m].y + v[m].z + v[m].w;
     }
+    verify_chunk(ap, a, c, base, N, v);
     long long excl[kSlices];
     long long carry = 0;
 #pragma unroll
@@ -104,6 +149,67 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
     }
 }
 
+// ---- two-launch form: the kernels ------------------------------------------------
+
+__global__ void __launch_bounds__(kThreads) scan_sums(AxisPtrs ap, long long N, int nchunk, long long *sums) {
+    __shared__ long long sh[kThreads / 32 + 1];
+    const int a = blockIdx.y, c = blockIdx.x;
+    const long long base = (long long)c * kChunk;
+    int4 v[kSlices];
+    long long tsum[kSlices];
+    load_chunk(ap.counts[a], base, N, v, tsum);
+    verify_chunk(ap, a, c, base, N, v);
+    long long total;
+    block_exclusive_scan<kThreads>(tsum[0] + tsum[1] + tsum[2] + tsum[3], sh, &total);
+    if (threadIdx.x == 0) sums[(size_t)a * nchunk + c] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) scan_prefix(AxisPtrs ap, long long N, int nchunk, const long long *sums,
+                                                        ldni_info_t *info, int info_base) {
+    __shared__ long long sh[kThreads / 32 + 1];
+    const int a = blockIdx.y, c = blockIdx.x;
+    const long long base = (long long)c * kChunk;
+    int4 v[kSlices];
+    long long tsum[kSlices];
+    load_chunk(ap.counts[a], base, N, v, tsum);
+    long long before = 0;  // sum of the chunk sums before c
+    for (int k = threadIdx.x; k < c; k += kThreads) before += sums[(size_t)a * nchunk + k];
+    long long b0;
+    block_exclusive_scan<kThreads>(before, sh, &b0);
+    long long excl[kSlices];
+    long long carry = 0;
+#pragma unroll
+    for (int m = 0; m < kSlices; ++m) {
+        long long tot;
+        excl[m] = carry + block_exclusive_scan<kThreads>(tsum[m], sh, &tot);
+        carry += tot;
+    }
+    int *out = ap.offsets[a];
+    if (ap.tinfo[a] && threadIdx.x == 0) ap.tinfo[a][c] = make_int2(clamp_int(b0), clamp_int(carry));
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
+#pragma unroll
+    for (int m = 0; m < kSlices; ++m) {
+        const long long e = base + (long long)m * kSlice + threadIdx.x * kVec;
+        const long long o0 = b0 + excl[m];
+        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v[m].x), clamp_int(o0 + v[m].x + v[m].y),
+                                 clamp_int(o0 + v[m].x + v[m].y + v[m].z));
+        if (vec_ok && e + 3 < N) {
+            *reinterpret_cast<int4 *>(out + e) = w;
+        } else {
+            if (e < N) out[e] = w.x;
+            if (e + 1 < N) out[e + 1] = w.y;
+            if (e + 2 < N) out[e + 2] = w.z;
+            if (e + 3 < N) out[e + 3] = w.w;
+        }
+    }
+    if (c == nchunk - 1 && threadIdx.x == 0) {
+        const long long total = b0 + carry;
+        if (info) info->n[info_base + a] = total;
+        if (total > INT_MAX && info) atomicOr(&info->status, LDNI_ST_TOOLARGE);
+        out[N] = clamp_int(total);
+    }
+}
+
 __global__ void scan_empty(AxisPtrs ap, ldni_info_t *info, int info_base) {
     const int a = blockIdx.x;
     ap.offsets[a][0] = 0;
@@ -118,8 +224,12 @@ size_t csr_scan_partials(long long N) {
 }
 
 int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long N, long long *partials,
-             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo) {
+             ldni_info_t *info, int info_base, cudaStream_t s, int2 *const *tinfo, const ScanVerify *verify) {
     AxisPtrs ap{};
+    if (verify) {
+        ap.ver = *verify;
+        ap.verify = true;
+    }
     for (int a = 0; a < naxes; ++a) {
         ap.counts[a] = counts[a];
         ap.offsets[a] = offsets[a];
@@ -128,6 +238,12 @@ int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long
     const int nchunk = (int)((N + kChunk - 1) / kChunk);
     if (nchunk == 0) {
         LDNI_LAUNCH(K_SCAN_TOP, s, scan_empty<<<naxes, 1, 0, s>>>(ap, info, info_base));
+        return cuda_status();
+    }
+    if (nchunk <= kMaxSumChunks) {
+        LDNI_LAUNCH(K_SCAN_TOP, s, scan_sums<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials));
+        LDNI_LAUNCH(K_SCAN_DOWN, s,
+                    scan_prefix<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials, info, info_base));
         return cuda_status();
     }
     unsigned long long *words = reinterpret_cast<unsigned long long *>(partials);

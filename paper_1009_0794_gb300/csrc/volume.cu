@@ -38,10 +38,24 @@ __device__ __forceinline__ DF df_add(DF x, DF y) {
     return r;
 }
 
-__global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const int *__restrict__ off,
-                                                          const float *__restrict__ d, long long cap,
-                                                          double *partials, unsigned *done, double h2,
-                                                          double *vol, ldni_info_t *info) {
+// The images of one call (blockIdx.y = image), all at one resolution.
+struct VolJobs {
+    const int *off[LDNI_MAX_IMAGES];
+    const float *d[LDNI_MAX_IMAGES];
+    long long cap[LDNI_MAX_IMAGES];
+    double *vol[LDNI_MAX_IMAGES];
+    ldni_info_t *info[LDNI_MAX_IMAGES];
+};
+
+__global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const __grid_constant__ VolJobs J,
+                                                          double *partials_all, unsigned *done_all, double h2) {
+    const int job = blockIdx.y;
+    const int *__restrict__ off = J.off[job];
+    const float *__restrict__ d = J.d[job];
+    const long long cap = J.cap[job];
+    double *partials = partials_all + (size_t)job * gridDim.x;
+    unsigned *done = done_all + job;
+    ldni_info_t *info = J.info[job];
     __shared__ DF sh[kThreads / 32];
     __shared__ bool s_last;
     DF acc{0.0f, 0.0f};
@@ -112,7 +126,7 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
         if (threadIdx.x < w) shd[threadIdx.x] += shd[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *vol = shd[0] * h2;
+    if (threadIdx.x == 0) *J.vol[job] = shd[0] * h2;
 }
 
 int volume_blocks(long long nrays) {
@@ -127,27 +141,44 @@ int volume_blocks(long long nrays) {
 
 using namespace ldni;
 
-extern "C" int ldni_volume_workspace_size(int32_t res, size_t *bytes) {
-    if (!bytes || res < 1 || res > 8192) return LDNI_EINVAL;
-    *bytes = align_up(sizeof(double) * (size_t)volume_blocks((long long)res * res) + sizeof(double));
+extern "C" int ldni_volume_many_workspace_size(int32_t res, int32_t count, size_t *bytes) {
+    if (!bytes || res < 1 || res > 8192 || count < 1 || count > LDNI_MAX_IMAGES) return LDNI_EINVAL;
+    *bytes = align_up((sizeof(double) * (size_t)volume_blocks((long long)res * res) + sizeof(unsigned)) * count);
     return LDNI_OK;
+}
+
+extern "C" int ldni_volume_workspace_size(int32_t res, size_t *bytes) {
+    return ldni_volume_many_workspace_size(res, 1, bytes);
+}
+
+extern "C" int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldni_grid_t *grid, double *vols,
+                                ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
+    if (count < 1 || count > LDNI_MAX_IMAGES || !L || !grid_valid(grid) || !vols || !infos || !ws)
+        return LDNI_EINVAL;
+    VolJobs J{};
+    for (int j = 0; j < count; ++j) {
+        if (!L[j].offsets || (L[j].capacity > 0 && !L[j].depth) || L[j].capacity < 0) return LDNI_EINVAL;
+        J.off[j] = L[j].offsets;
+        J.d[j] = L[j].depth;
+        J.cap[j] = L[j].capacity;
+        J.vol[j] = vols + j;
+        J.info[j] = infos + j;
+    }
+    const long long N = (long long)grid->res * grid->res;
+    const int nb = volume_blocks(N);
+    size_t need = 0;
+    ldni_volume_many_workspace_size(grid->res, count, &need);
+    if (ws_bytes < need) return LDNI_EWORKSPACE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    double *partials = static_cast<double *>(ws);
+    unsigned *done = reinterpret_cast<unsigned *>(partials + (size_t)nb * count);
+    if (cudaMemsetAsync(done, 0, sizeof(unsigned) * count, s) != cudaSuccess) return LDNI_ECUDA;
+    const double h = (double)grid->width / (double)grid->res;
+    LDNI_LAUNCH(K_VOL_PARTIAL, s, volume_kernel<<<dim3(nb, count), kThreads, 0, s>>>(N, J, partials, done, h * h));
+    return cuda_status();
 }
 
 extern "C" int ldni_volume(const ldni_layers_t *L, const ldni_grid_t *grid, double *vol, ldni_info_t *info, void *ws,
                            size_t ws_bytes, void *stream) {
-    if (!L || !L->offsets || (L->capacity > 0 && !L->depth) || L->capacity < 0 || !grid_valid(grid) || !vol ||
-        !info || !ws)
-        return LDNI_EINVAL;
-    const long long N = (long long)grid->res * grid->res;
-    const int nb = volume_blocks(N);
-    if (ws_bytes < sizeof(double) * (size_t)nb + sizeof(double)) return LDNI_EWORKSPACE;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    double *partials = static_cast<double *>(ws);
-    unsigned *done = reinterpret_cast<unsigned *>(partials + nb);
-    if (cudaMemsetAsync(done, 0, sizeof(unsigned), s) != cudaSuccess) return LDNI_ECUDA;
-    const double h = (double)grid->width / (double)grid->res;
-    LDNI_LAUNCH(K_VOL_PARTIAL, s,
-                volume_kernel<<<nb, kThreads, 0, s>>>(N, L->offsets, L->depth, L->capacity, partials, done, h * h,
-                                                      vol, info));
-    return cuda_status();
+    return ldni_volume_many(1, L, grid, vol, info, ws, ws_bytes, stream);
 }

@@ -288,6 +288,77 @@ def volume(L: LDNI, stream=None, out: Optional[torch.Tensor] = None, ws: Optiona
     return float(out.item())
 
 
+def boolean_many_workspace_size(res: int, count: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_boolean_many_workspace_size(int(res), int(count), ctypes.byref(sz)),
+               "ldni_boolean_many_workspace_size")
+    return sz.value
+
+
+def boolean_many(As: Sequence[LDNI], Bs: Sequence[LDNI], op, eps: float = 0.0, stream=None,
+                 outs: Optional[Sequence[LDNI]] = None, ws: Optional[torch.Tensor] = None,
+                 infos: Optional[torch.Tensor] = None, sync: bool = True) -> List[LDNI]:
+    """A[j] op B[j] for every j (all on one grid) in one set of launches."""
+    lib = _lib.load()
+    count = len(As)
+    grid = As[0].grid
+    for X in list(As) + list(Bs):
+        if X.grid != grid:
+            raise _lib.LDNIError(-2, "boolean_many")
+    opc = OPS[op] if isinstance(op, str) else int(op)
+    if outs is None:
+        outs = [empty_layers(grid, A.axis, A.capacity + B.capacity) for A, B in zip(As, Bs)]
+    if ws is None:
+        ws = torch.empty(boolean_many_workspace_size(grid.res, count), dtype=torch.uint8, device="cuda")
+    if infos is None:
+        infos = torch.zeros(count, _lib.INFO_BYTES // 8, dtype=torch.int64, device="cuda")
+    arr = lambda xs: (_CLayers * count)(*[x.c() for x in xs])
+    la, lb, lo = arr(As), arr(Bs), arr(outs)
+    g = grid.c()
+    _lib.check(lib.ldni_boolean_many(count, la, lb, ctypes.byref(g), opc, float(eps), lo, infos.data_ptr(),
+                                     ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "ldni_boolean_many")
+    if sync:
+        h = infos.cpu().numpy()
+        for j, o in enumerate(outs):
+            st = int(h[j, 3]) & 0xFFFFFFFF
+            _raise_status(st, "ldni_boolean_many")
+            if st & _lib.ST_ODD:
+                raise _lib.LDNIError(-3, "ldni_boolean_many")
+            o.n = int(h[j, 0])
+    return list(outs)
+
+
+def volume_many_workspace_size(res: int, count: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_volume_many_workspace_size(int(res), int(count), ctypes.byref(sz)),
+               "ldni_volume_many_workspace_size")
+    return sz.value
+
+
+def volume_many(Ls: Sequence[LDNI], stream=None, out: Optional[torch.Tensor] = None,
+                ws: Optional[torch.Tensor] = None, infos: Optional[torch.Tensor] = None, sync: bool = True):
+    """Volumes of several images of one grid in one launch."""
+    lib = _lib.load()
+    count = len(Ls)
+    grid = Ls[0].grid
+    if out is None:
+        out = torch.zeros(count, dtype=torch.float64, device="cuda")
+    if ws is None:
+        ws = torch.empty(volume_many_workspace_size(grid.res, count), dtype=torch.uint8, device="cuda")
+    if infos is None:
+        infos = torch.zeros(count, _lib.INFO_BYTES // 8, dtype=torch.int64, device="cuda")
+    arr = (_CLayers * count)(*[x.c() for x in Ls])
+    g = grid.c()
+    _lib.check(lib.ldni_volume_many(count, arr, ctypes.byref(g), out.data_ptr(), infos.data_ptr(), ws.data_ptr(),
+                                    ws.numel(), _stream_ptr(stream)), "ldni_volume_many")
+    if not sync:
+        return out
+    h = infos.cpu().numpy()
+    if any((int(h[j, 3]) & 0xFFFFFFFF) & _lib.ST_ODD for j in range(count)):
+        raise _lib.LDNIError(-3, "ldni_volume_many")
+    return [float(v) for v in out.cpu().numpy()]
+
+
 # ---- one-pass sampling with learned capacity -------------------------------------
 
 def auto_stride(nt: int, budget: int = 65536) -> int:

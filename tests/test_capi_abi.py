@@ -73,7 +73,7 @@ def test_tuning_knobs_validate_on_host():
     lib = _lib.load()
     t = _lib.Tuning()
     assert lib.ldni_get_tuning(ctypes.byref(t)) == 0
-    assert (t.bool_tile_rays, t.bool_stage_samples, t.tri_blocks_per_sm, t.bool_split) == (1024, 4096, 16, -1)
+    assert (t.bool_tile_rays, t.bool_stage_samples, t.tri_blocks_per_sm, t.bool_split) == (256, 4096, 16, -1)
     for bad in (_lib.Tuning(300, 4096, 16, 0), _lib.Tuning(1024, 20000, 16, 0), _lib.Tuning(1024, 4096, 0, 0),
                 _lib.Tuning(1024, 4096, 16, 2)):
         assert lib.ldni_set_tuning(ctypes.byref(bad)) == -1
@@ -81,4 +81,4 @@ def test_tuning_knobs_validate_on_host():
     assert lib.ldni_set_tuning(ctypes.byref(good)) == 0
     assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and (t.bool_tile_rays, t.tri_blocks_per_sm) == (512, 4)
     assert lib.ldni_set_tuning(None) == 0
-    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 1024
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 256

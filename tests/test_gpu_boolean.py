@@ -156,3 +156,84 @@ def test_tuner_picks_a_valid_choice(ldni, tmp_path, monkeypatch):
         assert s["choice"]["tri_blocks_per_sm"] in (4, 16)
     finally:
         tune.set(**prev)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+def test_many_images_in_one_call(ldni, split):
+    """ldni_boolean_many and ldni_volume_many over the three images equal
+    the one-image calls bit for bit."""
+    from paper_1009_0794_gb300 import tune
+    prev = tune.set(bool_split=split)
+    try:
+        (fv, ft), (kv, kt) = M.flower(96, 96), M.torus_knot(n_ring=128, n_side=16)
+        LA, LB = _pairs(ldni, (fv, ft), (kv, kt), 130)
+        for op in ("union", "inter", "diff"):
+            many = ldni.boolean_many(LA, LB, op, eps=1e-5)
+            for a in range(3):
+                one = ldni.boolean(LA[a], LB[a], op, eps=1e-5)
+                assert bit_equal(many[a].numpy(), one.numpy())
+            vols = ldni.volume_many(many)
+            assert vols == [ldni.volume(U) for U in many]
+    finally:
+        tune.set(**prev)
+
+
+def _ldni_from_rays(ldni, grid, rays, seed):
+    """An LDNI whose ray p holds the sorted depths rays[p] (other rays empty),
+    with seeded unit normals and distinct triangle ids."""
+    N = grid.res * grid.res
+    counts = np.zeros(N, np.int64)
+    counts[:len(rays)] = [len(r) for r in rays]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int32)
+    depth = np.concatenate([np.asarray(r, np.float32) for r in rays] + [np.zeros(0, np.float32)])
+    n = depth.size
+    rng = np.random.default_rng(seed)
+    nrm = rng.normal(size=(n, 3)).astype(np.float32)
+    nrm /= np.linalg.norm(nrm, axis=1, keepdims=True)
+    tri = np.arange(n, dtype=np.int32) + 1000 * (seed + 1)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    L = ldni.LDNI(grid, 0, t(off), t(depth), t(nrm[:, 0]), t(nrm[:, 1]), t(nrm[:, 2]), t(tri), n)
+    return L, {"offsets": off.astype(np.int64), "depth": depth, "nrm": nrm, "tri": tri}
+
+
+def _tie_cases(rng):
+    """Every pair of intervals with endpoints in {0, 1, 2, 3} (ties, touching,
+    nested, zero-length), single intervals against nothing, and random
+    multi-interval rays with shared depths."""
+    iv = [(x, y) for x in range(4) for y in range(x, 4)]
+    A, B = [], []
+    for a in iv:
+        for b in iv:
+            A.append([0.25 * a[0], 0.25 * a[1]])
+            B.append([0.25 * b[0], 0.25 * b[1]])
+    for a in iv:
+        A.append([0.25 * a[0], 0.25 * a[1]]); B.append([])
+        A.append([]); B.append([0.25 * a[0], 0.25 * a[1]])
+    A.append([]); B.append([])
+    for _ in range(300):
+        na, nb = 2 * rng.integers(0, 4), 2 * rng.integers(0, 4)
+        A.append(sorted(0.25 * rng.integers(0, 6, na)))
+        B.append(sorted(0.25 * rng.integers(0, 6, nb)))
+    return A, B
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("tile", [256, 1024])
+def test_interval_ties_against_oracle(ldni, split, tile):
+    """All tie and touching configurations of one interval per operand (the
+    closed-form path) and random multi-interval rays (the general merge),
+    every operation, eps 0 and 0.3, against the oracle bit for bit."""
+    from paper_1009_0794_gb300 import tune
+    prev = tune.set(bool_split=split, bool_tile_rays=tile, bool_stage_samples=4096)
+    try:
+        ra, rb = _tie_cases(np.random.default_rng(5))
+        grid = ldni.Grid.cube(O3, 1.0, 24)
+        LA, hA = _ldni_from_rays(ldni, grid, ra, 1)
+        LB, hB = _ldni_from_rays(ldni, grid, rb, 2)
+        for op in ("union", "inter", "diff"):
+            for eps in (0.0, 0.3):
+                got = ldni.boolean(LA, LB, op, eps=eps).numpy()
+                ref = oracle.boolean(hA, hB, op, eps=eps)
+                assert bit_equal(got, ref), (op, eps)
+    finally:
+        tune.set(**prev)
