@@ -42,6 +42,25 @@ def _dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(value: float, dist=None) -> float:
+    """The largest value over all ranks (each rank times its own replica;
+    the job takes as long as its slowest rank).  Works with nccl (a CUDA
+    tensor) and gloo (a CPU tensor)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(value)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_step: float, steps: int, max_ms: float) -> float:
+    """Units per second of the whole job: every rank processes its own
+    replica of the step (weak scaling), timed by the slowest rank."""
+    return world * units_per_step * steps / (max_ms * 1e-3)
+
+
 def _meshes():
     import meshgen
     return meshgen.scale_sphere(), meshgen.torus_knot(2, 3, 0.25, 0.1, 0.035, 256, 32)
@@ -399,11 +418,7 @@ def run_ours(args):
     clk = clocks.stop()
     launches = launches_per_step * steps
     step_ms = [st_b[k].elapsed_time(st_e[k]) for k in range(steps)]
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(float(sum(step_ms)), dist)
     main_plan.finish()  # raises if any step overflowed or mis-snapped
 
     # per-kernel averages over the same number of profiled replays
@@ -421,8 +436,8 @@ def run_ours(args):
     dk_ms = per_kernel[dominant]
 
     rays_per_step = 3 * RES * RES
-    value = ws * rays_per_step * steps / (total_ms * 1e-3)
-    samples_per_s = ws * sum(n_sphere) * steps / (total_ms * 1e-3)
+    value = whole_job_rate(ws, rays_per_step, steps, total_ms)
+    samples_per_s = whole_job_rate(ws, sum(n_sphere), steps, total_ms)
 
     # end to end through the public API from pinned host buffers
     e2e = None if args.no_e2e else run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step,

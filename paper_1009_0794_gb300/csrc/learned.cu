@@ -466,7 +466,10 @@ __global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict_
 
 // ---- gather ----------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info) {
+// (n_over, if given: the number of redone tiles, counted by the thread of each
+// tile's first ray; cleared before the launch.)
+__global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info,
+                                                          int *n_over) {
     const int a = ax_lo + blockIdx.y;
     const int *off = pick3(o.offsets, a);
     float *D = pick3(o.depth, a);
@@ -478,10 +481,31 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
     const int *over = pick3(o.over, a);
     const int *kc = pick3(o.kcap, a);
     const long long *sb = pick3(o.slab_base, a);
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
-         p += (long long)gridDim.x * blockDim.x) {
-        const long long b = off[p];
-        const long long e = off[p + 1];
+    const float4 *NRM = o.nrm;
+    const int lane = threadIdx.x & 31;
+    // a warp takes 32 consecutive rays, which lie in one tile (tiles are
+    // multiples of 32 rays): the tile's values are loaded once per warp
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nrays;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long p = base + lane;
+        const bool act = p < nrays;
+        const int tile = (int)(base >> kTileBits);
+        int t_over = 0, kt = 0;
+        long long tbase = 0;
+        if (lane == 0) {
+            t_over = over[tile];
+            kt = kc[tile];
+            tbase = sb[tile];
+            if (n_over && (base & (kTilePix - 1)) == 0 && t_over) atomicAdd(n_over, 1);
+        }
+        t_over = __shfl_sync(0xffffffffu, t_over, 0);
+        kt = __shfl_sync(0xffffffffu, kt, 0);
+        tbase = __shfl_sync(0xffffffffu, tbase, 0);
+        const long long b = act ? off[p] : 0;
+        long long e = __shfl_down_sync(0xffffffffu, b, 1);
+        if (lane == 31 && act) e = off[p + 1];
+        if (!act) continue;
+        if (lane < 31 && p + 1 == nrays) e = off[p + 1];  // the last ray of the image
         const int c = (int)(e - b);
         if (c & 1) {
             atomicAdd(&info->odd_rays, 1u);
@@ -492,38 +516,41 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             set_status(info, LDNI_ST_CAPACITY);
             continue;
         }
-        const int tile = (int)(p >> kTileBits);
-        if (over[tile]) {  // filled exactly by the redo pass: order in place
+        if (t_over) {  // filled exactly by the redo pass: order in place
             sort_ray_global(b, e, D, Tr, X, Y, Z);
             continue;
         }
-        const int kt = kc[tile];
         if (c > kt) {  // cannot happen for a tile that did not overflow
             set_status(info, LDNI_ST_CAPACITY);
             continue;
         }
-        const long long s0 = sb[tile] + (p & (kTilePix - 1)) * kt;
-        const float4 *NRM = o.nrm;
+        const long long s0 = tbase + (p & (kTilePix - 1)) * kt;
         if (c == 2) {  // the common case: everything in registers
-            int2 v0 = o.slab[s0], v1 = o.slab[s0 + 1];
+            int2 v0, v1;
+            if ((s0 & 1) == 0) {  // the slot pair is one 16-byte record
+                const int4 v = *reinterpret_cast<const int4 *>(o.slab + s0);
+                v0 = make_int2(v.x, v.y);
+                v1 = make_int2(v.z, v.w);
+            } else {
+                v0 = o.slab[s0];
+                v1 = o.slab[s0 + 1];
+            }
             if (key_less(__int_as_float(v1.x), v1.y, __int_as_float(v0.x), v0.y)) {
                 const int2 w = v0;
                 v0 = v1;
                 v1 = w;
             }
             const float4 q0 = NRM[v0.y], q1 = NRM[v1.y];
-            const float x0 = q0.x, y0 = q0.y, z0 = q0.z;
-            const float x1 = q1.x, y1 = q1.y, z1 = q1.z;
             D[b] = __int_as_float(v0.x);
             D[b + 1] = __int_as_float(v1.x);
             Tr[b] = v0.y;
             Tr[b + 1] = v1.y;
-            X[b] = x0;
-            X[b + 1] = x1;
-            Y[b] = y0;
-            Y[b + 1] = y1;
-            Z[b] = z0;
-            Z[b + 1] = z1;
+            X[b] = q0.x;
+            X[b + 1] = q1.x;
+            Y[b] = q0.y;
+            Y[b + 1] = q1.y;
+            Z[b] = q0.z;
+            Z[b + 1] = q1.z;
             continue;
         }
         for (int x = 0; x < c; ++x) {  // copy, then order in place
@@ -537,17 +564,6 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
         }
         sort_ray_global(b, e, D, Tr, X, Y, Z);
     }
-}
-
-__global__ void count_overflow(int ntiles, int ax_lo, int naxes, LImg o, int *n_over) {
-    __shared__ int sh;
-    if (threadIdx.x == 0) sh = 0;
-    __syncthreads();
-    int c = 0;
-    for (int k = threadIdx.x; k < ntiles * naxes; k += blockDim.x) c += pick3(o.over, ax_lo + k / ntiles)[k % ntiles];
-    atomicAdd(&sh, c);
-    __syncthreads();
-    if (threadIdx.x == 0) *n_over = sh;
 }
 
 // per-tile training targets: log1p of the largest ray count in the tile
@@ -701,6 +717,7 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     o.any_over = w.any_over;
 
     if (cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    if (overflow_tiles && cudaMemsetAsync(overflow_tiles, 0, sizeof(int32_t), s) != cudaSuccess) return LDNI_ECUDA;
     if (mlp && nt > 0)
         LDNI_LAUNCH(K_FEATURES, s,
                     features_kernel<<<dim3(feature_blocks(nt, feature_stride), naxes), kThreads, 0, s>>>(
@@ -738,12 +755,12 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     if (rc != LDNI_OK) return rc;
     if (nt > 0) {
         LDNI_LAUNCH(K_REDO, s,
-                    redo_kernel<<<4 * num_sms(), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o,
-                                                                   w.big_q, w.big_n, 3 * num_sms(), info));
+                    // a small grid: the launch is usually a no-op (no tile overflowed)
+                    redo_kernel<<<num_sms() + num_sms() / 2, kThreads, 0, s>>>(
+                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o, w.big_q, w.big_n, num_sms(), info));
     }
     LDNI_LAUNCH(K_GATHER, s,
-                gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info));
-    if (overflow_tiles) LDNI_LAUNCH(K_GATHER, s, count_overflow<<<1, 256, 0, s>>>(ntiles, ax_lo, naxes, o, overflow_tiles));
+                gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info, overflow_tiles));
     return cuda_status();
 }
 

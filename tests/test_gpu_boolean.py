@@ -237,3 +237,30 @@ def test_interval_ties_against_oracle(ldni, split, tile):
                 assert bit_equal(got, ref), (op, eps)
     finally:
         tune.set(**prev)
+
+
+def test_hand_worked_cases(ldni):
+    """The CUDA Boolean (both launch forms) on the hand-worked cases of
+    tests/golden/boolean_segments.txt, each case on its own ray."""
+    from golden_cases import cases, expected, ray
+    from paper_1009_0794_gb300 import tune
+    cs = cases()
+    grid = ldni.Grid.cube(O3, 1.0, 1)
+    for split in (0, 1):
+        prev = tune.set(bool_split=split)
+        try:
+            for c in cs:
+                A, B = ray(c["A"], 1, 1), ray(c["B"], 100, 2)
+                LA, _ = _ldni_from_rays(ldni, grid, [c["A"]], 1)
+                LB, _ = _ldni_from_rays(ldni, grid, [c["B"]], 2)
+                # same normals and ids as the dicts
+                for L, H in ((LA, A), (LB, B)):
+                    if H["depth"].size:
+                        L.nx.copy_(torch.from_numpy(H["nrm"][:, 0]))
+                        L.ny.copy_(torch.from_numpy(H["nrm"][:, 1]))
+                        L.nz.copy_(torch.from_numpy(H["nrm"][:, 2]))
+                        L.tri.copy_(torch.from_numpy(H["tri"]))
+                got = ldni.boolean(LA, LB, c["op"], eps=c["eps"]).numpy()
+                assert bit_equal(got, expected(c, A, B)), c["name"]
+        finally:
+            tune.set(**prev)
