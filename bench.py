@@ -461,12 +461,15 @@ def run_ours(args):
     ab = algorithmic_bytes(dominant, len(sv), len(st), RES, n_sphere, [L.n for L in K], n_union)
     achieved = ab / (dk_avg_ms * 1e-3) / 1e9
     traffic = None
+    ncu_note = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tj = _json.load(fh)
         name = lib.ldni_kernel_name(dominant).decode()
         if name in tj and tj[name].get("source_hash") == _source_hash():
             traffic = tj[name]["bytes_per_launch"]
+            ncu_note = {k: tj[name][k] for k in ("alu_pipe_pct", "issue_active_pct", "dram_pct") if k in tj[name]}
+            ncu_note["from"] = "profiles/traffic.json (ncu --set full of this kernel, same sources)"
     except Exception:
         traffic = None
     stages = {}
@@ -494,7 +497,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "kernel": lib.ldni_kernel_name(dominant).decode(), "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dk_avg_ms},
+                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dk_avg_ms, "ncu": ncu_note},
         "gpu_launches": launches,
         "clocks": clk,
         "stages_ms_per_step": stages,
