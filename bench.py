@@ -315,6 +315,35 @@ def _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, reps):
     return res
 
 
+def _node_classify(ldni, lib, U, flush, reps):
+    """Grid-node classification (Section 5.1, Step 1) of the union's three
+    images: res^3 nodes, one CUDA graph replay per measurement, L2 flushed
+    before each.  Bytes: the three images read, the bit volume written."""
+    import torch
+    res = U[0].grid.res
+    out = torch.empty(res, res, (res + 31) // 32, dtype=torch.int32, device="cuda")
+    sz = __import__("ctypes").c_size_t(0)
+    lib.ldni_classify_nodes_workspace_size(res, __import__("ctypes").byref(sz))
+    ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    info = ldni.new_info()
+    g, nl = _capture(lib, lambda: ldni.classify_nodes(U, out=out, ws=ws, info=info, sync=False))
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    nbytes = 3 * 4.0 * (res * res + 1) + 4.0 * sum(L.n for L in U) + res * res * 4.0 * ((res + 31) // 32)
+    return {"workload": f"{res}^3 nodes of the union's three images (2-of-3 vote)", "ms": ms,
+            "nodes_per_s": res ** 3 / (ms * 1e-3), "algorithmic_bytes": nbytes, "gbs": nbytes / (ms * 1e-3) / 1e9,
+            "kernels": nl}
+
+
 def _events(n):
     """n timing events with their CUDA handles created (torch creates an
     event lazily at its first record)."""
@@ -392,6 +421,7 @@ def run_ours(args):
 
     learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)))
     learned["train"] = train_meta
+    next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
 
     # timed region: K graph replays, per-step events, L2 flushed between steps
     steps = args.steps
@@ -502,6 +532,7 @@ def run_ours(args):
         "clocks": clk,
         "stages_ms_per_step": stages,
         "e2e": e2e,
+        "next_rows": next_rows,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_meshes(), budget_s=args.cpu_budget)

@@ -383,6 +383,27 @@ int ldni_volume_many_workspace_size(int32_t res, int32_t count, size_t *bytes_ho
 int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldni_grid_t *grid, double *vols, ldni_info_t *infos,
                      void *ws, size_t ws_bytes, void *stream);
 
+/* ---- grid-node classification (Section 5.1, Step 1) -------------------- */
+
+/* Workspace bytes for ldni_classify_nodes at resolution res (<= 4096):
+ * three bit volumes of res^2 * ceil(res / 32) words. */
+int ldni_classify_nodes_workspace_size(int32_t res, size_t *bytes_host);
+
+/*
+ * Inside/outside status of the res^3 grid nodes where the rays of the three
+ * images meet (Definition 3).  Node (i, j, k) lies at (c_x(i), c_y(j),
+ * c_z(k)), c_a(t) = fl32(o_a + fl32((t + 1/2) * h)), h = fl32(width / res).
+ * Image a puts the node inside when an odd number of the samples of its ray
+ * through the node are strictly below c_a; the node is inside when at least
+ * two images do (Section 5.1, Step 1).
+ *   L      : host array of the three images x, y, z of one solid on `grid`.
+ *   inside : device uint32[res][res][ceil(res/32)], bit (i % 32) of word
+ *            [k][j][i / 32] = node (i, j, k); bits past res are 0.
+ * Odd rays set LDNI_ST_ODD in info.
+ */
+int ldni_classify_nodes(const ldni_layers_t *L, const ldni_grid_t *grid, uint32_t *inside, ldni_info_t *info,
+                        void *ws, size_t ws_bytes, void *stream);
+
 /* ---- adjoint of depth and volume ---------------------------------------- */
 
 /*
@@ -434,7 +455,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -96,6 +96,8 @@ SIGNATURES = {
     "ldni_boolean_many": (ctypes.c_int, [_I32, _P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "ldni_volume_many_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
     "ldni_volume_many": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
+    "ldni_classify_nodes": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
     "ldni_get_tuning": (ctypes.c_int, [_P]),
     "ldni_set_tuning": (ctypes.c_int, [_P]),
     "ldni_sample_batch_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_SZ)]),

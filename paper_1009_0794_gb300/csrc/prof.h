@@ -37,7 +37,8 @@ enum KernelId : int {
     K_MLP = 21,
     K_GRAD = 22,
     K_BATCH = 23,
-    K_NUM = 24
+    K_NODES = 24,
+    K_NUM = 25
 };
 
 struct ProfState {

@@ -439,6 +439,47 @@ def sample_learned(verts, tris, grid: Grid, axis="all", net=None, layers: int = 
     return outs if n_img > 1 else outs[0]
 
 
+# ---- grid-node classification (Section 5.1, Step 1) -----------------------------
+
+def classify_nodes(Ls: Sequence[LDNI], stream=None, out: Optional[torch.Tensor] = None,
+                   ws: Optional[torch.Tensor] = None, info: Optional[torch.Tensor] = None,
+                   sync: bool = True) -> torch.Tensor:
+    """Inside bits of the res^3 grid nodes from the three images of one
+    solid (2-of-3 vote): int32 tensor [res(k), res(j), ceil(res/32)] whose
+    bit i % 32 of word [k, j, i // 32] is node (i, j, k)."""
+    lib = _lib.load()
+    grid = Ls[0].grid
+    if len(Ls) != 3 or any(L.grid != grid for L in Ls) or [L.axis for L in Ls] != [0, 1, 2]:
+        raise _lib.LDNIError(-1, "classify_nodes needs the x, y and z images of one grid")
+    res = grid.res
+    W = (res + 31) // 32
+    if out is None:
+        out = torch.empty(res, res, W, dtype=torch.int32, device="cuda")
+    if ws is None:
+        sz = ctypes.c_size_t(0)
+        _lib.check(lib.ldni_classify_nodes_workspace_size(res, ctypes.byref(sz)), "ldni_classify_nodes_workspace_size")
+        ws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+    if info is None:
+        info = new_info()
+    arr = (_CLayers * 3)(*[L.c() for L in Ls])
+    g = grid.c()
+    _lib.check(lib.ldni_classify_nodes(arr, ctypes.byref(g), out.data_ptr(), info.data_ptr(), ws.data_ptr(),
+                                       ws.numel(), _stream_ptr(stream)), "ldni_classify_nodes")
+    if sync:
+        meta = info_decode(info)
+        _raise_status(meta["status"], "ldni_classify_nodes")
+        if meta["status"] & _lib.ST_ODD:
+            raise _lib.LDNIError(-3, "ldni_classify_nodes")
+    return out
+
+
+def unpack_nodes(words: torch.Tensor, res: int) -> np.ndarray:
+    """Bit words of classify_nodes -> bool array [k, j, i]."""
+    w = words.cpu().numpy().view(np.uint32)
+    bits = (w[..., None] >> np.arange(32, dtype=np.uint32)) & 1
+    return bits.reshape(res, res, -1)[:, :, :res].astype(bool)
+
+
 # ---- adjoint -------------------------------------------------------------------
 
 def depth_vjp(verts: torch.Tensor, tris: torch.Tensor, L: LDNI, grad_depth: torch.Tensor,
