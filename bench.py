@@ -32,7 +32,7 @@ import numpy as np  # noqa: E402
 METRIC = "LDNI rays/s & samples/s at 1024²; learned-sized 1-pass vs exact 2-pass speedup"
 RES = 1024
 WORKLOAD = ("noisy geodesic sphere freq 256 (655,362 verts / 1,310,720 tris, r 0.35, 4-octave radial noise 0.05)"
-            " -> 3 LDNIs at 1024^2 -> union with resident (2,3) torus-knot LDNIs -> volume")
+            " -> 3 LDNIs at 1024^2 -> union with resident (2,3) torus-knot LDNIs -> volume of the union")
 
 
 def _dist_env():

@@ -334,10 +334,14 @@ int ldni_boolean_many_workspace_size(int32_t res, int32_t count, size_t *bytes_h
  * two solids (Definition 3).  A, B, out: host arrays of count layers; infos:
  * device array of count ldni_info_t.  Each result is the one ldni_boolean
  * gives for that pair.
+ * vols: NULL, or device double[count] receiving the volume of each result
+ * as ldni_volume defines it (h^2 times the summed inside lengths), summed
+ * while the result is written (double-float, fixed order; equal to
+ * ldni_volume's value to about 1e-13 relative).
  */
 int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, const ldni_grid_t *grid,
-                      int32_t op, float eps, ldni_layers_t *out, ldni_info_t *infos, void *ws, size_t ws_bytes,
-                      void *stream);
+                      int32_t op, float eps, ldni_layers_t *out, ldni_info_t *infos, double *vols, void *ws,
+                      size_t ws_bytes, void *stream);
 
 /*
  * ldni_boolean without a workspace argument, for callers that cannot

@@ -93,7 +93,7 @@ SIGNATURES = {
     "ldni_depth_vjp": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _P, _P]),
     "ldni_volume_grad": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, ctypes.c_double, _P, _P, _P]),
     "ldni_boolean_many_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
-    "ldni_boolean_many": (ctypes.c_int, [_I32, _P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    "ldni_boolean_many": (ctypes.c_int, [_I32, _P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _P, _SZ, _P]),
     "ldni_volume_many_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
     "ldni_volume_many": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),

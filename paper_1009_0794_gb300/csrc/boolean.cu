@@ -22,6 +22,7 @@
 #include <climits>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "ldni_host.h"
 #include "lookback.cuh"
 
@@ -59,6 +60,7 @@ struct BoolJobs {
     Side B[kMaxJobs];
     Out o[kMaxJobs];
     ldni_info_t *info[kMaxJobs];
+    double *vol[kMaxJobs];  // optional: volume of each result (three-launch form only)
 };
 
 // Truth table of an operation: bit (2 inA + inB) = op(inA, inB).
@@ -690,7 +692,8 @@ __device__ __forceinline__ void put_sample(const Out &o, long long at, float d, 
 // every ray at its offset.
 template <int kR>
 __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const __grid_constant__ BoolJobs J, int op,
-                                                              float eps, const long long *tile_pre, int tpj) {
+                                                              float eps, const long long *tile_pre, int tpj,
+                                                              double *tile_vol) {
     constexpr int kRays = kR * kBoolThreads;
     __shared__ long long sh[kBoolThreads / 32 + 1];
     const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
@@ -726,6 +729,8 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
     }
     const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;
     const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+    const bool want_vol = J.vol[job] != nullptr;
+    DF vacc{0.0f, 0.0f};  // inside lengths of the written result (when its volume is asked for)
     long long at = base;
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
@@ -734,11 +739,14 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
             if (kind == 4) {
                 const long long a0 = ra[k], b0 = rb[k];
                 int src[4];
-                const int c = two_two(op, eps, A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1], src);
+                const float dd[4] = {A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1]};
+                const int c = two_two(op, eps, dd[0], dd[1], dd[2], dd[3], src);
                 for (int m = 0; m < c; ++m) {
                     const bool fb = src[m] >= 2;
                     emit_global(fb, (fb ? b0 : a0) + (src[m] & 1), A, B, op, o, at + m, info);
                 }
+                if (want_vol)
+                    for (int m = 0; m < c; m += 2) vacc = df_add(vacc, df_diff(dd[src[m + 1]], dd[src[m]]));
             } else if (kind == 3) {
                 const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
                 const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
@@ -747,6 +755,8 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
                 merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
                     emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
                     emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
+                    if (want_vol)
+                        vacc = df_add(vacc, df_diff((cb ? B.d + b0 : A.d + a0)[ci], (pb ? B.d + b0 : A.d + a0)[pi]));
                 });
             } else {  // a kept pair of one operand: copy both samples
                 const bool fa = kind == 1;
@@ -766,10 +776,32 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
                 }
                 put_sample(o, at, e0, f * x0, f * y0, f * z0, t0, info);
                 put_sample(o, at + 1, e1, f * x1, f * y1, f * z1, t1, info);
+                if (want_vol) vacc = df_add(vacc, df_diff(e1, e0));
             }
         }
         at += cnt[k];
     }
+    if (!want_vol) return;  // block-uniform
+    // volume of the result: one partial per warp, no block-wide wait
+    // (bool_vol_finish adds them in a fixed order)
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) {
+        const DF y{__shfl_down_sync(0xffffffffu, vacc.hi, o2), __shfl_down_sync(0xffffffffu, vacc.lo, o2)};
+        vacc = df_add(vacc, y);
+    }
+    if ((threadIdx.x & 31) == 0)
+        tile_vol[(size_t)blockIdx.x * (kBoolThreads / 32) + (threadIdx.x >> 5)] = (double)vacc.hi + (double)vacc.lo;
+}
+
+// The volume of each result: its tiles' partials added in a fixed order (one
+// block per job).
+__global__ void __launch_bounds__(kBoolThreads) bool_vol_finish(const __grid_constant__ BoolJobs J,
+                                                                const double *tile_vol, int tpj, double h2) {
+    __shared__ double sh_sum[kBoolThreads];
+    const int job = blockIdx.x;
+    constexpr int kWarps = kBoolThreads / 32;
+    const double sum = fixed_order_sum<kBoolThreads>(tile_vol + (size_t)job * tpj * kWarps, tpj * kWarps, sh_sum);
+    if (threadIdx.x == 0) *J.vol[job] = sum * h2;
 }
 
 // ---- host side ------------------------------------------------------------------
@@ -806,7 +838,7 @@ size_t bool_ws_words(long long N) { return (size_t)((N + kMinTileRays - 1) / kMi
 
 template <int kR>
 int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, void *ws, int budget, bool split,
-                cudaStream_t s) {
+                double h2, cudaStream_t s) {
     constexpr int kRays = kR * kBoolThreads;
     const int tpj = (int)((N + kRays - 1) / kRays);
     const int nblocks = tpj * njobs;
@@ -823,14 +855,17 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
                     bool_tiled<kR><<<nblocks, kBoolThreads, smem, s>>>(N, J, op, eps, words, tpj, njobs, budget));
         return cuda_status();
     }
+    // workspace: tile totals (cleared) | tile prefixes | warp volumes (kBoolThreads / 32 per tile)
     unsigned long long *tile_total = static_cast<unsigned long long *>(ws);
     long long *tile_pre = reinterpret_cast<long long *>(tile_total + nblocks);
+    double *tile_vol = reinterpret_cast<double *>(tile_pre + nblocks);
     if (cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s) != cudaSuccess)
         return LDNI_ECUDA;
     LDNI_LAUNCH(K_BOOL_COUNT, s, bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj));
     LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J));
     LDNI_LAUNCH(K_BOOL_WRITE, s,
-                bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
+                bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj, tile_vol));
+    if (J.vol[0]) LDNI_LAUNCH(K_VOL_PARTIAL, s, bool_vol_finish<<<njobs, kBoolThreads, 0, s>>>(J, tile_vol, tpj, h2));
     return cuda_status();
 }
 
@@ -840,7 +875,8 @@ bool same_grid(const ldni_grid_t *a, const ldni_grid_t *b) {
 }
 
 int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, const ldni_grid_t *grid, int32_t op,
-                 float eps, ldni_layers_t *out, ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
+                 float eps, ldni_layers_t *out, ldni_info_t *infos, double *vols, void *ws, size_t ws_bytes,
+                 void *stream) {
     if (count < 1 || count > kMaxJobs || !A || !B || !out || !infos || !ws || !grid_valid(grid) ||
         op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
         return LDNI_EINVAL;
@@ -851,20 +887,25 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
         J.B[j] = Side{B[j].capacity, B[j].offsets, B[j].depth, B[j].nx, B[j].ny, B[j].nz, B[j].tri_id};
         J.o[j] = Out{out[j].offsets, out[j].depth, out[j].nx, out[j].ny, out[j].nz, out[j].tri_id, out[j].capacity};
         J.info[j] = infos + j;
+        J.vol[j] = vols ? vols + j : nullptr;
     }
     const long long N = (long long)grid->res * grid->res;
-    if (ws_bytes < 2 * sizeof(long long) * (bool_ws_words(N) * count + 1)) return LDNI_EWORKSPACE;
+    size_t need = 0;
+    ldni_boolean_many_workspace_size(grid->res, count, &need);
+    if (ws_bytes < need) return LDNI_EWORKSPACE;
     const ldni_tuning_t tune = current_tuning();
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int budget = tune.bool_stage_samples;
     const int rays = tune.bool_tile_rays;
-    const bool split =
-        tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
+    // the volumes come from the three-launch form's write pass
+    const bool split = vols != nullptr ||
+                       (tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0);
+    const double h = (double)grid->width / (double)grid->res;
     switch (rays) {
-        case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, split, s);
-        case 512: return launch_bool<2>(N, J, count, op, eps, ws, budget, split, s);
-        case 2048: return launch_bool<8>(N, J, count, op, eps, ws, budget, split, s);
-        default: return launch_bool<4>(N, J, count, op, eps, ws, budget, split, s);
+        case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, split, h * h, s);
+        case 512: return launch_bool<2>(N, J, count, op, eps, ws, budget, split, h * h, s);
+        case 2048: return launch_bool<8>(N, J, count, op, eps, ws, budget, split, h * h, s);
+        default: return launch_bool<4>(N, J, count, op, eps, ws, budget, split, h * h, s);
     }
 }
 
@@ -879,9 +920,10 @@ extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
 
 extern "C" int ldni_boolean_many_workspace_size(int32_t res, int32_t count, size_t *bytes) {
     if (!bytes || res < 1 || res > 8192 || count < 1 || count > kMaxJobs) return LDNI_EINVAL;
-    // look-back words and ticket of the one-launch form, or tile totals and
-    // prefixes of the three-launch form, for the smallest tile
-    *bytes = align_up(2 * sizeof(long long) * (bool_ws_words((long long)res * res) * count + 1));
+    // look-back words and ticket of the one-launch form, or tile totals,
+    // tile prefixes and warp volumes of the three-launch form, for the
+    // smallest tile
+    *bytes = align_up(sizeof(long long) * ((2 + kBoolThreads / 32) * bool_ws_words((long long)res * res) * count + 8));
     return LDNI_OK;
 }
 
@@ -890,13 +932,13 @@ extern "C" int ldni_boolean(const ldni_layers_t *A, const ldni_grid_t *grid_a, c
                             void *ws, size_t ws_bytes, void *stream) {
     if (!grid_valid(grid_a) || !grid_valid(grid_b)) return LDNI_EINVAL;
     if (!same_grid(grid_a, grid_b)) return LDNI_EGRID_MISMATCH;
-    return boolean_jobs(1, A, B, grid_a, op, eps, out, info, ws, ws_bytes, stream);
+    return boolean_jobs(1, A, B, grid_a, op, eps, out, info, nullptr, ws, ws_bytes, stream);
 }
 
 extern "C" int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B,
                                  const ldni_grid_t *grid, int32_t op, float eps, ldni_layers_t *out,
-                                 ldni_info_t *infos, void *ws, size_t ws_bytes, void *stream) {
-    return boolean_jobs(count, A, B, grid, op, eps, out, infos, ws, ws_bytes, stream);
+                                 ldni_info_t *infos, double *vols, void *ws, size_t ws_bytes, void *stream) {
+    return boolean_jobs(count, A, B, grid, op, eps, out, infos, vols, ws, ws_bytes, stream);
 }
 
 // ---- Boolean without a caller workspace -------------------------------------

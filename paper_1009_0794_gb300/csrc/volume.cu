@@ -10,6 +10,7 @@
 // widened to FP64 once; the last block to finish adds the block partials in
 // a fixed order.  The result is deterministic for a given device and within
 // about 1e-13 relative of the exact sum.
+#include "dfloat.cuh"
 #include "ldni_host.h"
 
 namespace ldni {
@@ -17,26 +18,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kRaysPerThread = 4;
-
-// s + e == a + b exactly (round-to-nearest FP32 arithmetic, no FMA)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-struct DF {
-    float hi, lo;
-};
-
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-    float s, e;
-    two_sum(x.hi, y.hi, s, e);
-    e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
-    DF r;
-    two_sum(s, e, r.hi, r.lo);
-    return r;
-}
 
 // The images of one call (blockIdx.y = image), all at one resolution.
 struct VolJobs {
@@ -96,42 +77,24 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
             }
         }
     }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        DF y{__shfl_down_sync(0xffffffffu, acc.hi, o), __shfl_down_sync(0xffffffffu, acc.lo, o)};
-        acc = df_add(acc, y);
-    }
-    if (lane == 0) sh[warp] = acc;
-    __syncthreads();
+    const DF t = df_block_sum<kThreads>(acc, sh);
     if (threadIdx.x == 0) {
-        DF t = sh[0];
-        for (int w = 1; w < kThreads / 32; ++w) t = df_add(t, sh[w]);
         partials[blockIdx.x] = (double)t.hi + (double)t.lo;
         __threadfence();
         s_last = atomicAdd(done, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!s_last) return;
-    // last block: FP64 sum of the block partials in a fixed order (each
-    // thread a strided subset, then a fixed tree), loads issued in parallel
+    // last block: FP64 sum of the block partials in a fixed order
     __threadfence();
     __shared__ double shd[kThreads];
-    const volatile double *vp = partials;
-    double sum = 0.0;
-    for (unsigned k = threadIdx.x; k < gridDim.x; k += blockDim.x) sum += vp[k];
-    shd[threadIdx.x] = sum;
-    __syncthreads();
-    for (int w = kThreads / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) shd[threadIdx.x] += shd[threadIdx.x + w];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *J.vol[job] = shd[0] * h2;
+    const double sum = fixed_order_sum<kThreads>(partials, (int)gridDim.x, shd);
+    if (threadIdx.x == 0) *J.vol[job] = sum * h2;
 }
 
 int volume_blocks(long long nrays) {
     long long b = (nrays + (long long)kThreads * kRaysPerThread - 1) / ((long long)kThreads * kRaysPerThread);
-    const long long lim = (long long)num_sms() * 8;  // grid-stride beyond one resident wave
+    const long long lim = (long long)num_sms() * 2;  // few blocks: each ends with a reduction and a fence
     if (b > lim) b = lim;
     return (int)(b > 0 ? b : 1);
 }

@@ -297,8 +297,10 @@ def boolean_many_workspace_size(res: int, count: int) -> int:
 
 def boolean_many(As: Sequence[LDNI], Bs: Sequence[LDNI], op, eps: float = 0.0, stream=None,
                  outs: Optional[Sequence[LDNI]] = None, ws: Optional[torch.Tensor] = None,
-                 infos: Optional[torch.Tensor] = None, sync: bool = True) -> List[LDNI]:
-    """A[j] op B[j] for every j (all on one grid) in one set of launches."""
+                 infos: Optional[torch.Tensor] = None, sync: bool = True,
+                 vols: Optional[torch.Tensor] = None) -> List[LDNI]:
+    """A[j] op B[j] for every j (all on one grid) in one set of launches;
+    with `vols` (device float64[count]) also the volume of every result."""
     lib = _lib.load()
     count = len(As)
     grid = As[0].grid
@@ -316,7 +318,8 @@ def boolean_many(As: Sequence[LDNI], Bs: Sequence[LDNI], op, eps: float = 0.0, s
     la, lb, lo = arr(As), arr(Bs), arr(outs)
     g = grid.c()
     _lib.check(lib.ldni_boolean_many(count, la, lb, ctypes.byref(g), opc, float(eps), lo, infos.data_ptr(),
-                                     ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "ldni_boolean_many")
+                                     vols.data_ptr() if vols is not None else None, ws.data_ptr(), ws.numel(),
+                                     _stream_ptr(stream)), "ldni_boolean_many")
     if sync:
         h = infos.cpu().numpy()
         for j, o in enumerate(outs):

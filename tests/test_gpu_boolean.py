@@ -174,6 +174,10 @@ def test_many_images_in_one_call(ldni, split):
                 assert bit_equal(many[a].numpy(), one.numpy())
             vols = ldni.volume_many(many)
             assert vols == [ldni.volume(U) for U in many]
+            fused = torch.zeros(3, dtype=torch.float64, device="cuda")
+            ldni.boolean_many(LA, LB, op, eps=1e-5, vols=fused)
+            for v, f in zip(vols, fused.cpu().numpy()):
+                assert f == pytest.approx(v, rel=1e-12, abs=1e-15)
     finally:
         tune.set(**prev)
 
