@@ -344,6 +344,49 @@ def _node_classify(ldni, lib, U, flush, reps):
             "kernels": nl}
 
 
+def _other_workloads(ldni, lib, flush, reps):
+    """The batched workload (256 meshes of 1k-200k triangles at 64..512^2,
+    one batch call) and the 64-step union chain of a translated torus at
+    512^2 (three images), each replayed as one CUDA graph."""
+    import torch
+    import meshgen
+    o = (-0.5, -0.5, -0.5)
+
+    def timed(fn):
+        g, nl = _capture(lib, fn)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts)), nl
+
+    batch = meshgen.batch_meshes(256, seed=7)
+    plan = ldni.BatchPlan([(v, t) for v, t, _ in batch], [ldni.Grid.cube(o, 1.0, r) for _, _, r in batch])
+    ms_b, nl_b = timed(plan.run)
+    rays = sum(3 * r * r for _, _, r in batch)
+    tris = sum(len(t) for _, t, _ in batch)
+    base = meshgen.torus(R=0.1, r=0.04, nu=100, nv=100)
+    meshes = [meshgen.translate(base, d) for d in meshgen.helix_offsets(64, seed=11)]
+    grid = ldni.Grid.cube(o, 1.0, 512)
+    cplan = ldni.BatchPlan(meshes, [grid] * 64)
+    cplan.run()
+    parts = cplan.finish()
+    chains = [ldni.union_chain([parts[k][a] for k in range(64)]) for a in range(3)]
+    ms_c, nl_c = timed(lambda: [run() for run, _ in chains])
+    return {"batch_256": {"workload": f"256 meshes, {tris} triangles, resolutions 64..512, three images each, "
+                                      "one batch call", "ms": ms_b, "rays_per_s": rays / (ms_b * 1e-3),
+                          "meshes_per_s": 256 / (ms_b * 1e-3), "kernels": nl_b},
+            "union_chain_64": {"workload": "64 translated 20,000-triangle tori at 512^2: 63 unions per image, "
+                                           "three images", "ms": ms_c, "unions_per_s": 189 / (ms_c * 1e-3),
+                               "kernels": nl_c}}
+
+
 def _events(n):
     """n timing events with their CUDA handles created (torch creates an
     event lazily at its first record)."""
@@ -422,6 +465,7 @@ def run_ours(args):
     learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)))
     learned["train"] = train_meta
     next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
+    other = _other_workloads(ldni, lib, flush, 5)
 
     # timed region: K graph replays, per-step events, L2 flushed between steps
     steps = args.steps
@@ -533,6 +577,7 @@ def run_ours(args):
         "stages_ms_per_step": stages,
         "e2e": e2e,
         "next_rows": next_rows,
+        "other_workloads": other,
     }
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(*_meshes(), budget_s=args.cpu_budget)

@@ -459,7 +459,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -291,6 +291,32 @@ def box(lo, hi):
     return _finish(v, f)
 
 
+def slab_stack(k: int, axis: int = 0, seed: int = 0, lo: float = -0.45, hi: float = 0.45):
+    """k disjoint thin boxes stacked along ``axis`` inside [lo, hi], each with
+    seeded cross-section extents, so that a ray along ``axis`` meets the two
+    faces of every box over its pixel: up to 2k samples per ray, varying
+    across the image."""
+    rng = np.random.default_rng(seed)
+    step = (hi - lo) / k
+    parts = []
+    for m in range(k):
+        a0 = lo + m * step
+        blo = np.empty(3)
+        bhi = np.empty(3)
+        blo[axis], bhi[axis] = a0 + 0.2 * step, a0 + 0.7 * step
+        for b in range(3):
+            if b == axis:
+                continue
+            c = rng.uniform(-0.1, 0.1)
+            w = rng.uniform(0.2, 0.4)
+            blo[b], bhi[b] = c - w, c + w
+        parts.append(box(blo, bhi))
+    verts = np.concatenate([v for v, _ in parts])
+    offs = np.cumsum([0] + [len(v) for v, _ in parts[:-1]])
+    tris = np.concatenate([t + o for (_, t), o in zip(parts, offs)])
+    return verts, tris.astype(np.int32)
+
+
 def octahedron(center, c):
     """Regular octahedron with vertices center +- c e_k."""
     ce = np.asarray(center, dtype=np.float64)

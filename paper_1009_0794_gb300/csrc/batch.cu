@@ -19,7 +19,8 @@ struct Tables {
     long long *chunk_prefix;  // [3 count + 1]  scan chunks
     long long *count_base;    // [3 count]      start of the image's counts
     long long *big;           // queued big (item, triangle, image): item << 34 | tri << 2 | a
-    int *big_n;
+    long long qcap;
+    int *big_n;               // counts of the queue's two ends
 };
 
 __device__ __forceinline__ int find(const long long *prefix, int n, long long x) {  // prefix[k] <= x < prefix[k+1]
@@ -44,26 +45,45 @@ __device__ __forceinline__ GridDev grid_dev(const ldni_grid_t &g) {
     return d;
 }
 
-// one block: prefix tables of the batch
-__global__ void setup_kernel(const ldni_batch_item_t *items, int count, Tables T) {
-    if (threadIdx.x != 0) return;
-    long long tri = 0, ray = 0, chunk = 0, cbase = 0;
-    for (int m = 0; m < count; ++m) {
-        T.tri_prefix[m] = tri;
-        tri += items[m].nt;
-        const long long N = (long long)items[m].grid.res * items[m].grid.res;
-        for (int a = 0; a < 3; ++a) {
-            T.ray_prefix[3 * m + a] = ray;
-            T.chunk_prefix[3 * m + a] = chunk;
-            T.count_base[3 * m + a] = cbase;
-            ray += N;
-            chunk += (N + kScanChunk - 1) / kScanChunk;
-            cbase += (N + 63) / 64 * 64;
+// One block builds the prefix tables of the batch, kThreads items at a time:
+// per item its triangles, and per image its rays, scan chunks and counts
+// (padded to 64 ints); the images of an item have the same size.
+__global__ void __launch_bounds__(kThreads) setup_kernel(const ldni_batch_item_t *items, int count, Tables T) {
+    __shared__ long long sh[4][kThreads / 32 + 1];
+    __shared__ long long carry[4];
+    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+    __syncthreads();
+    for (int m0 = 0; m0 < count; m0 += kThreads) {
+        const int m = m0 + threadIdx.x;
+        long long v[4] = {0, 0, 0, 0};  // triangles, rays, chunks, count ints of one image
+        if (m < count) {
+            const long long N = (long long)items[m].grid.res * items[m].grid.res;
+            v[0] = items[m].nt;
+            v[1] = N;
+            v[2] = (N + kScanChunk - 1) / kScanChunk;
+            v[3] = (N + 63) / 64 * 64;
         }
+        long long ex[4], tot[4];
+        ex[0] = block_exclusive_scan<kThreads>(v[0], sh[0], &tot[0]);
+#pragma unroll
+        for (int q = 1; q < 4; ++q) ex[q] = block_exclusive_scan<kThreads>(3 * v[q], sh[q], &tot[q]);
+        if (m < count) {
+            T.tri_prefix[m] = carry[0] + ex[0];
+            for (int a = 0; a < 3; ++a) {
+                T.ray_prefix[3 * m + a] = carry[1] + ex[1] + a * v[1];
+                T.chunk_prefix[3 * m + a] = carry[2] + ex[2] + a * v[2];
+                T.count_base[3 * m + a] = carry[3] + ex[3] + a * v[3];
+            }
+        }
+        __syncthreads();  // every thread has read the carries
+        if (threadIdx.x < 4) carry[threadIdx.x] += tot[threadIdx.x];
+        __syncthreads();
     }
-    T.tri_prefix[count] = tri;
-    T.ray_prefix[3 * count] = ray;
-    T.chunk_prefix[3 * count] = chunk;
+    if (threadIdx.x == 0) {
+        T.tri_prefix[count] = carry[0];
+        T.ray_prefix[3 * count] = carry[1];
+        T.chunk_prefix[3 * count] = carry[2];
+    }
 }
 
 template <bool kFill>
@@ -94,7 +114,8 @@ __device__ __forceinline__ void batch_axis(const ldni_batch_item_t &it, int m, c
     const int kind = setup_axis<A, kFill>(Tv, res, S);
     if (kind == kNone) return;
     if (kind == kBig) {
-        if (!kFill) T.big[atomicAdd(T.big_n, 1)] = ((long long)m << 34) | ((long long)t << 2) | A;
+        if (!kFill)
+            enqueue_big(T.big, T.qcap, T.big_n, ((long long)m << 34) | ((long long)t << 2) | A, (long long)S.w * S.h);
         return;
     }
     int *cnt = counts + T.count_base[3 * m + A];
@@ -141,29 +162,28 @@ __global__ void __launch_bounds__(kThreads) batch_tri_pass(const ldni_batch_item
 
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) batch_big(const ldni_batch_item_t *items, Tables T, int *counts,
-                                                      ldni_info_t *infos) {
-    const int nq = *T.big_n;
-    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
-        const long long code = T.big[e];
+                                                      int huge_blocks, ldni_info_t *infos) {
+    for_each_big(T.big, T.qcap, T.big_n, (int)blockIdx.x, (int)gridDim.x, huge_blocks,
+                 [&](long long code, int first, int step) {
         const int m = (int)(code >> 34), t = (int)((code >> 2) & 0xFFFFFFFF), a = (int)(code & 3);
         const ldni_batch_item_t &it = items[m];
         const GridDev g = grid_dev(it.grid);
         TriView Tv;
-        if (load_tri(it.verts, it.tris, t, (int)it.nv, g, Tv)) continue;
+        if (load_tri(it.verts, it.tris, t, (int)it.nv, g, Tv)) return;
         Setup64 S;
         int i0, i1, j0, j1;
-        if (!setup_big(Tv, a, g.res, S, i0, i1, j0, j1)) continue;
+        if (!setup_big(Tv, a, g.res, S, i0, i1, j0, j1)) return;
         float3 n = make_float3(0.f, 0.f, 0.f);
         if (kFill) face_normal(Tv.p[0], Tv.p[1], Tv.p[2], n.x, n.y, n.z);
         int *cnt = counts + T.count_base[3 * m + a];
         const int w = i1 - i0 + 1;
         const long long npx = (long long)w * (j1 - j0 + 1);
-        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+        for (long long k = first; k < npx; k += step) {
             const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
             if (S.inside(i, j))
                 batch_emit<kFill>(it, a, (long long)j * g.res + i, kFill ? S.depth(i, j) : 0.0f, t, n, cnt, infos + m);
         }
-    }
+    });
 }
 
 // Scan of every image's counts: chunks of all images in one launch; the
@@ -216,23 +236,44 @@ __global__ void __launch_bounds__(kThreads) batch_scan(const ldni_batch_item_t *
     }
 }
 
+// Ordering of every ray of the batch as in the single-mesh sampling: a warp
+// takes 32 consecutive rays of the batch; its first lane finds the image of
+// the first ray, and the others step forward from there.
 __global__ void __launch_bounds__(kThreads) batch_sort(const ldni_batch_item_t *items, int count, Tables T,
                                                        ldni_info_t *infos) {
+    __shared__ SortStage stage[kThreads / 32];
     const long long total = T.ray_prefix[3 * count];
-    for (long long gr = blockIdx.x * (long long)blockDim.x + threadIdx.x; gr < total;
-         gr += (long long)gridDim.x * blockDim.x) {
-        const int img = find(T.ray_prefix, 3 * count, gr);
+    const int lane = threadIdx.x & 31;
+    SortStage &st = stage[threadIdx.x >> 5];
+    const auto in_place = [](long long, long long b, const RayOut &o) { return InPlace{o, b}; };
+    for (long long wb = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); wb < total;
+         wb += (long long)gridDim.x * blockDim.x) {
+        int img = lane == 0 ? find(T.ray_prefix, 3 * count, wb) : 0;
+        img = __shfl_sync(0xffffffffu, img, 0);
+        const long long gr = wb + lane;
+        const bool act = gr < total;
+        if (act)
+            while (gr >= T.ray_prefix[img + 1]) ++img;
         const int m = img / 3, a = img % 3;
-        const long long p = gr - T.ray_prefix[img];
-        const ldni_layers_t &L = items[m].out[a];
-        const long long b = L.offsets[p];
-        long long e = L.offsets[p + 1];
-        if ((e - b) & 1) {
-            atomicAdd(&infos[m].odd_rays, 1u);
-            set_status(infos + m, LDNI_ST_ODD);
+        RayOut r{};
+        long long b = 0;
+        int n = 0;
+        if (act) {
+            const ldni_layers_t &L = items[m].out[a];
+            r = RayOut{L.depth, L.tri_id, L.nx, L.ny, L.nz};
+            const long long p = gr - T.ray_prefix[img];
+            b = L.offsets[p];
+            long long e = L.offsets[p + 1];
+            if ((e - b) & 1) {
+                atomicAdd(&infos[m].odd_rays, 1u);
+                set_status(infos + m, LDNI_ST_ODD);
+            }
+            if (e > L.capacity) e = L.capacity;
+            if (e - b >= 2) n = (int)(e - b);
         }
-        if (e > L.capacity) e = L.capacity;
-        if (e - b >= 2) sort_ray_global(b, e, L.depth, L.tri_id, L.nx, L.ny, L.nz);
+        // the rays of a warp may belong to two or more images: each is
+        // ordered with the arrays of its own lane
+        order_warp_rays<false>(b, n, b, in_place, r, st, lane);
     }
 }
 
@@ -262,7 +303,8 @@ BatchWs carve_batch(Carver &c, const ldni_batch_item_t *items_host, int count) {
     w.T.ray_prefix = c.take<long long>(3 * (size_t)count + 1);
     w.T.chunk_prefix = c.take<long long>(3 * (size_t)count + 1);
     w.T.count_base = c.take<long long>(3 * (size_t)count);
-    w.T.big = c.take<long long>((size_t)(3 * tris > 0 ? 3 * tris : 1));
+    w.T.qcap = 3 * tris > 0 ? 3 * tris : 1;
+    w.T.big = c.take<long long>((size_t)w.T.qcap);
     return w;
 }
 
@@ -317,18 +359,20 @@ extern "C" int ldni_sample_batch(const ldni_batch_item_t *items_dev, const ldni_
     if (cudaMemsetAsync(w.counts, 0, w.counts_bytes, s) != cudaSuccess) return LDNI_ECUDA;
     if (cudaMemsetAsync(w.words, 0, w.words_bytes, s) != cudaSuccess) return LDNI_ECUDA;
     if (cudaMemsetAsync(infos, 0, sizeof(ldni_info_t) * (size_t)count, s) != cudaSuccess) return LDNI_ECUDA;
-    LDNI_LAUNCH(K_BATCH, s, setup_kernel<<<1, 32, 0, s>>>(items_dev, count, w.T));
+    LDNI_LAUNCH(K_BATCH, s, setup_kernel<<<1, kThreads, 0, s>>>(items_dev, count, w.T));
     if (tris > 0) {
         LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<false><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,
                                                                                              w.counts, infos));
-        LDNI_LAUNCH(K_BATCH, s, batch_big<false><<<num_sms() * 2, kThreads, 0, s>>>(items_dev, w.T, w.counts, infos));
+        LDNI_LAUNCH(K_BATCH, s,
+                    batch_big<false><<<5 * num_sms(), kThreads, 0, s>>>(items_dev, w.T, w.counts, num_sms(), infos));
     }
     LDNI_LAUNCH(K_BATCH, s,
                 batch_scan<<<(unsigned)chunks, kThreads, 0, s>>>(items_dev, count, w.T, w.counts, w.words, infos));
     if (tris > 0) {
         LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<true><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,
                                                                                             w.counts, infos));
-        LDNI_LAUNCH(K_BATCH, s, batch_big<true><<<num_sms() * 2, kThreads, 0, s>>>(items_dev, w.T, w.counts, infos));
+        LDNI_LAUNCH(K_BATCH, s,
+                    batch_big<true><<<5 * num_sms(), kThreads, 0, s>>>(items_dev, w.T, w.counts, num_sms(), infos));
     }
     LDNI_LAUNCH(K_BATCH, s, batch_sort<<<blocks_for(rays), kThreads, 0, s>>>(items_dev, count, w.T, infos));
     return cuda_status();

@@ -51,6 +51,8 @@ struct LImg {
     int *kcap[3];                // layers per ray
     long long *slab_base[3];     // first slab slot of the tile
     int *over[3];                // 1 = overflowed, redone exactly
+    unsigned *deep[3];           // per image, bit c of word w: chunk 32 w + c (rays 32 (32 w + c) ...) has a
+                                 // ray of more than kLanePer samples, ordered by order_deep
     int2 *slab;                  // (depth bits, tri) per slot
     float4 *nrm;                 // per-triangle unit normal (x, y, z, 0): one 16-byte load per sample
     long long slab_cap;
@@ -301,12 +303,12 @@ __device__ __forceinline__ void onepass_hit(int a, long long p, float d, int t, 
 
 template <int A>
 __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const float3 &n, int res, const LImg &o,
-                                             int *big_q, int *big_n) {
+                                             int *big_q, long long qcap, int *big_n) {
     Setup32 S;
     const int kind = setup_axis<A>(T, res, S);
     if (kind == kNone) return;
     if (kind == kBig) {
-        big_q[atomicAdd(big_n, 1)] = t * 4 + A;
+        enqueue_big(big_q, qcap, big_n, t * 4 + A, (long long)S.w * S.h);
         return;
     }
     const unsigned long long m = hit_mask(S);
@@ -324,7 +326,8 @@ __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const floa
 
 __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restrict__ verts,
                                                            const int *__restrict__ tris, int nt, int nv, GridDev g,
-                                                           int ax_lo, int ax_hi, LImg o, int *big_q, int *big_n,
+                                                           int ax_lo, int ax_hi, LImg o, int *big_q, long long qcap,
+                                                           int *big_n,
                                                            ldni_info_t *info) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         TriView T;
@@ -336,33 +339,31 @@ __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restri
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
         o.nrm[t] = make_float4(n.x, n.y, n.z, 0.0f);  // coalesced: the gather looks normals up by triangle
-        if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, big_n);
-        if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, big_n);
-        if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, big_n);
+        if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, qcap, big_n);
+        if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, qcap, big_n);
+        if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, qcap, big_n);
     }
 }
 
 __global__ void __launch_bounds__(kThreads) onepass_big(const float *__restrict__ verts, const int *__restrict__ tris,
-                                                        int nv, GridDev g, LImg o, const int *big_q,
-                                                        const int *big_n) {
-    const int nq = *big_n;
-    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
-        const int code = big_q[e];
+                                                        int nv, GridDev g, LImg o, const int *big_q, long long qcap,
+                                                        const int *big_n, int huge_blocks) {
+    for_each_big(big_q, qcap, big_n, (int)blockIdx.x, (int)gridDim.x, huge_blocks, [&](int code, int first, int step) {
         const int t = code >> 2, a = code & 3;
         TriView T;
-        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        if (load_tri(verts, tris, t, nv, g, T)) return;
         Setup64 S;
         int i0, i1, j0, j1;
-        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) return;
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
         const int w = i1 - i0 + 1;
         const long long npx = (long long)w * (j1 - j0 + 1);
-        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+        for (long long k = first; k < npx; k += step) {
             const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
             if (S.inside(i, j)) onepass_hit(a, (long long)j * g.res + i, S.depth(i, j), t, n, S.exiting, o);
         }
-    }
+    });
 }
 
 // ---- exact redo of overflowed tiles ------------------------------------------
@@ -418,26 +419,24 @@ __device__ __forceinline__ void redo_axis(const TriView &T, int t, const float3 
 }
 
 __device__ __forceinline__ void redo_big_block(const float *__restrict__ verts, const int *__restrict__ tris, int nv,
-                                               const GridDev &g, const LImg &o, const int *big_q, const int *big_n,
-                                               int blk, int nblk, ldni_info_t *info) {
-    const int nq = *big_n;
-    for (int e = blk; e < nq; e += nblk) {
-        const int code = big_q[e];
+                                               const GridDev &g, const LImg &o, const int *big_q, long long qcap,
+                                               const int *big_n, int blk, int nblk, ldni_info_t *info) {
+    for_each_big(big_q, qcap, big_n, blk, nblk, max(1, nblk / 3), [&](int code, int first, int step) {
         const int t = code >> 2, a = code & 3;
         TriView T;
-        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        if (load_tri(verts, tris, t, nv, g, T)) return;
         Setup64 S;
         int i0, i1, j0, j1;
-        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) return;
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
         const int w = i1 - i0 + 1;
         const long long npx = (long long)w * (j1 - j0 + 1);
-        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+        for (long long k = first; k < npx; k += step) {
             const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
             if (S.inside(i, j)) redo_hit(a, (long long)j * g.res + i, S.depth(i, j), t, o, n, info);
         }
-    }
+    });
 }
 
 // One launch for both redo traversals: blocks below tri_blocks walk the
@@ -445,11 +444,13 @@ __device__ __forceinline__ void redo_big_block(const float *__restrict__ verts, 
 // case) costs one load per block.
 __global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict__ verts, const int *__restrict__ tris,
                                                         int nt, int nv, GridDev g, int ax_lo, int ax_hi, LImg o,
-                                                        const int *big_q, const int *big_n, int tri_blocks,
+                                                        const int *big_q, long long qcap, const int *big_n,
+                                                        int tri_blocks,
                                                         ldni_info_t *info) {
     if (*(volatile int *)o.any_over == 0) return;
     if (blockIdx.x >= tri_blocks) {
-        redo_big_block(verts, tris, nv, g, o, big_q, big_n, blockIdx.x - tri_blocks, gridDim.x - tri_blocks, info);
+        redo_big_block(verts, tris, nv, g, o, big_q, qcap, big_n, blockIdx.x - tri_blocks, gridDim.x - tri_blocks,
+                       info);
         return;
     }
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += tri_blocks * blockDim.x) {
@@ -468,19 +469,31 @@ __global__ void __launch_bounds__(kThreads) redo_kernel(const float *__restrict_
 
 // (n_over, if given: the number of redone tiles, counted by the thread of each
 // tile's first ray; cleared before the launch.)
+struct SlabSrc {  // a ray's samples in its tile's slab, normals from the table
+    const int2 *slab;
+    const float4 *nrm;
+    long long s0;
+    __device__ __forceinline__ void operator()(int i, float &d, int &t, float &x, float &y, float &z) const {
+        const int2 v = slab[s0 + i];
+        d = __int_as_float(v.x);
+        t = v.y;
+        const float4 q = nrm[v.y];
+        x = q.x;
+        y = q.y;
+        z = q.z;
+    }
+};
+
 __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info,
                                                           int *n_over) {
     const int a = ax_lo + blockIdx.y;
     const int *off = pick3(o.offsets, a);
-    float *D = pick3(o.depth, a);
-    int *Tr = pick3(o.tri, a);
-    float *X = pick3(o.nx, a);
-    float *Y = pick3(o.ny, a);
-    float *Z = pick3(o.nz, a);
+    const RayOut r{pick3(o.depth, a), pick3(o.tri, a), pick3(o.nx, a), pick3(o.ny, a), pick3(o.nz, a)};
     const long long cap = pick3(o.cap, a);
     const int *over = pick3(o.over, a);
     const int *kc = pick3(o.kcap, a);
     const long long *sb = pick3(o.slab_base, a);
+    unsigned *deep = pick3(o.deep, a);
     const float4 *NRM = o.nrm;
     const int lane = threadIdx.x & 31;
     // a warp takes 32 consecutive rays, which lie in one tile (tiles are
@@ -516,15 +529,19 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             set_status(info, LDNI_ST_CAPACITY);
             continue;
         }
-        if (t_over) {  // filled exactly by the redo pass: order in place
-            sort_ray_global(b, e, D, Tr, X, Y, Z);
-            continue;
-        }
-        if (c > kt) {  // cannot happen for a tile that did not overflow
+        if (!t_over && c > kt) {  // cannot happen for a tile that did not overflow
             set_status(info, LDNI_ST_CAPACITY);
             continue;
         }
+        if (c > kLanePer) {  // ordered by order_deep, from where the samples are now
+            atomicOr(deep + (p >> 10), 1u << ((p >> 5) & 31));
+            continue;
+        }
         const long long s0 = tbase + (p & (kTilePix - 1)) * kt;
+        if (t_over) {  // filled exactly by the redo pass: order in place
+            sort_ray_global(b, e, r.D, r.Tr, r.X, r.Y, r.Z);
+            continue;
+        }
         if (c == 2) {  // the common case: everything in registers
             int2 v0, v1;
             if ((s0 & 1) == 0) {  // the slot pair is one 16-byte record
@@ -541,28 +558,73 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
                 v1 = w;
             }
             const float4 q0 = NRM[v0.y], q1 = NRM[v1.y];
-            D[b] = __int_as_float(v0.x);
-            D[b + 1] = __int_as_float(v1.x);
-            Tr[b] = v0.y;
-            Tr[b + 1] = v1.y;
-            X[b] = q0.x;
-            X[b + 1] = q1.x;
-            Y[b] = q0.y;
-            Y[b + 1] = q1.y;
-            Z[b] = q0.z;
-            Z[b + 1] = q1.z;
+            r.D[b] = __int_as_float(v0.x);
+            r.D[b + 1] = __int_as_float(v1.x);
+            r.Tr[b] = v0.y;
+            r.Tr[b + 1] = v1.y;
+            r.X[b] = q0.x;
+            r.X[b + 1] = q1.x;
+            r.Y[b] = q0.y;
+            r.Y[b + 1] = q1.y;
+            r.Z[b] = q0.z;
+            r.Z[b + 1] = q1.z;
             continue;
         }
-        for (int x = 0; x < c; ++x) {  // copy, then order in place
-            const int2 v = o.slab[s0 + x];
-            D[b + x] = __int_as_float(v.x);
-            Tr[b + x] = v.y;
-            const float4 q = NRM[v.y];
-            X[b + x] = q.x;
-            Y[b + x] = q.y;
-            Z[b + x] = q.z;
+        const SlabSrc src{o.slab, NRM, s0};  // 1, 3 or 4 samples: copy, then order in place
+        for (int x = 0; x < c; ++x) src(x, r.D[b + x], r.Tr[b + x], r.X[b + x], r.Y[b + x], r.Z[b + x]);
+        sort_ray_global(b, e, r.D, r.Tr, r.X, r.Y, r.Z);
+    }
+}
+
+// The rays of more than kLanePer samples in the chunks of 32 rays that
+// gather marked, ordered by whole warps: from the slab, or in place in a
+// redone tile.  A warp reads 32 words of marks, then orders the chunks of
+// the set bits one after another.
+__global__ void __launch_bounds__(kThreads) order_deep(long long nrays, int ax_lo, LImg o) {
+    __shared__ SortStage stage[kThreads / 32];
+    const int a = ax_lo + blockIdx.y;
+    const unsigned *deep = pick3(o.deep, a);
+    const int *off = pick3(o.offsets, a);
+    const RayOut r{pick3(o.depth, a), pick3(o.tri, a), pick3(o.nx, a), pick3(o.ny, a), pick3(o.nz, a)};
+    const long long cap = pick3(o.cap, a);
+    const int *over = pick3(o.over, a);
+    const int *kc = pick3(o.kcap, a);
+    const long long *sb = pick3(o.slab_base, a);
+    const int lane = threadIdx.x & 31;
+    SortStage &st = stage[threadIdx.x >> 5];
+    const auto in_place = [](long long, long long b, const RayOut &ro) { return InPlace{ro, b}; };
+    const auto from_slab = [&](long long s0, long long, const RayOut &) { return SlabSrc{o.slab, o.nrm, s0}; };
+    const long long nwords = (nrays + 1023) >> 10;
+    const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < nwords;
+         w0 += warps * 32) {
+        const unsigned word = w0 + lane < nwords ? deep[w0 + lane] : 0u;
+        unsigned any = __ballot_sync(0xffffffffu, word != 0u);
+        while (any) {
+            const int src = __ffs(any) - 1;
+            any &= any - 1;
+            unsigned bits = __shfl_sync(0xffffffffu, word, src);
+            while (bits) {
+                const int bit = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const long long base = ((w0 + src) * 32 + bit) * 32;  // first ray of the chunk
+                const int tile = (int)(base >> kTileBits);
+                const int t_over = over[tile], kt = kc[tile];
+                const long long p = base + lane;
+                long long b = 0;
+                int n = 0;
+                if (p < nrays) {
+                    b = off[p];
+                    const long long e = off[p + 1];
+                    const int c = (int)(e - b);
+                    if (c > kLanePer && e <= cap && (t_over || c <= kt)) n = c;
+                }
+                if (t_over)  // the same in every lane: a chunk lies in one tile
+                    order_warp_rays<true>(b, n, b, in_place, r, st, lane);
+                else
+                    order_warp_rays<true>(b, n, sb[tile] + (p & (kTilePix - 1)) * kt, from_slab, r, st, lane);
+            }
         }
-        sort_ray_global(b, e, D, Tr, X, Y, Z);
     }
 }
 
@@ -597,11 +659,13 @@ struct LearnedWs {
     int *any_over;
     float *feat[3];
     int *over[3];
-    size_t clear_bytes;  // counts, flags, features and overflow marks: one memset
+    unsigned *deep[3];
+    size_t clear_bytes;  // counts, flags, features, overflow and deep-ray marks: one memset
     long long *scan_words;
     int *kcap[3];
     long long *slab_base[3];
     int *big_q;
+    long long qcap;
     float4 *nrm;
     int2 *slab;
     long long slab_cap;
@@ -613,9 +677,11 @@ LearnedWs carve_learned_ws(Carver &c, long long nt, int res, int naxes, long lon
     const long long stride = (N + 63) / 64 * 64;
     const long long ntiles = (N + kTilePix - 1) / kTilePix;
     const long long tstride = (ntiles + 63) / 64 * 64;
-    // one cleared block: counts | big_n, any_over (64 ints) | features | overflow marks
-    // one cleared block: counts | big_n, any_over (64 ints) | features | overflow marks | exiting counts
-    const size_t ints = (size_t)(stride * naxes + 64 + tstride * naxes * kRawFeat + tstride * naxes + stride * naxes);
+    // one cleared block: counts | 64 ints (queue counts at 0 and 1, any_over at 8, slab cursor at
+    // 10..11) | features | overflow marks | exiting counts | deep-ray marks
+    const size_t deep_at = (size_t)(stride * naxes + 64 + tstride * naxes * kRawFeat + tstride * naxes + stride * naxes);
+    const long long dstride = ((N + 1023) / 1024 + 63) / 64 * 64;  // words of chunk marks per image
+    const size_t ints = deep_at + (size_t)dstride * naxes;
     int *block = c.take<int>(ints);
     for (int a = 0; a < naxes; ++a) {
         w.count[a] = block ? block + (size_t)a * stride : nullptr;
@@ -626,9 +692,10 @@ LearnedWs carve_learned_ws(Carver &c, long long nt, int res, int naxes, long lon
                           : nullptr;
         w.over[a] = block ? block + (size_t)stride * naxes + 64 + (size_t)tstride * naxes * kRawFeat + (size_t)a * tstride
                           : nullptr;
+        w.deep[a] = block ? reinterpret_cast<unsigned *>(block + deep_at) + (size_t)a * dstride : nullptr;
     }
     w.big_n = block ? block + (size_t)stride * naxes : nullptr;
-    w.any_over = block ? block + (size_t)stride * naxes + 1 : nullptr;
+    w.any_over = block ? block + (size_t)stride * naxes + 8 : nullptr;
     w.clear_bytes = sizeof(int) * ints;
     w.scan_words = c.take<long long>(csr_scan_partials(N) * naxes);
     int *kc = c.take<int>((size_t)(tstride * naxes));
@@ -637,7 +704,8 @@ LearnedWs carve_learned_ws(Carver &c, long long nt, int res, int naxes, long lon
         w.kcap[a] = kc ? kc + (size_t)a * tstride : nullptr;
         w.slab_base[a] = sb ? sb + (size_t)a * tstride : nullptr;
     }
-    w.big_q = c.take<int>((size_t)(nt * naxes > 0 ? nt * naxes : 1));
+    w.qcap = nt * naxes > 0 ? nt * naxes : 1;
+    w.big_q = c.take<int>((size_t)w.qcap);
     w.nrm = c.take<float4>((size_t)(nt > 0 ? nt : 1));
     w.slab = c.take<int2>((size_t)(slab_samples > 0 ? slab_samples : 1));
     w.slab_cap = slab_samples;
@@ -710,6 +778,7 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
         o.kcap[a] = w.kcap[k];
         o.slab_base[a] = w.slab_base[k];
         o.over[a] = w.over[k];
+        o.deep[a] = w.deep[k];
     }
     o.slab = w.slab;
     o.nrm = w.nrm;
@@ -728,13 +797,14 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     LDNI_LAUNCH(K_CAPACITY, s,
                 capacity_kernel<<<(ntiles * naxes + kCapTiles - 1) / kCapTiles, kCapWarps * 32, 0, s>>>(
                     ntiles, N, ax_lo, naxes, o, W, B, margin, fixed_layers,
-                    reinterpret_cast<unsigned long long *>(w.any_over + 1)));  // 8-byte aligned, cleared
+                    reinterpret_cast<unsigned long long *>(w.any_over + 2)));  // 8-byte aligned, cleared
     if (nt > 0) {
         LDNI_LAUNCH(K_ONEPASS, s,
                     onepass_kernel<<<grid_blocks(nt), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
-                                                                        o, w.big_q, w.big_n, info));
+                                                                        o, w.big_q, w.qcap, w.big_n, info));
         LDNI_LAUNCH(K_ONEPASS_BIG, s,
-                    onepass_big<<<num_sms() * 2, kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.big_n));
+                    onepass_big<<<5 * num_sms(), kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.qcap,
+                                                                   w.big_n, num_sms()));
     }
     const int *cnt[3];
     int *off[3];
@@ -757,10 +827,12 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
         LDNI_LAUNCH(K_REDO, s,
                     // a small grid: the launch is usually a no-op (no tile overflowed)
                     redo_kernel<<<num_sms() + num_sms() / 2, kThreads, 0, s>>>(
-                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o, w.big_q, w.big_n, num_sms(), info));
+                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o, w.big_q, w.qcap, w.big_n, num_sms(), info));
     }
     LDNI_LAUNCH(K_GATHER, s,
                 gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info, overflow_tiles));
+    LDNI_LAUNCH(K_ORDER, s,
+                order_deep<<<dim3((unsigned)((N + 1023) / 1024 + 255) / 256, naxes), kThreads, 0, s>>>(N, ax_lo, o));
     return cuda_status();
 }
 

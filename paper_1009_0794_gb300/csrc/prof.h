@@ -38,7 +38,8 @@ enum KernelId : int {
     K_GRAD = 22,
     K_BATCH = 23,
     K_NODES = 24,
-    K_NUM = 25
+    K_ORDER = 25,
+    K_NUM = 26
 };
 
 struct ProfState {

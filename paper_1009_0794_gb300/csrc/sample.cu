@@ -70,12 +70,12 @@ __device__ __forceinline__ void emit(float d, int a, int t, long long p, const f
 
 template <bool kFill, int A>
 __device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &n, const Img &o, int res, int *big_q,
-                                         int *big_n, ldni_info_t *info) {
+                                         long long qcap, int *big_n, ldni_info_t *info) {
     Setup32 S;
     const int kind = setup_axis<A, kFill>(T, res, S);
     if (kind == kNone) return;
     if (kind == kBig) {
-        if (!kFill) big_q[atomicAdd(big_n, 1)] = t * 4 + A;  // the fill pass reuses this queue
+        if (!kFill) enqueue_big(big_q, qcap, big_n, t * 4 + A, (long long)S.w * S.h);  // the fill pass reuses it
         return;
     }
     if (!kFill) {
@@ -100,7 +100,7 @@ __device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) tri_pass(const float *__restrict__ verts, const int *__restrict__ tris,
                                                      int nt, int nv, GridDev g, int ax_lo, int ax_hi, Img o,
-                                                     int *big_q, int *big_n, ldni_info_t *info) {
+                                                     int *big_q, long long qcap, int *big_n, ldni_info_t *info) {
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
         TriView T;
         const unsigned bad = load_tri(verts, tris, t, nv, g, T);
@@ -110,77 +110,89 @@ __global__ void __launch_bounds__(kThreads) tri_pass(const float *__restrict__ v
         }
         float3 n = make_float3(0.f, 0.f, 0.f);
         if (kFill) face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        if (ax_lo <= 0 && 0 <= ax_hi) tri_axis<kFill, 0>(T, t, n, o, g.res, big_q, big_n, info);
-        if (ax_lo <= 1 && 1 <= ax_hi) tri_axis<kFill, 1>(T, t, n, o, g.res, big_q, big_n, info);
-        if (ax_lo <= 2 && 2 <= ax_hi) tri_axis<kFill, 2>(T, t, n, o, g.res, big_q, big_n, info);
+        if (ax_lo <= 0 && 0 <= ax_hi) tri_axis<kFill, 0>(T, t, n, o, g.res, big_q, qcap, big_n, info);
+        if (ax_lo <= 1 && 1 <= ax_hi) tri_axis<kFill, 1>(T, t, n, o, g.res, big_q, qcap, big_n, info);
+        if (ax_lo <= 2 && 2 <= ax_hi) tri_axis<kFill, 2>(T, t, n, o, g.res, big_q, qcap, big_n, info);
     }
 }
 
-// One block per queued (triangle, image) pair; threads stride over its pixels.
+// The queued big (triangle, image) pairs, a warp or a block per pair
+// (for_each_big); the pair's threads stride over its box pixels.
 template <bool kFill>
 __global__ void __launch_bounds__(kThreads) big_pass(const float *__restrict__ verts, const int *__restrict__ tris,
-                                                     int nv, GridDev g, Img o, const int *big_q, const int *big_n,
-                                                     ldni_info_t *info) {
-    const int nq = *big_n;
-    for (int e = blockIdx.x; e < nq; e += gridDim.x) {
-        const int code = big_q[e];
+                                                     int nv, GridDev g, Img o, const int *big_q, long long qcap,
+                                                     const int *big_n, int huge_blocks, ldni_info_t *info) {
+    for_each_big(big_q, qcap, big_n, (int)blockIdx.x, (int)gridDim.x, huge_blocks, [&](int code, int first, int step) {
         const int t = code >> 2, a = code & 3;
         TriView T;
-        if (load_tri(verts, tris, t, nv, g, T)) continue;
+        if (load_tri(verts, tris, t, nv, g, T)) return;
         Setup64 S;
         int i0, i1, j0, j1;
-        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) continue;
+        if (!setup_big(T, a, g.res, S, i0, i1, j0, j1)) return;
         float3 n = make_float3(0.f, 0.f, 0.f);
         if (kFill) face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
         const int w = i1 - i0 + 1;
         const long long npx = (long long)w * (j1 - j0 + 1);
-        for (long long k = threadIdx.x; k < npx; k += blockDim.x) {
+        for (long long k = first; k < npx; k += step) {
             const int j = j0 + (int)(k / w), i = i0 + (int)(k % w);
             if (S.inside(i, j)) emit<kFill>(kFill ? S.depth(i, j) : 0.0f, a, t, (long long)j * g.res + i, n, o, info);
         }
-    }
+    });
 }
 
-// Per-ray ordering by (depth, tri_id) in place; also flags odd rays.
+// Per-ray ordering by (depth, tri_id) in place; also flags odd rays.  A warp
+// takes 32 consecutive rays: two samples are ordered by their lane directly,
+// longer rays by the rank orderings.
 __global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo, Img o, ldni_info_t *info) {
+    __shared__ SortStage stage[kThreads / 32];
     const int a = ax_lo + blockIdx.y;
     const int *off = a == 0 ? o.offsets[0] : (a == 1 ? o.offsets[1] : o.offsets[2]);
-    float *D = a == 0 ? o.depth[0] : (a == 1 ? o.depth[1] : o.depth[2]);
-    int *Tr = a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]);
-    float *X = a == 0 ? o.nx[0] : (a == 1 ? o.nx[1] : o.nx[2]);
-    float *Y = a == 0 ? o.ny[0] : (a == 1 ? o.ny[1] : o.ny[2]);
-    float *Z = a == 0 ? o.nz[0] : (a == 1 ? o.nz[1] : o.nz[2]);
+    RayOut r;
+    r.D = a == 0 ? o.depth[0] : (a == 1 ? o.depth[1] : o.depth[2]);
+    r.Tr = a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]);
+    r.X = a == 0 ? o.nx[0] : (a == 1 ? o.nx[1] : o.nx[2]);
+    r.Y = a == 0 ? o.ny[0] : (a == 1 ? o.ny[1] : o.ny[2]);
+    r.Z = a == 0 ? o.nz[0] : (a == 1 ? o.nz[1] : o.nz[2]);
     const long long cap = a == 0 ? o.cap[0] : (a == 1 ? o.cap[1] : o.cap[2]);
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < nrays;
-         p += (long long)gridDim.x * blockDim.x) {
-        const long long b = off[p];
-        long long e = off[p + 1];
-        if ((e - b) & 1) {
-            atomicAdd(&info->odd_rays, 1u);
-            set_status(info, LDNI_ST_ODD);
-        }
-        if (e > cap) e = cap;
-        if (e - b < 2) continue;
-        if (e - b == 2) {
-            const float d0 = D[b], d1 = D[b + 1];
-            const int t0 = Tr[b], t1 = Tr[b + 1];
-            if (key_less(d1, t1, d0, t0)) {
-                D[b] = d1; D[b + 1] = d0;
-                Tr[b] = t1; Tr[b + 1] = t0;
-                float s;
-                s = X[b]; X[b] = X[b + 1]; X[b + 1] = s;
-                s = Y[b]; Y[b] = Y[b + 1]; Y[b + 1] = s;
-                s = Z[b]; Z[b] = Z[b + 1]; Z[b + 1] = s;
+    const int lane = threadIdx.x & 31;
+    SortStage &st = stage[threadIdx.x >> 5];
+    const auto in_place = [](long long, long long b, const RayOut &o) { return InPlace{o, b}; };
+    for (long long base = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31); base < nrays;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long p = base + lane;
+        long long b = 0;
+        int n = 0;
+        if (p < nrays) {
+            b = off[p];
+            long long e = off[p + 1];
+            if ((e - b) & 1) {
+                atomicAdd(&info->odd_rays, 1u);
+                set_status(info, LDNI_ST_ODD);
             }
-            continue;
+            if (e > cap) e = cap;
+            if (e - b == 2) {
+                const float d0 = r.D[b], d1 = r.D[b + 1];
+                const int t0 = r.Tr[b], t1 = r.Tr[b + 1];
+                if (key_less(d1, t1, d0, t0)) {
+                    r.D[b] = d1; r.D[b + 1] = d0;
+                    r.Tr[b] = t1; r.Tr[b + 1] = t0;
+                    float s;
+                    s = r.X[b]; r.X[b] = r.X[b + 1]; r.X[b + 1] = s;
+                    s = r.Y[b]; r.Y[b] = r.Y[b + 1]; r.Y[b + 1] = s;
+                    s = r.Z[b]; r.Z[b] = r.Z[b + 1]; r.Z[b + 1] = s;
+                }
+            } else if (e - b > 2) {
+                n = (int)(e - b);
+            }
         }
-        sort_ray_global(b, e, D, Tr, X, Y, Z);
+        order_warp_rays<true>(b, n, b, in_place, r, st, lane);
     }
 }
 
 struct SampleWs {
     int *count[3];
-    int *big_n;          // right after the counts: one memset clears both
+    int *big_n;          // two queue counts right after the counts: one memset clears all
+    long long qcap;
     size_t clear_bytes;
     long long *scan_words;
     int *big_q;
@@ -190,12 +202,13 @@ SampleWs carve_sample_ws(Carver &c, long long nt, int res, int naxes) {
     SampleWs w{};
     const long long N = (long long)res * res;
     const long long stride = (N + 63) / 64 * 64;  // every image's counts start 256-byte aligned
-    int *block = c.take<int>((size_t)(stride * naxes + 1));
+    int *block = c.take<int>((size_t)(stride * naxes + 2));
     for (int a = 0; a < naxes; ++a) w.count[a] = block ? block + (size_t)a * stride : nullptr;
     w.big_n = block ? block + (size_t)stride * naxes : nullptr;
-    w.clear_bytes = sizeof(int) * (size_t)(stride * naxes + 1);
+    w.clear_bytes = sizeof(int) * (size_t)(stride * naxes + 2);
     w.scan_words = c.take<long long>(csr_scan_partials(N) * naxes);
-    w.big_q = c.take<int>((size_t)(nt * naxes > 0 ? nt * naxes : 1));
+    w.qcap = nt * naxes > 0 ? nt * naxes : 1;
+    w.big_q = c.take<int>((size_t)w.qcap);
     return w;
 }
 
@@ -257,10 +270,10 @@ int run_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, c
         LDNI_LAUNCH(K_COUNT_TRI, C.s,
                     tri_pass<false><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g,
                                                                           C.ax_lo, C.ax_hi, C.o, C.w.big_q,
-                                                                          C.w.big_n, info));
+                                                                          C.w.qcap, C.w.big_n, info));
         LDNI_LAUNCH(K_COUNT_BIG, C.s,
-                    big_pass<false><<<num_sms() * 2, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
-                                                                        C.w.big_n, info));
+                    big_pass<false><<<5 * num_sms(), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                        C.w.qcap, C.w.big_n, num_sms(), info));
     }
     const int *cnt[3];
     int *off[3];
@@ -278,10 +291,10 @@ int run_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, co
         LDNI_LAUNCH(K_FILL_TRI, C.s,
                     tri_pass<true><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g,
                                                                          C.ax_lo, C.ax_hi, C.o, C.w.big_q,
-                                                                         C.w.big_n, info));
+                                                                         C.w.qcap, C.w.big_n, info));
         LDNI_LAUNCH(K_FILL_BIG, C.s,
-                    big_pass<true><<<num_sms() * 2, kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
-                                                                       C.w.big_n, info));
+                    big_pass<true><<<5 * num_sms(), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                       C.w.qcap, C.w.big_n, num_sms(), info));
     }
     LDNI_LAUNCH(K_SORT, C.s,
                 sort_rays<<<dim3(grid_blocks(C.nrays), C.naxes), kThreads, 0, C.s>>>(C.nrays, C.ax_lo, C.o, info));

@@ -14,7 +14,8 @@ namespace ldni {
 constexpr int kTileBits = 12;
 constexpr int kTilePix = 1 << kTileBits;  // rays per tile (= one scan chunk)
 static_assert(kTilePix == kScanChunk, "a tile is one scan chunk");
-constexpr int kBigPixels = 64;            // pixel-centre box of a thread-handled triangle (fits one mask)
+constexpr int kBigPixels = 16;            // pixel-centre box of a thread-handled triangle (fits one mask)
+constexpr int kHugePixels = 2048;         // boxes above this take a whole block, smaller big ones a warp
 // Largest snapped extent (fixed-point units) of a triangle handled with
 // 32-bit edge functions.  With every vertex and every visited pixel centre
 // (plus one step beyond the box) within 32768 units of each other, each edge
@@ -143,8 +144,9 @@ __device__ __forceinline__ int setup_axis(const TriView &T, int res, Setup32 &S)
     const int i0 = max((umin + 127) >> 8, 0), i1 = min((umax - 128) >> 8, res - 1);
     const int j0 = max((vmin + 127) >> 8, 0), j1 = min((vmax - 128) >> 8, res - 1);
     if (i0 > i1 || j0 > j1) return kNone;
-    if (umax - umin >= kSmallExtent || vmax - vmin >= kSmallExtent || (i1 - i0 + 1) * (j1 - j0 + 1) > kBigPixels)
-        return kBig;
+    S.w = i1 - i0 + 1;
+    S.h = j1 - j0 + 1;
+    if (umax - umin >= kSmallExtent || vmax - vmin >= kSmallExtent || S.w * S.h > kBigPixels) return kBig;
     int A2 = (u1 - u0) * (v2 - v0) - (v1 - v0) * (u2 - u0);
     if (A2 == 0) return kNone;  // face parallel to the ray (Definition 1 note)
     float a0 = comp(T.p[0], A), a1 = comp(T.p[1], A), a2 = comp(T.p[2], A);
@@ -219,6 +221,35 @@ __device__ __forceinline__ bool setup_big(const TriView &T, int a, int res, Setu
     return i0 <= i1 && j0 <= j1;
 }
 
+// Queue of big (triangle, image) pairs: boxes up to kHugePixels from the
+// front (a warp each), larger ones from the back (a block each); n[0], n[1]
+// count the two ends.  The queue holds qcap entries.
+template <class Code>
+__device__ __forceinline__ void enqueue_big(Code *q, long long qcap, int *n, Code code, long long npx) {
+    if (npx > kHugePixels)
+        q[qcap - 1 - atomicAdd(n + 1, 1)] = code;
+    else
+        q[atomicAdd(n, 1)] = code;
+}
+
+// Visit every queued pair with body(code, first, step), which walks the
+// pair's box pixels first, first + step, ...  Blocks blk of nblk: the last
+// huge_blocks take the huge pairs a block each, the others the rest a warp each.
+template <class Code, class F>
+__device__ __forceinline__ void for_each_big(const Code *q, long long qcap, const int *n, int blk, int nblk,
+                                             int huge_blocks, F &&body) {
+    const int med_blocks = nblk - huge_blocks;
+    if (blk < med_blocks) {
+        const int nmed = n[0];
+        const int wpb = blockDim.x >> 5;
+        for (int e = blk * wpb + (threadIdx.x >> 5); e < nmed; e += med_blocks * wpb)
+            body(q[e], (int)(threadIdx.x & 31), 32);
+    } else {
+        const int nh = n[1];
+        for (int e = blk - med_blocks; e < nh; e += huge_blocks) body(q[qcap - 1 - e], (int)threadIdx.x, (int)blockDim.x);
+    }
+}
+
 __device__ __forceinline__ bool key_less(float d0, int t0, float d1, int t1) {
     return d0 < d1 || (d0 == d1 && t0 < t1);
 }
@@ -244,6 +275,176 @@ __device__ __forceinline__ void sort_ray_global(long long b, long long e, float 
         X[y + 1] = nx;
         Y[y + 1] = ny;
         Z[y + 1] = nz;
+    }
+}
+
+// ---- ordering by ranks ------------------------------------------------------------
+// Sample i of a ray moves to position b + rank(i), the rank counting the
+// samples with a smaller key (equal keys, which valid input never has, by
+// index).  The key maps the depth's bits to an unsigned order in which -0 and
+// +0 are equal, as under key_less, then the triangle index; every key is
+// below ~0 because triangle indices are below INT_MAX.
+
+__device__ __forceinline__ unsigned long long sort_key(float d, int t) {
+    unsigned u = __float_as_uint(__fadd_rn(d, 0.0f));
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)u << 32) | (unsigned)(t ^ (int)0x80000000);
+}
+
+__device__ __forceinline__ int key_tri(unsigned long long k) { return (int)((unsigned)k ^ 0x80000000u); }
+
+__device__ __forceinline__ int rank_step(unsigned long long kj, unsigned long long ki, int j, int i) {
+    return (kj < ki) | ((kj == ki) & (j < i));
+}
+
+constexpr int kLanePer = 4;        // a lane orders rays of up to 4 samples by itself
+constexpr int kWarpSortMax = 128;  // longest ray a warp stages in shared memory
+constexpr int kRankMax = 768;      // longest ray ordered by ranks in place
+
+// one warp's staging area (3 KB): 128 samples, or 4 per lane, or 768 ranks
+struct SortStage {
+    unsigned long long key[kWarpSortMax];
+    float d[kWarpSortMax], x[kWarpSortMax], y[kWarpSortMax], z[kWarpSortMax];
+};
+static_assert(sizeof(SortStage) >= kRankMax * sizeof(int), "ranks fit the stage");
+
+struct RayOut {
+    float *D;
+    int *Tr;
+    float *X, *Y, *Z;
+};
+
+// source of a ray's samples that sits where the ordered ray goes
+struct InPlace {
+    RayOut o;
+    long long b;
+    __device__ __forceinline__ void operator()(int i, float &d, int &t, float &x, float &y, float &z) const {
+        d = o.D[b + i];
+        t = o.Tr[b + i];
+        x = o.X[b + i];
+        y = o.Y[b + i];
+        z = o.Z[b + i];
+    }
+};
+
+__device__ __forceinline__ void stage_put(SortStage &st, int s, float d, int t, float x, float y, float z) {
+    st.key[s] = sort_key(d, t);
+    st.d[s] = d;
+    st.x[s] = x;
+    st.y[s] = y;
+    st.z[s] = z;
+}
+
+__device__ __forceinline__ void stage_get(const SortStage &st, int s, const RayOut &o, long long dst) {
+    o.D[dst] = st.d[s];
+    o.Tr[dst] = key_tri(st.key[s]);
+    o.X[dst] = st.x[s];
+    o.Y[dst] = st.y[s];
+    o.Z[dst] = st.z[s];
+}
+
+// Stages samples [0, n) at slots base + i, then writes each to b + its rank
+// among them; every sample is read before the first store.  kWarp: the 32
+// lanes share the ray (lane l takes samples l, l + 32, ...); else one lane
+// orders it alone.
+template <bool kWarp, class Src>
+__device__ __forceinline__ void rank_staged(long long b, int n, const Src &src, const RayOut &o, SortStage &st,
+                                            int lane, int base) {
+    const int first = kWarp ? lane : 0, step = kWarp ? 32 : 1;
+    for (int i = first; i < n; i += step) {
+        float d, x, y, z;
+        int t;
+        src(i, d, t, x, y, z);
+        stage_put(st, base + i, d, t, x, y, z);
+    }
+    if (kWarp) __syncwarp();
+    for (int i = first; i < n; i += step) {
+        const unsigned long long ki = st.key[base + i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += rank_step(st.key[base + j], ki, j, i);
+        stage_get(st, base + i, o, b + r);
+    }
+    if (kWarp) __syncwarp();
+}
+
+// In-place ordering of a ray of kWarpSortMax < n <= kRankMax samples by the
+// warp: ranks from the keys in global memory, then the permutation applied
+// cycle by cycle by the first lane.
+__device__ __forceinline__ void rank_long(long long b, int n, const RayOut &o, SortStage &st, int lane) {
+    int *rank = reinterpret_cast<int *>(&st);
+    for (int i = lane; i < n; i += 32) {
+        const unsigned long long ki = sort_key(o.D[b + i], o.Tr[b + i]);
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += rank_step(sort_key(o.D[b + j], o.Tr[b + j]), ki, j, i);
+        rank[i] = r;
+    }
+    __syncwarp();
+    if (lane == 0) {
+        for (int s0 = 0; s0 < n; ++s0) {
+            int pos = rank[s0];
+            if (pos < 0 || pos == s0) continue;
+            rank[s0] = -1;
+            float d = o.D[b + s0], x = o.X[b + s0], y = o.Y[b + s0], z = o.Z[b + s0];
+            int t = o.Tr[b + s0];
+            while (pos != s0) {  // carry the element to its place, pick up the one there
+                const long long q = b + pos;
+                const float d2 = o.D[q], x2 = o.X[q], y2 = o.Y[q], z2 = o.Z[q];
+                const int t2 = o.Tr[q];
+                o.D[q] = d;
+                o.Tr[q] = t;
+                o.X[q] = x;
+                o.Y[q] = y;
+                o.Z[q] = z;
+                const int nxt = rank[pos];
+                rank[pos] = -1;
+                d = d2, t = t2, x = x2, y = y2, z = z2;
+                pos = nxt;
+            }
+            o.D[b + s0] = d;
+            o.Tr[b + s0] = t;
+            o.X[b + s0] = x;
+            o.Y[b + s0] = y;
+            o.Z[b + s0] = z;
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ RayOut shfl_out(const RayOut &o, int src) {
+    RayOut r;
+    r.D = reinterpret_cast<float *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(o.D), src));
+    r.Tr = reinterpret_cast<int *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(o.Tr), src));
+    r.X = reinterpret_cast<float *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(o.X), src));
+    r.Y = reinterpret_cast<float *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(o.Y), src));
+    r.Z = reinterpret_cast<float *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(o.Z), src));
+    return r;
+}
+
+// Orders the rays of the 32 lanes of a warp; every lane calls it, with n = 0
+// when it has nothing to order.  Rays of up to kLanePer samples are ordered
+// by their own lane, up to kWarpSortMax by the warp from the staged samples,
+// up to kRankMax by the warp in place (their samples must already sit at b),
+// longer ones by their lane's insertion.  make(sb, b, o) gives the source of
+// a ray whose samples are read from sb and go to b in o.  kOneOut: o is the
+// same in every lane.
+template <bool kOneOut, class Make>
+__device__ __forceinline__ void order_warp_rays(long long b, int n, long long sb, const Make &make, const RayOut &o,
+                                                SortStage &st, int lane) {
+    if (n >= 2 && n <= kLanePer) rank_staged<false>(b, n, make(sb, b, o), o, st, lane, kLanePer * lane);
+    if (n > kRankMax) sort_ray_global(b, b + n, o.D, o.Tr, o.X, o.Y, o.Z);
+    __syncwarp();
+    unsigned deep = __ballot_sync(0xffffffffu, n > kLanePer && n <= kRankMax);
+    while (deep) {
+        const int src = __ffs(deep) - 1;
+        deep &= deep - 1;
+        const RayOut oo = kOneOut ? o : shfl_out(o, src);
+        const long long bb = __shfl_sync(0xffffffffu, b, src);
+        const long long sbb = __shfl_sync(0xffffffffu, sb, src);
+        const int nn = __shfl_sync(0xffffffffu, n, src);
+        if (nn <= kWarpSortMax)
+            rank_staged<true>(bb, nn, make(sbb, bb, oo), oo, st, lane, 0);
+        else
+            rank_long(bb, nn, oo, st, lane);
     }
 }
 

@@ -57,6 +57,18 @@ def test_mixed_batch_equals_single(ldni):
     _check(ldni, meshes, grids, plan.finish())
 
 
+def test_deep_rays_batch_equals_single(ldni):
+    """Stacked boxes of every ordering tier in one batch, whose warps of 32
+    rays straddle images of different meshes (resolutions 5 and 7 have fewer
+    rays than a warp)."""
+    meshes = [M.slab_stack(k, axis=k % 3, seed=k) for k in (3, 40, 100, 450, 40, 3)]
+    res = [48, 5, 40, 48, 7, 33]
+    grids = [ldni.Grid.cube(O3, 1.0, r) for r in res]
+    plan = ldni.BatchPlan(meshes, grids)
+    plan.run()
+    _check(ldni, meshes, grids, plan.finish())
+
+
 def test_many_small_meshes(ldni):
     """96 meshes of 320 to 20,480 triangles, each on its own bounding grid."""
     batch = M.batch_meshes(96, seed=5, tmin=300, tmax=20_000, resolutions=(48, 64, 96, 128))
@@ -136,3 +148,51 @@ def test_union_chain_eager_graph_oracle(ldni, res):
         for k in range(1, steps):
             acc = oracle.boolean(acc, P[k].numpy(), "union")
         assert bit_equal(eager, acc)
+
+
+def test_full_batch_workload(ldni):
+    """The batched workload at full size: 256 seeded noisy icospheres and tori
+    of 1k-200k triangles at resolutions drawn from {64, 128, 256, 512}, each
+    on the cube [-0.5, 0.5]^3, sampled by one batch call; every mesh's three
+    images equal a per-mesh sampling bit for bit."""
+    batch = M.batch_meshes(256, seed=7)
+    meshes = [(v, t) for v, t, _ in batch]
+    grids = [ldni.Grid.cube(O3, 1.0, r) for _, _, r in batch]
+    plan = ldni.BatchPlan(meshes, grids)
+    plan.run()
+    outs = plan.finish()
+    for (v, t), g, got in zip(meshes, grids, outs):
+        ref = ldni.sample(torch.from_numpy(v).cuda(), torch.from_numpy(t).cuda(), g, "all")
+        for a in range(3):
+            assert ldni.identical(got[a], ref[a])
+
+
+def test_full_union_chain_workload(ldni):
+    """The sweep chain at full size: a 20,000-triangle torus (R 0.1, r 0.04,
+    100 x 100 quads) translated along a seeded helix for 64 steps at 512^2;
+    the graph-captured chain equals the oracle's step-by-step unions."""
+    base = M.torus(R=0.1, r=0.04, nu=100, nv=100)
+    offs = M.helix_offsets(64, seed=11)
+    meshes = [M.translate(base, d) for d in offs]
+    grid = ldni.Grid.cube(O3, 1.0, 512)
+    plan = ldni.BatchPlan(meshes, [grid] * 64)
+    plan.run()
+    parts = plan.finish()
+    for a in range(3):
+        P = [parts[k][a] for k in range(64)]
+        run_g, finish_g = ldni.union_chain(P)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            run_g(stream=s)
+        torch.cuda.current_stream().wait_stream(s)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            run_g(stream=s)
+        g.replay()
+        torch.cuda.synchronize()
+        got = finish_g().numpy()
+        acc = P[0].numpy()
+        for k in range(1, 64):
+            acc = oracle.boolean(acc, P[k].numpy(), "union")
+        assert bit_equal(got, acc)

@@ -94,6 +94,19 @@ def test_multilayer_and_big_triangles_equal_exact(ldni):
                 assert bit_equal(got[a], ref[a])
 
 
+@pytest.mark.parametrize("k", [3, 40, 100, 450])
+def test_deep_rays_equal_exact(ldni, k):
+    """Rays of up to 2k samples: read from the slab when the tile's capacity
+    holds them, redone exactly and ordered in place when it does not."""
+    mesh = M.slab_stack(k, axis=k % 3, seed=k)
+    grid = ldni.Grid.cube(O3, 1.0, 48)
+    ref = _exact(ldni, mesh, grid)
+    for layers in (0, 6, 64):
+        got, _ = _learned(ldni, mesh, grid, layers=layers, slab=max(4, layers) * 3 * 48 * 48)
+        for a in range(3):
+            assert bit_equal(got[a], ref[a]), (layers, a)
+
+
 def test_network_capacity_equals_exact(ldni, small_net):
     net, _ = small_net
     for mesh, res in ((M.pr1_pair()[0], 128), (M.icosphere(40, r=0.33, noise=0.05, noise_kind="octave", seed=9), 256)):

@@ -78,6 +78,16 @@ def test_flower_and_knot_multilayer(ldni):
     _check_all_axes(ldni, M.torus_knot(n_ring=128, n_side=16), 160)
 
 
+@pytest.mark.parametrize("k", [3, 40, 100, 450])
+def test_deep_rays_ordered(ldni, k):
+    """Stacked boxes give rays of up to 2k samples, so every way of ordering
+    a ray is taken: by its lane (up to 4), by a warp from shared memory (up to
+    128), by ranks in place (up to 768) and by insertion beyond."""
+    mesh = M.slab_stack(k, axis=k % 3, seed=k)
+    got, _ = _check_all_axes(ldni, mesh, 48)
+    assert int(got[k % 3].counts().max()) > {3: 4, 40: 64, 100: 128, 450: 768}[k]
+
+
 def test_grid_offset_and_scale(ldni):
     """A non-unit cube with a non-trivial origin."""
     v, t = M.icosphere(6, r=0.3, noise=0.02, seed=8)
@@ -144,11 +154,15 @@ def test_repeatable_bitwise(ldni):
             assert np.array_equal(x[a][k], y[a][k])
 
 
-@pytest.mark.parametrize("res", [1024])
+@pytest.mark.parametrize("res", [1024, 2048])
 def test_scale_sphere_full_size(ldni, res):
-    """The 1,310,720-triangle noisy icosphere at the benchmark resolution,
-    every ray compared with the oracle."""
-    _check_all_axes(ldni, M.scale_sphere(), res)
+    """The 1,310,720-triangle noisy icosphere at both resolutions of the
+    sampling-throughput workload, every ray compared with the oracle; the
+    one-pass form with fixed two-layer capacity gives the same bits."""
+    got, _ = _check_all_axes(ldni, M.scale_sphere(), res)
+    grid = ldni.Grid.cube(O3, 1.0, res)
+    one = ldni.sample_learned(*M.scale_sphere(), grid, "all", net=None, layers=2)
+    assert all(ldni.identical(x, y) for x, y in zip(one, got))
 
 
 def test_max_resolution_sampled_rays(ldni):
