@@ -8,8 +8,8 @@ library and does not import it.
 
 Sampling follows Definitions 1-4 and Remark 1 (Section 2) with the
 pixel-centre convention of Section 3; the Boolean follows Section 4.1 and the
-small-interval removal of Section 4.1.1; the volume follows the
-odd-to-even-inside statement after Proposition 1.
+small-interval removal of Section 4.1.1; offsetting follows Section 4.2; the
+volume follows the odd-to-even-inside statement after Proposition 1.
 """
 from __future__ import annotations
 
@@ -70,6 +70,10 @@ def _load():
             lib.oracle_boolean.argtypes = [ctypes.c_int64, P, P, P, P, P, P, P, P, ctypes.c_int32,
                                            ctypes.c_float, ctypes.POINTER(ctypes.c_int32)]
             lib.oracle_bool_free.argtypes = [ctypes.POINTER(_OracleBool)]
+            lib.oracle_offset.restype = ctypes.POINTER(_OracleBool)
+            lib.oracle_offset.argtypes = [ctypes.c_int32, P, ctypes.c_float, P, P, P, P, P, ctypes.c_int32,
+                                          ctypes.c_float, ctypes.c_int32, ctypes.c_float,
+                                          ctypes.POINTER(ctypes.c_int32)]
             lib.oracle_volume.restype = ctypes.c_int32
             lib.oracle_volume.argtypes = [ctypes.c_int64, P, P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
             _lib = lib
@@ -152,6 +156,52 @@ def boolean(A, B, op, eps=0.0):
         }
     finally:
         lib.oracle_bool_free(h)
+    return out
+
+
+def offset(Ls, origin, width, res, r, inner=False, eps=0.0, axes=(0, 1, 2)):
+    """Offset of the solid given by its three LDNIs Ls (Section 4.2): the
+    union of the solid with one sphere of radius r at every sample (inner:
+    the difference), sphere by sphere in sample order (x-, y-, z-image, each
+    in CSR order), then small-interval removal with eps.  Ls: three dicts
+    with offsets, depth (f32), nrm (f32 [n,3]) and tri (int32).  Returns the
+    images listed in axes, as oracle.boolean returns an image; sphere
+    samples carry id s | 0x80000000 for sphere s."""
+    lib = _load()
+    nrays = int(res) * int(res)
+    offs, ds, ns, ts, cnt = [], [], [], [], []
+    for L in Ls:
+        o = np.asarray(L["offsets"], dtype=np.int64)
+        if o.size != nrays + 1:
+            raise ValueError("an image does not match the resolution")
+        offs.append(o - o[0])
+        ds.append(np.asarray(L["depth"], dtype=np.float32)[o[0]:o[-1]])
+        ns.append(np.asarray(L["nrm"], dtype=np.float32).reshape(-1, 3)[o[0]:o[-1]])
+        ts.append(np.asarray(L["tri"], dtype=np.int32)[o[0]:o[-1]])
+        cnt.append(int(o[-1] - o[0]))
+    off = np.ascontiguousarray(np.concatenate(offs))
+    d = np.ascontiguousarray(np.concatenate(ds), dtype=np.float32)
+    nr = np.ascontiguousarray(np.concatenate(ns), dtype=np.float32)
+    t = np.ascontiguousarray(np.concatenate(ts), dtype=np.int32)
+    n = np.asarray(cnt, dtype=np.int64)
+    org = np.ascontiguousarray(origin, dtype=np.float32)
+    out = []
+    for b in axes:
+        err = ctypes.c_int32(0)
+        h = lib.oracle_offset(int(res), _ptr(org), float(width), _ptr(off), _ptr(d), _ptr(nr), _ptr(t), _ptr(n),
+                              int(b), float(r), OP_DIFF if inner else OP_UNION, float(eps), ctypes.byref(err))
+        if not h:
+            raise ValueError(f"oracle_offset failed with code {err.value}")
+        try:
+            R = h.contents
+            out.append({
+                "offsets": _copy(R.offsets, R.nrays + 1, np.int64),
+                "depth": _copy(R.depth, R.n, np.float32),
+                "nrm": _copy(R.nrm, 3 * R.n, np.float32).reshape(R.n, 3),
+                "tri": _copy(R.tri, R.n, np.int32),
+            })
+        finally:
+            lib.oracle_bool_free(h)
     return out
 
 

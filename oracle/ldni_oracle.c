@@ -476,3 +476,206 @@ int32_t oracle_volume(int64_t nrays, const int64_t *off, const float *depth, dou
     *vol = acc * h * h;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------ */
+/* offsetting (Section 4.2)                                             */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Offsetting of a solid H by r (Section 4.2): one sphere of radius r is
+ * placed at every depth-normal sample of H's three LDNIs, and H is united
+ * with the spheres one after another (outer offset), or the spheres are
+ * subtracted one after another (inner offset), each sphere itself given by
+ * its LDNIs on H's grid.
+ *
+ * Readings (the paper gives no arithmetic for the sphere's samples):
+ *  - a sample of image a at pixel (i, j) with depth d sits at the point with
+ *    a-coordinate d and in-plane coordinates c_u(i), c_v(j), where
+ *    c(t) = fl32(o + fl32((t + 1/2) * h)), h = fl32(W / res);
+ *  - the spheres are taken in the order of the samples: image x, y, z, each
+ *    in CSR order; sphere s is the s-th sample in that order;
+ *  - the sphere about C meets the ray through (P_u, P_v) of image b iff
+ *    q < fl32(r * r), q = fl32(fl32(du * du) + fl32(dv * dv)),
+ *    du = fl32(P_u - C_u), dv = fl32(P_v - C_v); its two samples are
+ *    fl32(C_b -+ t), t = sqrt(fl32(r * r - q)) rounded to FP32, with the
+ *    outward normals (du, dv, -+t) / r (each component rounded to FP32) and
+ *    id s;
+ *  - each step is the Boolean of Section 4.1 with no small-interval removal;
+ *    the removal (eps) is applied once, to the final result, so that the
+ *    result does not depend on the order of the spheres.
+ * All sphere arithmetic is single precision, each operation rounded to
+ * nearest, so the samples are exact functions of the inputs.
+ */
+
+static float pixel_coord(int64_t t, float o, float h) {
+    float x = ((float)t + 0.5f) * h;
+    return o + x;
+}
+
+/* The sphere about c on the ray (pu, pv) of image b: 1 and its two samples
+ * (entering, leaving), or 0 when it misses the ray. */
+static int sphere_on_ray(const float c[3], int b, float pu, float pv, float r, float r2, float d[2], float n[6]) {
+    int iu, iv;
+    plane_axes(b, &iu, &iv);
+    float du = pu - c[iu];
+    float dv = pv - c[iv];
+    float du2 = du * du;
+    float dv2 = dv * dv;
+    float q = du2 + dv2;
+    if (!(q < r2)) return 0;
+    float t = sqrtf(r2 - q);
+    d[0] = c[b] - t;
+    d[1] = c[b] + t;
+    float nu = du / r, nv = dv / r, na = t / r;
+    n[b] = -na;
+    n[iu] = nu;
+    n[iv] = nv;
+    n[3 + b] = na;
+    n[3 + iu] = nu;
+    n[3 + iv] = nv;
+    return 1;
+}
+
+/*
+ * Image b of the offset of H.  off: the three images' offsets one after
+ * another (3 (res^2 + 1) values, each image's starting at 0); depth, nrm
+ * ([n][3]) and tri: the three images' samples one after another, n[a] each.
+ * op: OP_UNION (outer offset) or OP_DIFF (inner offset).
+ */
+oracle_bool *oracle_offset(int32_t res, const float *origin, float width, const int64_t *off, const float *depth,
+                           const float *nrm, const int32_t *tri, const int64_t *n, int32_t b, float r, int32_t op,
+                           float eps, int32_t *err) {
+    *err = OR_OK;
+    if (res < 1 || b < 0 || b > 2 || !(r > 0.0f) || (op != OP_UNION && op != OP_DIFF)) {
+        *err = OR_EINVAL;
+        return NULL;
+    }
+    const int64_t nrays = (int64_t)res * res;
+    const float h = width / (float)res;
+    const float r2 = r * r;
+    int64_t S = n[0] + n[1] + n[2], base[3] = {0, n[0], n[0] + n[1]};
+    /* sphere centres, in sample order */
+    float *C = (float *)malloc((size_t)(S > 0 ? S : 1) * 3 * sizeof(float));
+    int64_t *cnt = (int64_t *)calloc((size_t)nrays + 1, sizeof(int64_t));
+    if (!C || !cnt) { free(C); free(cnt); *err = OR_ENOMEM; return NULL; }
+    for (int a = 0; a < 3; ++a) {
+        int iu, iv;
+        plane_axes(a, &iu, &iv);
+        const int64_t *oa = off + (int64_t)a * (nrays + 1);
+        for (int64_t p = 0; p < nrays; ++p) {
+            float cu = pixel_coord(p % res, origin[iu], h), cv = pixel_coord(p / res, origin[iv], h);
+            for (int64_t k = oa[p]; k < oa[p + 1]; ++k) {
+                float *c = C + 3 * (base[a] + k);
+                c[a] = depth[base[a] + k];
+                c[iu] = cu;
+                c[iv] = cv;
+            }
+        }
+    }
+    /* the spheres that may meet each ray of image b (a box of pixel centres
+     * one pixel wider than the sphere's shadow), in sphere order */
+    int bu, bv;
+    plane_axes(b, &bu, &bv);
+    int64_t *box = (int64_t *)malloc((size_t)(S > 0 ? S : 1) * 4 * sizeof(int64_t));
+    if (!box) { free(C); free(cnt); *err = OR_ENOMEM; return NULL; }
+    for (int64_t s = 0; s < S; ++s) {
+        const float *c = C + 3 * s;
+        double lo_u = ((double)c[bu] - r - origin[bu]) / h - 0.5, hi_u = ((double)c[bu] + r - origin[bu]) / h - 0.5;
+        double lo_v = ((double)c[bv] - r - origin[bv]) / h - 0.5, hi_v = ((double)c[bv] + r - origin[bv]) / h - 0.5;
+        int64_t i0 = (int64_t)floor(lo_u) - 1, i1 = (int64_t)ceil(hi_u) + 1;
+        int64_t j0 = (int64_t)floor(lo_v) - 1, j1 = (int64_t)ceil(hi_v) + 1;
+        if (i0 < 0) i0 = 0;
+        if (j0 < 0) j0 = 0;
+        if (i1 > res - 1) i1 = res - 1;
+        if (j1 > res - 1) j1 = res - 1;
+        box[4 * s] = i0, box[4 * s + 1] = i1, box[4 * s + 2] = j0, box[4 * s + 3] = j1;
+        for (int64_t j = j0; j <= j1; ++j)
+            for (int64_t i = i0; i <= i1; ++i) cnt[j * res + i + 1]++;
+    }
+    for (int64_t p = 0; p < nrays; ++p) cnt[p + 1] += cnt[p];
+    int64_t *lst = (int64_t *)malloc((size_t)(cnt[nrays] > 0 ? cnt[nrays] : 1) * sizeof(int64_t));
+    int64_t *fillp = (int64_t *)malloc((size_t)nrays * sizeof(int64_t));
+    if (!lst || !fillp) { free(C); free(cnt); free(box); free(lst); free(fillp); *err = OR_ENOMEM; return NULL; }
+    memcpy(fillp, cnt, (size_t)nrays * sizeof(int64_t));
+    for (int64_t s = 0; s < S; ++s)
+        for (int64_t j = box[4 * s + 2]; j <= box[4 * s + 3]; ++j)
+            for (int64_t i = box[4 * s]; i <= box[4 * s + 1]; ++i) lst[fillp[j * res + i]++] = s;
+    free(box);
+    free(fillp);
+
+    /* ray by ray: H's samples, then one Boolean per sphere that meets the ray */
+    const int64_t *ob = off + (int64_t)b * (nrays + 1);
+    const float *db = depth + base[b];
+    const float *nb = nrm + 3 * base[b];
+    const int32_t *tb = tri + base[b];
+    int64_t maxlen = 0, total_cap = 0;
+    for (int64_t p = 0; p < nrays; ++p) {
+        int64_t len = (ob[p + 1] - ob[p]) + 2 * (cnt[p + 1] - cnt[p]) + 2;
+        if ((ob[p + 1] - ob[p]) & 1) { *err = OR_EODD; }
+        if (len > maxlen) maxlen = len;
+        total_cap += len;
+    }
+    if (*err != OR_OK) { free(C); free(cnt); free(lst); return NULL; }
+    oracle_bool *R = (oracle_bool *)calloc(1, sizeof(oracle_bool));
+    float *bd[2], *bn[2], *cand = (float *)malloc((size_t)maxlen * sizeof(float));
+    int32_t *bt[2];
+    int ok = R && cand;
+    for (int q = 0; q < 2; ++q) {
+        bd[q] = (float *)malloc((size_t)maxlen * sizeof(float));
+        bn[q] = (float *)malloc((size_t)maxlen * 3 * sizeof(float));
+        bt[q] = (int32_t *)malloc((size_t)maxlen * sizeof(int32_t));
+        ok = ok && bd[q] && bn[q] && bt[q];
+    }
+    if (ok) {
+        R->nrays = nrays;
+        R->offsets = (int64_t *)calloc((size_t)nrays + 1, sizeof(int64_t));
+        R->depth = (float *)malloc((size_t)(total_cap > 0 ? total_cap : 1) * sizeof(float));
+        R->nrm = (float *)malloc((size_t)(total_cap > 0 ? total_cap : 1) * 3 * sizeof(float));
+        R->tri = (int32_t *)malloc((size_t)(total_cap > 0 ? total_cap : 1) * sizeof(int32_t));
+        ok = R->offsets && R->depth && R->nrm && R->tri;
+    }
+    int64_t w = 0;
+    for (int64_t p = 0; ok && p < nrays; ++p) {
+        float pu = pixel_coord(p % res, origin[bu], h), pv = pixel_coord(p / res, origin[bv], h);
+        int cur = 0;
+        int64_t m = ob[p + 1] - ob[p];
+        for (int64_t k = 0; k < m; ++k) {
+            bd[cur][k] = db[ob[p] + k];
+            for (int c = 0; c < 3; ++c) bn[cur][3 * k + c] = nb[3 * (ob[p] + k) + c];
+            bt[cur][k] = tb[ob[p] + k];
+        }
+        for (int64_t e = cnt[p]; e < cnt[p + 1]; ++e) {
+            int64_t s = lst[e];
+            float sd[2], sn[6];
+            int32_t st[2] = {(int32_t)s, (int32_t)s};
+            if (!sphere_on_ray(C + 3 * s, b, pu, pv, r, r2, sd, sn)) continue;
+            m = bool_ray(bd[cur], bn[cur], bt[cur], m, sd, sn, st, 2, op, 0.0f, bd[1 - cur], bn[1 - cur],
+                         bt[1 - cur], cand);
+            cur = 1 - cur;
+        }
+        /* small-interval removal, once */
+        for (int64_t k = 0; k + 1 < m; k += 2) {
+            float th = bd[cur][k + 1] - bd[cur][k];
+            if (th < eps) continue;
+            for (int q = 0; q < 2; ++q) {
+                R->depth[w] = bd[cur][k + q];
+                for (int c = 0; c < 3; ++c) R->nrm[3 * w + c] = bn[cur][3 * (k + q) + c];
+                R->tri[w] = bt[cur][k + q];
+                w++;
+            }
+        }
+        R->offsets[p + 1] = w;
+    }
+    if (R) R->n = w;
+    free(C);
+    free(cnt);
+    free(lst);
+    free(cand);
+    for (int q = 0; q < 2; ++q) { free(bd[q]); free(bn[q]); free(bt[q]); }
+    if (!ok) {
+        oracle_bool_free(R);
+        *err = OR_ENOMEM;
+        return NULL;
+    }
+    return R;
+}
