@@ -344,6 +344,61 @@ def _node_classify(ldni, lib, U, flush, reps):
             "kernels": nl}
 
 
+def _offsetting(ldni, lib, U, flush, reps):
+    """Offsetting by sphere unions (Section 4.2), one CUDA graph replay per
+    measurement, L2 flushed before each: the flower at 128^2 by 2.5 pixels
+    (the paper's offsetting examples are at 128^2, Table 4) and the union's
+    three 1024^2 images by 2 pixels."""
+    import ctypes
+    import torch
+    import meshgen
+    out = {}
+    fl = meshgen.flower(512, 512)
+    g128 = ldni.Grid.cube((-0.5, -0.5, -0.5), 1.0, 128)
+    F = ldni.sample(torch.from_numpy(fl[0]).cuda(), torch.from_numpy(fl[1]).cuda(), g128, "all")
+    for name, Ls, rpix in (("flower_128_r2.5px", F, 2.5), ("union_1024_r2px", U, 2.0)):
+        grid = Ls[0].grid
+        r = rpix * grid.width / grid.res
+        ref = ldni.offset(Ls, r)  # exact output sizes
+        outs = [ldni.empty_layers(grid, a, max(L.n, 1)) for a, L in enumerate(ref)]
+        n = [int(L.n) for L in Ls]
+        nn = (ctypes.c_int64 * 3)(*n)
+        ws = torch.empty(ldni.offset_workspace_size(n, grid.res, r, grid.width), dtype=torch.uint8, device="cuda")
+        info = ldni.new_info()
+        H = (ldni._CLayers * 3)(*[L.c() for L in Ls])
+        arr = (ldni._CLayers * 3)(*[o.c() for o in outs])
+        cg = grid.c()
+
+        def run():
+            lib.ldni_offset(H, nn, ctypes.byref(cg), ctypes.c_float(r), 0, ctypes.c_float(0.0), arr, info.data_ptr(),
+                            ws.data_ptr(), ws.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+        g, nl = _capture(lib, run)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        for o, q in zip(outs, ref):
+            o.n = q.n
+        same = all(ldni.identical(o, q) for o, q in zip(outs, ref)) if info_ok(ldni, info) else False
+        ms = float(np.median(ts))
+        out[name] = {"workload": f"offset of {sum(n)} samples' spheres (r = {rpix} pixels) at {grid.res}^2, "
+                                 "three images", "ms": ms, "rays_per_s": 3 * grid.res ** 2 / (ms * 1e-3),
+                     "spheres_per_s": sum(n) / (ms * 1e-3), "samples_out": [int(q.n) for q in ref],
+                     "graph_equals_eager": bool(same), "kernels": nl}
+    return out
+
+
+def info_ok(ldni, info):
+    return ldni.info_decode(info)["status"] == 0
+
+
 def _other_workloads(ldni, lib, flush, reps):
     """The batched workload (256 meshes of 1k-200k triangles at 64..512^2,
     one batch call) and the 64-step union chain of a translated torus at
@@ -465,6 +520,7 @@ def run_ours(args):
     learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)))
     learned["train"] = train_meta
     next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
+    next_rows.update(_offsetting(ldni, lib, U, flush, 10))
     other = _other_workloads(ldni, lib, flush, 5)
 
     # timed region: K graph replays, per-step events, L2 flushed between steps

@@ -55,6 +55,7 @@ extern "C" {
 #define LDNI_ST_TIMEOUT 8u        /* a bounded device wait expired */
 #define LDNI_ST_RANGE 16u         /* a vertex could not be snapped (outside +-2^24 units) */
 #define LDNI_ST_INDEX 32u         /* a triangle referenced a vertex index outside [0, nv) */
+#define LDNI_ST_EVENTS 64u        /* offsetting: a ray met more samples than one warp orders; left empty */
 
 /* ---- modes and operations ------------------------------------------ */
 #define LDNI_AXIS_X 0
@@ -387,6 +388,41 @@ int ldni_volume_many_workspace_size(int32_t res, int32_t count, size_t *bytes_ho
 int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldni_grid_t *grid, double *vols, ldni_info_t *infos,
                      void *ws, size_t ws_bytes, void *stream);
 
+/* ---- offsetting (Section 4.2) ------------------------------------------ */
+
+/* Workspace bytes for ldni_offset of a solid whose three images hold n[0],
+ * n[1], n[2] samples (host array), at resolution res, radius r and cube
+ * width `width`.  The sphere lists grow with (r / h)^2 per sample;
+ * LDNI_ETOOLARGE when they would pass 2^31 - 1 entries or the samples 2^30. */
+int ldni_offset_workspace_size(const int64_t *n, int32_t res, float r, float width, size_t *bytes_host);
+
+/*
+ * Offset of the solid H given by its three LDNIs (Section 4.2): H united
+ * with (inner = 1: minus) one sphere of radius r about every sample of H,
+ * each sphere represented by its LDNIs on H's grid, then small-interval
+ * removal with eps (FP32 difference, strict <) applied once.
+ * Sample (i, j, d) of image a sits at the point with a-coordinate d and
+ * in-plane coordinates c_u(i), c_v(j), c(t) = fl32(o + fl32((t + 1/2) h)),
+ * h = fl32(width / res); spheres are numbered in sample order (image x, y,
+ * z, each in CSR order).  Sphere s about C meets the ray (P_u, P_v) of image
+ * b iff q < fl32(r r), q = fl32(fl32(du du) + fl32(dv dv)),
+ * du = fl32(P_u - C_u), dv = fl32(P_v - C_v); its samples are
+ * fl32(C_b -+ sqrt(fl32(r r - q))) with outward normals (du, dv, -+t) / r
+ * (componentwise FP32), id s | 0x80000000.  The result equals uniting
+ * (subtracting) the spheres one by one in that order with the Boolean of
+ * Section 4.1: where the result changes state, its sample is taken from the
+ * first of H, sphere 0, sphere 1, ... that changes state there; normals of
+ * subtracted spheres are inverted.
+ * H, out: host arrays of 3 layers (image x, y, z) with device buffers on one
+ * grid; n: host int64[3], the samples of H's images.  info: device, n[b] =
+ * samples image b of the result needs; beyond out[b].capacity samples are
+ * dropped (LDNI_ST_CAPACITY) while the offsets are still complete.  A ray
+ * that meets more than 512 samples (H's plus two per sphere that can change
+ * it) is left empty with LDNI_ST_EVENTS.  Odd input rays set LDNI_ST_ODD.
+ */
+int ldni_offset(const ldni_layers_t *H, const int64_t *n, const ldni_grid_t *grid, float r, int32_t inner, float eps,
+                ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes, void *stream);
+
 /* ---- grid-node classification (Section 5.1, Step 1) -------------------- */
 
 /* Workspace bytes for ldni_classify_nodes at resolution res (<= 4096):
@@ -459,7 +495,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -21,7 +21,7 @@ MODE_EXACT2 = 0
 MODE_LEARNED1 = 1
 OP_UNION, OP_INTER, OP_DIFF = 0, 1, 2
 
-ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX = 1, 2, 4, 8, 16, 32
+ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX, ST_EVENTS = 1, 2, 4, 8, 16, 32, 64
 
 
 class Grid(ctypes.Structure):
@@ -96,6 +96,8 @@ SIGNATURES = {
     "ldni_boolean_many": (ctypes.c_int, [_I32, _P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _P, _SZ, _P]),
     "ldni_volume_many_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
     "ldni_volume_many": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "ldni_offset_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(_SZ)]),
+    "ldni_offset": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_classify_nodes": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
     "ldni_get_tuning": (ctypes.c_int, [_P]),

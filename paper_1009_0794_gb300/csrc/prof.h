@@ -39,7 +39,8 @@ enum KernelId : int {
     K_BATCH = 23,
     K_NODES = 24,
     K_ORDER = 25,
-    K_NUM = 26
+    K_OFFSET = 26,
+    K_NUM = 27
 };
 
 struct ProfState {

@@ -476,6 +476,54 @@ def classify_nodes(Ls: Sequence[LDNI], stream=None, out: Optional[torch.Tensor] 
     return out
 
 
+def offset_workspace_size(n: Sequence[int], res: int, r: float, width: float) -> int:
+    sz = ctypes.c_size_t(0)
+    nn = (ctypes.c_int64 * 3)(*[int(x) for x in n])
+    _lib.check(_lib.load().ldni_offset_workspace_size(nn, int(res), float(r), float(width), ctypes.byref(sz)),
+               "ldni_offset_workspace_size")
+    return int(sz.value)
+
+
+def offset(Ls: Sequence[LDNI], r: float, inner: bool = False, eps: float = 0.0, capacity: Optional[int] = None,
+           stream=None) -> List[LDNI]:
+    """Offset of the solid given by its x, y and z images (Section 4.2): the
+    union with (inner: difference with) a sphere of radius r about every
+    sample, then small-interval removal with eps.  Sizes the outputs with one
+    readback: a first call with `capacity` samples per image (default: twice
+    the input's plus 2 per ray), repeated once with the exact sizes if that
+    was too small."""
+    lib = _lib.load()
+    grid = Ls[0].grid
+    if len(Ls) != 3 or any(L.grid != grid for L in Ls) or [L.axis for L in Ls] != [0, 1, 2]:
+        raise _lib.LDNIError(-1, "offset needs the x, y and z images of one grid")
+    n = [int(L.n) for L in Ls]
+    nn = (ctypes.c_int64 * 3)(*n)
+    ws = torch.empty(offset_workspace_size(n, grid.res, r, grid.width), dtype=torch.uint8, device="cuda")
+    info = new_info()
+    H = (_CLayers * 3)(*[L.c() for L in Ls])
+    g = grid.c()
+    caps = [int(capacity)] * 3 if capacity is not None else [2 * x + 2 * grid.res * grid.res for x in n]
+    for attempt in range(2):
+        outs = [empty_layers(grid, a, caps[a]) for a in range(3)]
+        arr = (_CLayers * 3)(*[o.c() for o in outs])
+        info.zero_()
+        _lib.check(lib.ldni_offset(H, nn, ctypes.byref(g), float(r), 1 if inner else 0, float(eps), arr,
+                                   info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream)), "ldni_offset")
+        meta = info_decode(info)
+        if meta["status"] & _lib.ST_CAPACITY and attempt == 0:
+            caps = [max(int(x), 1) for x in meta["n"]]
+            continue
+        _raise_status(meta["status"], "ldni_offset")
+        if meta["status"] & _lib.ST_ODD:
+            raise _lib.LDNIError(-3, "ldni_offset")
+        if meta["status"] & _lib.ST_EVENTS:
+            raise _lib.LDNIError(-4, "ldni_offset (a ray meets more sphere samples than one warp orders)")
+        for a in range(3):
+            outs[a].n = meta["n"][a]
+        return outs
+    raise _lib.LDNIError(-9, "ldni_offset")
+
+
 def unpack_nodes(words: torch.Tensor, res: int) -> np.ndarray:
     """Bit words of classify_nodes -> bool array [k, j, i]."""
     w = words.cpu().numpy().view(np.uint32)
