@@ -88,7 +88,15 @@ typedef struct {
  * (depth, tri_id).  SoA arrays, each `capacity` long; offsets has res*res+1
  * entries.  tri_id is the index of the sampled triangle ("accurate normal
  * sampling", Section 3 item 2); in a Boolean result bit 31 marks a sample
- * taken from the second operand. */
+ * taken from the second operand.
+ * Normals: with nrm8 == NULL, FP32 unit normals in nx, ny, nz.  With nrm8
+ * set, approximate normals (Section 3 item 1): one 32-bit word per sample
+ * holding three 8-bit codes (x in bits 0-7, y 8-15, z 16-23, the rest 0),
+ * q = rint(fl32(fl32(n + 1) * 127.5)) half to even, clamped to [0, 255];
+ * nx, ny, nz are then not used.  A decoded component is
+ * fl32(fl32(q / 127.5) - 1), normalised (ldni_normals_decode8); inverting a
+ * packed normal (Boolean difference) maps every q to 255 - q.  The inputs
+ * and output of one call use one format; offsetting takes FP32 normals only. */
 typedef struct {
     int32_t *offsets;
     float *depth;
@@ -97,6 +105,7 @@ typedef struct {
     float *nz;
     int32_t *tri_id;
     int64_t capacity; /* host value: length of the five sample arrays */
+    uint32_t *nrm8;   /* NULL, or packed 8-bit normals (capacity words) in place of nx, ny, nz */
 } ldni_layers_t;
 
 /* Device block a call reports into (caller-owned, device memory).
@@ -388,6 +397,18 @@ int ldni_volume_many_workspace_size(int32_t res, int32_t count, size_t *bytes_ho
 int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldni_grid_t *grid, double *vols, ldni_info_t *infos,
                      void *ws, size_t ws_bytes, void *stream);
 
+/* ---- approximate normals (Section 3 item 1) ---------------------------- */
+
+/* Packed 8-bit codes of n FP32 normals (device arrays; the ldni_layers_t
+ * codec: q = rint(fl32(fl32(c + 1) * 127.5)) half to even, clamped to
+ * [0, 255], x in bits 0-7, y 8-15, z 16-23). */
+int ldni_normals_encode8(const float *nx, const float *ny, const float *nz, int64_t n, uint32_t *w, void *stream);
+
+/* Unit FP32 normals from n packed words: c = fl32(fl32(q / 127.5) - 1) per
+ * component, divided by sqrt(fl32(fl32(cx^2 + cy^2) + cz^2)), each operation
+ * rounded to nearest. */
+int ldni_normals_decode8(const uint32_t *w, int64_t n, float *nx, float *ny, float *nz, void *stream);
+
 /* ---- offsetting (Section 4.2) ------------------------------------------ */
 
 /* Workspace bytes for ldni_offset of a solid whose three images hold n[0],
@@ -495,7 +516,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

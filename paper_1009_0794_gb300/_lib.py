@@ -38,7 +38,7 @@ MLP_IN, MLP_WEIGHTS, MLP_BIASES, TILE_RAYS = 12, 9024, 193, 4096
 class Layers(ctypes.Structure):
     _fields_ = [("offsets", ctypes.c_void_p), ("depth", ctypes.c_void_p), ("nx", ctypes.c_void_p),
                 ("ny", ctypes.c_void_p), ("nz", ctypes.c_void_p), ("tri_id", ctypes.c_void_p),
-                ("capacity", ctypes.c_int64)]
+                ("capacity", ctypes.c_int64), ("nrm8", ctypes.c_void_p)]
 
 
 class Tuning(ctypes.Structure):
@@ -96,6 +96,8 @@ SIGNATURES = {
     "ldni_boolean_many": (ctypes.c_int, [_I32, _P, _P, _P, _I32, ctypes.c_float, _P, _P, _P, _P, _SZ, _P]),
     "ldni_volume_many_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
     "ldni_volume_many": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
+    "ldni_normals_encode8": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
+    "ldni_normals_decode8": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
     "ldni_offset_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(_SZ)]),
     "ldni_offset": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),

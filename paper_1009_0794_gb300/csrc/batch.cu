@@ -102,9 +102,13 @@ __device__ __forceinline__ void batch_emit(const ldni_batch_item_t &it, int a, l
     }
     L.depth[slot] = d;
     L.tri_id[slot] = t;
-    L.nx[slot] = n.x;
-    L.ny[slot] = n.y;
-    L.nz[slot] = n.z;
+    if (L.nrm8) {  // approximate normals (Section 3 item 1)
+        L.nrm8[slot] = encode_normal8(n.x, n.y, n.z);
+    } else {
+        L.nx[slot] = n.x;
+        L.ny[slot] = n.y;
+        L.nz[slot] = n.z;
+    }
 }
 
 template <bool kFill, int A>
@@ -260,7 +264,8 @@ __global__ void __launch_bounds__(kThreads) batch_sort(const ldni_batch_item_t *
         int n = 0;
         if (act) {
             const ldni_layers_t &L = items[m].out[a];
-            r = RayOut{L.depth, L.tri_id, L.nx, L.ny, L.nz};
+            r = L.nrm8 ? RayOut{L.depth, L.tri_id, reinterpret_cast<float *>(L.nrm8), nullptr, nullptr}
+                       : RayOut{L.depth, L.tri_id, L.nx, L.ny, L.nz};
             const long long p = gr - T.ray_prefix[img];
             b = L.offsets[p];
             long long e = L.offsets[p + 1];
@@ -316,7 +321,7 @@ bool items_ok(const ldni_batch_item_t *items, int count) {
             return false;
         for (int a = 0; a < 3; ++a) {
             const ldni_layers_t &L = it.out[a];
-            if (!L.offsets || L.capacity < 0 || (L.capacity > 0 && (!L.depth || !L.nx || !L.ny || !L.nz || !L.tri_id)))
+            if (!L.offsets || L.capacity < 0 || !samples_ok(L))
                 return false;
         }
     }

@@ -32,6 +32,9 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kBoolThreads = 256;
 
+// Normals are FP32 in nx, ny, nz, or packed 8-bit words in nx with ny = nz =
+// nullptr (Section 3 item 1); the operands and the output of a call share the
+// format.  An inverted packed normal has every code q replaced by 255 - q.
 struct Side {
     long long cap;  // samples beyond capacity are never read
     const int *off;
@@ -141,15 +144,22 @@ __device__ __forceinline__ void emit_global(bool from_b, long long idx, const Si
     if (!from_b) {
         o.d[at] = A.d[idx];
         o.nx[at] = A.nx[idx];
-        o.ny[at] = A.ny[idx];
-        o.nz[at] = A.nz[idx];
+        if (o.ny) {
+            o.ny[at] = A.ny[idx];
+            o.nz[at] = A.nz[idx];
+        }
         o.tri[at] = A.tri[idx];
     } else {
-        const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+        const bool inv = op == LDNI_OP_DIFF;
+        const float sg = inv ? -1.0f : 1.0f;
         o.d[at] = B.d[idx];
-        o.nx[at] = sg * B.nx[idx];
-        o.ny[at] = sg * B.ny[idx];
-        o.nz[at] = sg * B.nz[idx];
+        if (o.ny) {
+            o.nx[at] = sg * B.nx[idx];
+            o.ny[at] = sg * B.ny[idx];
+            o.nz[at] = sg * B.nz[idx];
+        } else {
+            o.nx[at] = __uint_as_float(__float_as_uint(B.nx[idx]) ^ (inv ? kInvert8 : 0u));
+        }
         o.tri[at] = (int)((unsigned)B.tri[idx] | 0x80000000u);
     }
 }
@@ -506,13 +516,17 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
                 const long long g = (fb ? T.gb0 : T.ga0) + i;
                 d[u] = fb ? sB[i] : sA[i];
                 x[u] = (fb ? B.nx : A.nx)[g];
-                y[u] = (fb ? B.ny : A.ny)[g];
-                z[u] = (fb ? B.nz : A.nz)[g];
+                y[u] = o.ny ? (fb ? B.ny : A.ny)[g] : 0.0f;
+                z[u] = o.ny ? (fb ? B.nz : A.nz)[g] : 0.0f;
                 t[u] = (fb ? B.tri : A.tri)[g];
                 if (fb) {
-                    x[u] *= sg;
-                    y[u] *= sg;
-                    z[u] *= sg;
+                    if (o.ny) {
+                        x[u] *= sg;
+                        y[u] *= sg;
+                        z[u] *= sg;
+                    } else if (sg < 0.0f) {
+                        x[u] = __uint_as_float(__float_as_uint(x[u]) ^ kInvert8);
+                    }
                     t[u] = (int)((unsigned)t[u] | 0x80000000u);
                 }
             }
@@ -528,8 +542,10 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
             }
             o.d[at] = d[u];
             o.nx[at] = x[u];
-            o.ny[at] = y[u];
-            o.nz[at] = z[u];
+            if (o.ny) {
+                o.ny[at] = y[u];
+                o.nz[at] = z[u];
+            }
             o.tri[at] = t[u];
         }
     }
@@ -675,16 +691,23 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
     if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
 }
 
+// One output sample; inv: the normal inverted (FP32: negated; packed: every
+// code q -> 255 - q).
 __device__ __forceinline__ void put_sample(const Out &o, long long at, float d, float x, float y, float z, int t,
-                                           ldni_info_t *info) {
+                                           bool inv, ldni_info_t *info) {
     if (at >= o.cap) {
         set_status(info, LDNI_ST_CAPACITY);
         return;
     }
     o.d[at] = d;
-    o.nx[at] = x;
-    o.ny[at] = y;
-    o.nz[at] = z;
+    if (o.ny) {
+        const float f = inv ? -1.0f : 1.0f;
+        o.nx[at] = f * x;
+        o.ny[at] = f * y;
+        o.nz[at] = f * z;
+    } else {
+        o.nx[at] = __uint_as_float(__float_as_uint(x) ^ (inv ? kInvert8 : 0u));
+    }
     o.tri[at] = t;
 }
 
@@ -762,20 +785,20 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
                 const bool fa = kind == 1;
                 const int i = fa ? ra[k] : rb[k];
                 const float *sd = (fa ? A.d : B.d) + i, *sx = (fa ? A.nx : B.nx) + i;
-                const float *sy = (fa ? A.ny : B.ny) + i, *sz = (fa ? A.nz : B.nz) + i;
+                const float *sy = fa ? A.ny : B.ny, *sz = fa ? A.nz : B.nz;
                 const int *st = (fa ? A.tri : B.tri) + i;
                 const float e0 = sd[0], e1 = sd[1];
                 const float x0 = sx[0], x1 = sx[1];
-                const float y0 = sy[0], y1 = sy[1];
-                const float z0 = sz[0], z1 = sz[1];
+                const float y0 = sy ? sy[i] : 0.0f, y1 = sy ? sy[i + 1] : 0.0f;
+                const float z0 = sz ? sz[i] : 0.0f, z1 = sz ? sz[i + 1] : 0.0f;
                 int t0 = st[0], t1 = st[1];
-                const float f = fa ? 1.0f : sg;
+                const bool inv = !fa && sg < 0.0f;
                 if (!fa) {
                     t0 = (int)((unsigned)t0 | 0x80000000u);
                     t1 = (int)((unsigned)t1 | 0x80000000u);
                 }
-                put_sample(o, at, e0, f * x0, f * y0, f * z0, t0, info);
-                put_sample(o, at + 1, e1, f * x1, f * y1, f * z1, t1, info);
+                put_sample(o, at, e0, x0, y0, z0, t0, inv, info);
+                put_sample(o, at + 1, e1, x1, y1, z1, t1, inv, info);
                 if (want_vol) vacc = df_add(vacc, df_diff(e1, e0));
             }
         }
@@ -826,9 +849,25 @@ BoolWs carve_bool_ws(Carver &c, int res) {
     return w;
 }
 
+Side side_of(const ldni_layers_t &L) {
+    float *x, *y, *z;
+    normal_arrays(L, x, y, z);
+    return Side{L.capacity, L.offsets, L.depth, x, y, z, L.tri_id};
+}
+
+Out out_of(const ldni_layers_t &L) {
+    float *x, *y, *z;
+    normal_arrays(L, x, y, z);
+    return Out{L.offsets, L.depth, x, y, z, L.tri_id, L.capacity};
+}
+
+bool same_format(const ldni_layers_t &A, const ldni_layers_t &B, const ldni_layers_t &o) {
+    return (A.nrm8 != nullptr) == (o.nrm8 != nullptr) && (B.nrm8 != nullptr) == (o.nrm8 != nullptr);
+}
+
 bool layers_ok(const ldni_layers_t *L, bool need) {
     if (!L || !L->offsets || L->capacity < 0) return false;
-    if (need && L->capacity > 0 && (!L->depth || !L->nx || !L->ny || !L->nz || !L->tri_id)) return false;
+    if (need && !samples_ok(*L)) return false;
     return true;
 }
 
@@ -882,10 +921,12 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
         return LDNI_EINVAL;
     BoolJobs J{};
     for (int j = 0; j < count; ++j) {
-        if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true)) return LDNI_EINVAL;
-        J.A[j] = Side{A[j].capacity, A[j].offsets, A[j].depth, A[j].nx, A[j].ny, A[j].nz, A[j].tri_id};
-        J.B[j] = Side{B[j].capacity, B[j].offsets, B[j].depth, B[j].nx, B[j].ny, B[j].nz, B[j].tri_id};
-        J.o[j] = Out{out[j].offsets, out[j].depth, out[j].nx, out[j].ny, out[j].nz, out[j].tri_id, out[j].capacity};
+        if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true) ||
+            !same_format(A[j], B[j], out[j]))
+            return LDNI_EINVAL;
+        J.A[j] = side_of(A[j]);
+        J.B[j] = side_of(B[j]);
+        J.o[j] = out_of(out[j]);
         J.info[j] = infos + j;
         J.vol[j] = vols ? vols + j : nullptr;
     }
@@ -987,7 +1028,8 @@ int static_scratch(void **out) {
 extern "C" int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
                                    const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out,
                                    ldni_info_t *info, void *stream) {
-    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !info || !grid_valid(grid_a) ||
+    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !same_format(*A, *B, *out) ||
+        !info || !grid_valid(grid_a) ||
         !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
         return LDNI_EINVAL;
     if (!same_grid(grid_a, grid_b)) return LDNI_EGRID_MISMATCH;
@@ -1003,9 +1045,9 @@ extern "C" int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *gr
     if (!c.fits()) return LDNI_ETOOLARGE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const long long N = (long long)res * res;
-    Side sa{A->capacity, A->offsets, A->depth, A->nx, A->ny, A->nz, A->tri_id};
-    Side sb{B->capacity, B->offsets, B->depth, B->nx, B->ny, B->nz, B->tri_id};
-    Out o{out->offsets, out->depth, out->nx, out->ny, out->nz, out->tri_id, out->capacity};
+    Side sa = side_of(*A);
+    Side sb = side_of(*B);
+    Out o = out_of(*out);
     LDNI_LAUNCH(K_BOOL_COUNT, s, bool_pass<false><<<grid_blocks(N), kThreads, 0, s>>>(N, sa, sb, op, eps, w.count, o, info));
     rc = cuda_status();
     if (rc != LDNI_OK) return rc;

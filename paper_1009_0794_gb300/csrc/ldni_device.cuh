@@ -55,6 +55,17 @@ __device__ __forceinline__ void face_normal(const float3 &p0, const float3 &p1, 
     }
 }
 
+// Packed approximate normal (Section 3 item 1): three 8-bit codes
+// q = rint(fl32(fl32(n + 1) * 127.5)), half to even, clamped to [0, 255].
+__device__ __forceinline__ unsigned normal_code8(float n) {
+    const float v = __fmul_rn(__fadd_rn(n, 1.0f), 127.5f);
+    return v >= 255.0f ? 255u : (v > 0.0f ? (unsigned)__float2int_rn(v) : 0u);
+}
+__device__ __forceinline__ unsigned encode_normal8(float x, float y, float z) {
+    return normal_code8(x) | (normal_code8(y) << 8) | (normal_code8(z) << 16);
+}
+constexpr unsigned kInvert8 = 0x00FFFFFFu;  // q -> 255 - q in every code (an inverted normal)
+
 __device__ __forceinline__ float comp(const float3 &p, int k) { return k == 0 ? p.x : (k == 1 ? p.y : p.z); }
 
 __device__ __forceinline__ void set_status(ldni_info_t *info, unsigned bits) {

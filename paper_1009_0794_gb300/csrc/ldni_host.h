@@ -39,6 +39,24 @@ inline bool grid_valid(const ldni_grid_t *g) {
     return g && g->res >= 1 && g->res <= 8192 && g->width > 0.0f && g->width < 3.0e38f;
 }
 
+// The sample arrays of a layer are present (capacity 0 needs none).
+inline bool samples_ok(const ldni_layers_t &L) {
+    return L.capacity == 0 || (L.depth && L.tri_id && (L.nrm8 || (L.nx && L.ny && L.nz)));
+}
+
+// Normal arrays as the kernels take them: FP32 in x, y, z, or the packed
+// 8-bit words in x with y = z = nullptr.
+inline void normal_arrays(const ldni_layers_t &L, float *&x, float *&y, float *&z) {
+    if (L.nrm8) {
+        x = reinterpret_cast<float *>(L.nrm8);
+        y = z = nullptr;
+    } else {
+        x = L.nx;
+        y = L.ny;
+        z = L.nz;
+    }
+}
+
 inline GridDev make_grid(const ldni_grid_t *g) {
     GridDev d;
     d.o[0] = g->origin[0];

@@ -338,7 +338,8 @@ __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restri
         }
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        o.nrm[t] = make_float4(n.x, n.y, n.z, 0.0f);  // coalesced: the gather looks normals up by triangle
+        // coalesced: the gather looks normals up by triangle (w: the packed 8-bit normal)
+        o.nrm[t] = make_float4(n.x, n.y, n.z, __uint_as_float(encode_normal8(n.x, n.y, n.z)));
         if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, qcap, big_n);
         if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, qcap, big_n);
         if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, qcap, big_n);
@@ -379,9 +380,13 @@ __device__ __forceinline__ void redo_hit(int a, long long p, float d, int t, con
     }
     pick3(o.depth, a)[slot] = d;
     pick3(o.tri, a)[slot] = t;
-    pick3(o.nx, a)[slot] = n.x;
-    pick3(o.ny, a)[slot] = n.y;
-    pick3(o.nz, a)[slot] = n.z;
+    if (float *Y = pick3(o.ny, a)) {
+        pick3(o.nx, a)[slot] = n.x;
+        Y[slot] = n.y;
+        pick3(o.nz, a)[slot] = n.z;
+    } else {  // approximate normals (Section 3 item 1)
+        pick3(o.nx, a)[slot] = __uint_as_float(encode_normal8(n.x, n.y, n.z));
+    }
 }
 
 template <int A>
@@ -473,16 +478,27 @@ struct SlabSrc {  // a ray's samples in its tile's slab, normals from the table
     const int2 *slab;
     const float4 *nrm;
     long long s0;
+    bool packed;  // the packed 8-bit normal (table entry w) in x
     __device__ __forceinline__ void operator()(int i, float &d, int &t, float &x, float &y, float &z) const {
         const int2 v = slab[s0 + i];
         d = __int_as_float(v.x);
         t = v.y;
         const float4 q = nrm[v.y];
-        x = q.x;
+        x = packed ? q.w : q.x;
         y = q.y;
         z = q.z;
     }
 };
+
+__device__ __forceinline__ void put_sample(const RayOut &o, long long at, float d, int t, float x, float y, float z) {
+    o.D[at] = d;
+    o.Tr[at] = t;
+    o.X[at] = x;
+    if (o.Y) {
+        o.Y[at] = y;
+        o.Z[at] = z;
+    }
+}
 
 __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info,
                                                           int *n_over) {
@@ -562,16 +578,26 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             r.D[b + 1] = __int_as_float(v1.x);
             r.Tr[b] = v0.y;
             r.Tr[b + 1] = v1.y;
-            r.X[b] = q0.x;
-            r.X[b + 1] = q1.x;
-            r.Y[b] = q0.y;
-            r.Y[b + 1] = q1.y;
-            r.Z[b] = q0.z;
-            r.Z[b + 1] = q1.z;
+            if (r.Y) {
+                r.X[b] = q0.x;
+                r.X[b + 1] = q1.x;
+                r.Y[b] = q0.y;
+                r.Y[b + 1] = q1.y;
+                r.Z[b] = q0.z;
+                r.Z[b + 1] = q1.z;
+            } else {
+                r.X[b] = q0.w;
+                r.X[b + 1] = q1.w;
+            }
             continue;
         }
-        const SlabSrc src{o.slab, NRM, s0};  // 1, 3 or 4 samples: copy, then order in place
-        for (int x = 0; x < c; ++x) src(x, r.D[b + x], r.Tr[b + x], r.X[b + x], r.Y[b + x], r.Z[b + x]);
+        const SlabSrc src{o.slab, NRM, s0, r.Y == nullptr};  // 1, 3 or 4 samples: copy, then order in place
+        for (int x = 0; x < c; ++x) {
+            float d, nx, ny, nz;
+            int t;
+            src(x, d, t, nx, ny, nz);
+            put_sample(r, b + x, d, t, nx, ny, nz);
+        }
         sort_ray_global(b, e, r.D, r.Tr, r.X, r.Y, r.Z);
     }
 }
@@ -593,7 +619,8 @@ __global__ void __launch_bounds__(kThreads) order_deep(long long nrays, int ax_l
     const int lane = threadIdx.x & 31;
     SortStage &st = stage[threadIdx.x >> 5];
     const auto in_place = [](long long, long long b, const RayOut &ro) { return InPlace{ro, b}; };
-    const auto from_slab = [&](long long s0, long long, const RayOut &) { return SlabSrc{o.slab, o.nrm, s0}; };
+    const bool packed = r.Y == nullptr;
+    const auto from_slab = [&](long long s0, long long, const RayOut &) { return SlabSrc{o.slab, o.nrm, s0, packed}; };
     const long long nwords = (nrays + 1023) >> 10;
     const long long warps = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long w0 = ((long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < nwords;
@@ -763,15 +790,13 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     for (int k = 0; k < naxes; ++k) {
         const int a = ax_lo + k;
         const ldni_layers_t &L = out[k];
-        if (!L.offsets || L.capacity < 0 || (L.capacity > 0 && (!L.depth || !L.nx || !L.ny || !L.nz || !L.tri_id)))
+        if (!L.offsets || L.capacity < 0 || !samples_ok(L))
             return LDNI_EINVAL;
         o.count[a] = w.count[k];
         o.exitc[a] = w.exitc[k];
         o.offsets[a] = L.offsets;
         o.depth[a] = L.depth;
-        o.nx[a] = L.nx;
-        o.ny[a] = L.ny;
-        o.nz[a] = L.nz;
+        normal_arrays(L, o.nx[a], o.ny[a], o.nz[a]);
         o.tri[a] = L.tri_id;
         o.cap[a] = L.capacity;
         o.feat[a] = w.feat[k];

@@ -444,7 +444,7 @@ extern "C" int ldni_offset(const ldni_layers_t *H, const int64_t *n, const ldni_
     if (n[0] < 0 || n[1] < 0 || n[2] < 0 || S >= (1ll << 29)) return LDNI_ETOOLARGE;
     for (int a = 0; a < 3; ++a) {
         if (!H[a].offsets || (n[a] > 0 && (!H[a].depth || !H[a].nx || !H[a].ny || !H[a].nz || !H[a].tri_id)) ||
-            H[a].capacity < n[a])
+            H[a].capacity < n[a] || H[a].nrm8 || out[a].nrm8)  // FP32 normals only
             return LDNI_EINVAL;
         if (!out[a].offsets || out[a].capacity < 0 ||
             (out[a].capacity > 0 && (!out[a].depth || !out[a].nx || !out[a].ny || !out[a].nz || !out[a].tri_id)))

@@ -40,7 +40,8 @@ enum KernelId : int {
     K_NODES = 24,
     K_ORDER = 25,
     K_OFFSET = 26,
-    K_NUM = 27
+    K_CODEC = 27,
+    K_NUM = 28
 };
 
 struct ProfState {

@@ -63,9 +63,13 @@ __device__ __forceinline__ void emit(float d, int a, int t, long long p, const f
     int *T = a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]);
     D[slot] = d;
     T[slot] = t;
-    X[slot] = n.x;
-    Y[slot] = n.y;
-    Z[slot] = n.z;
+    if (Y) {
+        X[slot] = n.x;
+        Y[slot] = n.y;
+        Z[slot] = n.z;
+    } else {  // approximate normals (Section 3 item 1)
+        X[slot] = __uint_as_float(encode_normal8(n.x, n.y, n.z));
+    }
 }
 
 template <bool kFill, int A>
@@ -178,8 +182,10 @@ __global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo
                     r.Tr[b] = t1; r.Tr[b + 1] = t0;
                     float s;
                     s = r.X[b]; r.X[b] = r.X[b + 1]; r.X[b + 1] = s;
-                    s = r.Y[b]; r.Y[b] = r.Y[b + 1]; r.Y[b + 1] = s;
-                    s = r.Z[b]; r.Z[b] = r.Z[b + 1]; r.Z[b + 1] = s;
+                    if (r.Y) {
+                        s = r.Y[b]; r.Y[b] = r.Y[b + 1]; r.Y[b + 1] = s;
+                        s = r.Z[b]; r.Z[b] = r.Z[b + 1]; r.Z[b + 1] = s;
+                    }
                 }
             } else if (e - b > 2) {
                 n = (int)(e - b);
@@ -243,14 +249,12 @@ int prepare(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, con
         const int a = C.ax_lo + k;
         const ldni_layers_t &L = out[k];
         if (!L.offsets) return LDNI_EINVAL;
-        if (need_samples && L.capacity > 0 && (!L.depth || !L.nx || !L.ny || !L.nz || !L.tri_id)) return LDNI_EINVAL;
+        if (need_samples && !samples_ok(L)) return LDNI_EINVAL;
         if (L.capacity < 0) return LDNI_EINVAL;
         C.o.count[a] = w.count[k];
         C.o.offsets[a] = L.offsets;
         C.o.depth[a] = L.depth;
-        C.o.nx[a] = L.nx;
-        C.o.ny[a] = L.ny;
-        C.o.nz[a] = L.nz;
+        normal_arrays(L, C.o.nx[a], C.o.ny[a], C.o.nz[a]);
         C.o.tri[a] = L.tri_id;
         C.o.cap[a] = L.capacity;
     }

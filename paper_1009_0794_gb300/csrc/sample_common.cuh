@@ -254,29 +254,37 @@ __device__ __forceinline__ bool key_less(float d0, int t0, float d1, int t1) {
     return d0 < d1 || (d0 == d1 && t0 < t1);
 }
 
-// In-place insertion sort of one ray's samples (five SoA arrays) by (depth, tri).
+// In-place insertion sort of one ray's samples (SoA arrays) by (depth, tri).
+// Normals: FP32 in X, Y, Z, or packed 8-bit words in X with Y = Z = nullptr
+// (moved as raw bits).
 __device__ __forceinline__ void sort_ray_global(long long b, long long e, float *D, int *Tr, float *X, float *Y,
                                                 float *Z) {
+    const bool three = Y != nullptr;
     for (long long x = b + 1; x < e; ++x) {
         const float d = D[x];
         const int t = Tr[x];
-        const float nx = X[x], ny = Y[x], nz = Z[x];
+        const float nx = X[x], ny = three ? Y[x] : 0.0f, nz = three ? Z[x] : 0.0f;
         long long y = x - 1;
         while (y >= b && key_less(d, t, D[y], Tr[y])) {
             D[y + 1] = D[y];
             Tr[y + 1] = Tr[y];
             X[y + 1] = X[y];
-            Y[y + 1] = Y[y];
-            Z[y + 1] = Z[y];
+            if (three) {
+                Y[y + 1] = Y[y];
+                Z[y + 1] = Z[y];
+            }
             --y;
         }
         D[y + 1] = d;
         Tr[y + 1] = t;
         X[y + 1] = nx;
-        Y[y + 1] = ny;
-        Z[y + 1] = nz;
+        if (three) {
+            Y[y + 1] = ny;
+            Z[y + 1] = nz;
+        }
     }
 }
+
 
 // ---- ordering by ranks ------------------------------------------------------------
 // Sample i of a ray moves to position b + rank(i), the rank counting the
@@ -311,7 +319,7 @@ static_assert(sizeof(SortStage) >= kRankMax * sizeof(int), "ranks fit the stage"
 struct RayOut {
     float *D;
     int *Tr;
-    float *X, *Y, *Z;
+    float *X, *Y, *Z;  // FP32 normals, or packed 8-bit normals in X with Y = Z = nullptr
 };
 
 // source of a ray's samples that sits where the ordered ray goes
@@ -322,8 +330,8 @@ struct InPlace {
         d = o.D[b + i];
         t = o.Tr[b + i];
         x = o.X[b + i];
-        y = o.Y[b + i];
-        z = o.Z[b + i];
+        y = o.Y ? o.Y[b + i] : 0.0f;
+        z = o.Y ? o.Z[b + i] : 0.0f;
     }
 };
 
@@ -339,8 +347,10 @@ __device__ __forceinline__ void stage_get(const SortStage &st, int s, const RayO
     o.D[dst] = st.d[s];
     o.Tr[dst] = key_tri(st.key[s]);
     o.X[dst] = st.x[s];
-    o.Y[dst] = st.y[s];
-    o.Z[dst] = st.z[s];
+    if (o.Y) {
+        o.Y[dst] = st.y[s];
+        o.Z[dst] = st.z[s];
+    }
 }
 
 // Stages samples [0, n) at slots base + i, then writes each to b + its rank
@@ -380,21 +390,26 @@ __device__ __forceinline__ void rank_long(long long b, int n, const RayOut &o, S
     }
     __syncwarp();
     if (lane == 0) {
+        const InPlace at{o, b};
         for (int s0 = 0; s0 < n; ++s0) {
             int pos = rank[s0];
             if (pos < 0 || pos == s0) continue;
             rank[s0] = -1;
-            float d = o.D[b + s0], x = o.X[b + s0], y = o.Y[b + s0], z = o.Z[b + s0];
-            int t = o.Tr[b + s0];
+            float d, x, y, z;
+            int t;
+            at(s0, d, t, x, y, z);
             while (pos != s0) {  // carry the element to its place, pick up the one there
                 const long long q = b + pos;
-                const float d2 = o.D[q], x2 = o.X[q], y2 = o.Y[q], z2 = o.Z[q];
-                const int t2 = o.Tr[q];
+                float d2, x2, y2, z2;
+                int t2;
+                at(pos, d2, t2, x2, y2, z2);
                 o.D[q] = d;
                 o.Tr[q] = t;
                 o.X[q] = x;
-                o.Y[q] = y;
-                o.Z[q] = z;
+                if (o.Y) {
+                    o.Y[q] = y;
+                    o.Z[q] = z;
+                }
                 const int nxt = rank[pos];
                 rank[pos] = -1;
                 d = d2, t = t2, x = x2, y = y2, z = z2;
@@ -403,8 +418,10 @@ __device__ __forceinline__ void rank_long(long long b, int n, const RayOut &o, S
             o.D[b + s0] = d;
             o.Tr[b + s0] = t;
             o.X[b + s0] = x;
-            o.Y[b + s0] = y;
-            o.Z[b + s0] = z;
+            if (o.Y) {
+                o.Y[b + s0] = y;
+                o.Z[b + s0] = z;
+            }
         }
     }
     __syncwarp();

@@ -56,12 +56,20 @@ class Grid:
 
 
 class LDNI:
-    """One layered depth-normal image in CSR form on the device."""
+    """One layered depth-normal image in CSR form on the device.  Normals are
+    FP32 in nx, ny, nz, or, with ``nrm8`` given, packed 8-bit codes
+    (approximate normals, Section 3 item 1; int32 tensor holding the words)
+    and nx, ny, nz empty."""
 
-    def __init__(self, grid: Grid, axis: int, offsets, depth, nx, ny, nz, tri, n: int):
+    def __init__(self, grid: Grid, axis: int, offsets, depth, nx, ny, nz, tri, n: int, nrm8=None):
         self.grid, self.axis = grid, axis
         self.offsets, self.depth, self.nx, self.ny, self.nz, self.tri = offsets, depth, nx, ny, nz, tri
+        self.nrm8 = nrm8
         self.n = int(n)
+
+    @property
+    def packed(self) -> bool:
+        return self.nrm8 is not None
 
     @property
     def capacity(self) -> int:
@@ -76,6 +84,7 @@ class LDNI:
         L.nz = self.nz.data_ptr() if self.nz.numel() else None
         L.tri_id = self.tri.data_ptr() if self.tri.numel() else None
         L.capacity = self.capacity
+        L.nrm8 = (self.nrm8.data_ptr() if self.nrm8.numel() else None) if self.packed else None
         return L
 
     def counts(self):
@@ -83,10 +92,13 @@ class LDNI:
 
     def numpy(self) -> dict:
         n = self.n
-        return {"offsets": self.offsets.cpu().numpy().astype(np.int64),
-                "depth": self.depth[:n].cpu().numpy(),
-                "nrm": torch.stack([self.nx[:n], self.ny[:n], self.nz[:n]], 1).cpu().numpy(),
-                "tri": self.tri[:n].cpu().numpy()}
+        out = {"offsets": self.offsets.cpu().numpy().astype(np.int64), "depth": self.depth[:n].cpu().numpy(),
+               "tri": self.tri[:n].cpu().numpy()}
+        if self.packed:
+            out["nrm8"] = self.nrm8[:n].cpu().numpy().view(np.uint32)
+        else:
+            out["nrm"] = torch.stack([self.nx[:n], self.ny[:n], self.nz[:n]], 1).cpu().numpy()
+        return out
 
 
 def identical(A: "LDNI", B: "LDNI") -> bool:
@@ -94,8 +106,12 @@ def identical(A: "LDNI", B: "LDNI") -> bool:
     if A.n != B.n or A.offsets.numel() != B.offsets.numel():
         return False
     n = A.n
+    if A.packed != B.packed:
+        return False
     same = torch.equal(A.offsets, B.offsets) and torch.equal(A.tri[:n], B.tri[:n])
-    for x, y in ((A.depth, B.depth), (A.nx, B.nx), (A.ny, B.ny), (A.nz, B.nz)):
+    pairs = [(A.depth, B.depth)]
+    pairs += [(A.nrm8, B.nrm8)] if A.packed else [(A.nx, B.nx), (A.ny, B.ny), (A.nz, B.nz)]
+    for x, y in pairs:
         same = same and torch.equal(x[:n].view(torch.int32), y[:n].view(torch.int32))
     return bool(same)
 
@@ -151,16 +167,21 @@ def sample_workspace_size(nv: int, nt: int, res: int, axis=_lib.AXIS_ALL) -> int
     return int(sz.value)
 
 
-def empty_layers(grid: Grid, axis: int, capacity: int) -> LDNI:
+def empty_layers(grid: Grid, axis: int, capacity: int, packed: bool = False) -> LDNI:
+    """Device buffers of one image; packed: 8-bit normals (one int32 word per
+    sample) instead of three FP32 arrays."""
     N = grid.res * grid.res
-    f = lambda: torch.empty(capacity, dtype=torch.float32, device="cuda")
-    return LDNI(grid, axis, torch.empty(N + 1, dtype=torch.int32, device="cuda"), f(), f(), f(), f(),
-                torch.empty(capacity, dtype=torch.int32, device="cuda"), 0)
+    f = lambda k: torch.empty(k, dtype=torch.float32, device="cuda")
+    i = lambda k: torch.empty(k, dtype=torch.int32, device="cuda")
+    nc = 0 if packed else capacity
+    return LDNI(grid, axis, i(N + 1), f(capacity), f(nc), f(nc), f(nc), i(capacity), 0,
+                nrm8=i(capacity) if packed else None)
 
 
 def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=None,
-           check_odd: bool = False) -> Union[LDNI, List[LDNI]]:
-    """Sample a closed mesh into LDNIs (Section 3, Definitions 1-4).
+           check_odd: bool = False, packed: bool = False) -> Union[LDNI, List[LDNI]]:
+    """Sample a closed mesh into LDNIs (Section 3, Definitions 1-4); packed:
+    approximate 8-bit normals (Section 3 item 1).
 
     Exact sizing: the count pass runs, the sample totals are read back (one
     device->host read, the only synchronisation), the sample arrays are
@@ -183,7 +204,7 @@ def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=Non
     res_list = []
     for k, a in enumerate(axes):
         n = meta["n"][a]
-        L = empty_layers(grid, a, n)
+        L = empty_layers(grid, a, n, packed)
         L.offsets = outs[k].offsets
         L.n = n
         res_list.append(L)
@@ -204,13 +225,14 @@ class SamplePlan:
     from a first exact call; a later call that needs more sets
     LDNI_ST_CAPACITY in ``info``."""
 
-    def __init__(self, nv: int, nt: int, grid: Grid, capacities: Sequence[int], axis="all", slack: float = 1.0):
+    def __init__(self, nv: int, nt: int, grid: Grid, capacities: Sequence[int], axis="all", slack: float = 1.0,
+                 packed: bool = False):
         self.grid = grid
         self.axes = _axes(axis)
         self.cax = _lib.AXIS_ALL if len(self.axes) == 3 else self.axes[0]
         self.ws = torch.empty(sample_workspace_size(nv, nt, grid.res, self.cax), dtype=torch.uint8, device="cuda")
         self.info = new_info()
-        self.outs = [empty_layers(grid, a, int(np.ceil(c * slack))) for a, c in zip(self.axes, capacities)]
+        self.outs = [empty_layers(grid, a, int(np.ceil(c * slack)), packed) for a, c in zip(self.axes, capacities)]
         self._arr = (_CLayers * len(self.axes))(*[o.c() for o in self.outs])
         self._g = grid.c()
 
@@ -242,7 +264,7 @@ def boolean(A: LDNI, B: LDNI, op, eps: float = 0.0, stream=None, out: Optional[L
     lib = _lib.load()
     opc = OPS[op] if isinstance(op, str) else int(op)
     if out is None:
-        out = empty_layers(A.grid, A.axis, A.capacity + B.capacity)
+        out = empty_layers(A.grid, A.axis, A.capacity + B.capacity, A.packed)
     if ws is None:
         ws = torch.empty(boolean_workspace_size(A.grid.res), dtype=torch.uint8, device="cuda")
     if info is None:
@@ -309,7 +331,7 @@ def boolean_many(As: Sequence[LDNI], Bs: Sequence[LDNI], op, eps: float = 0.0, s
             raise _lib.LDNIError(-2, "boolean_many")
     opc = OPS[op] if isinstance(op, str) else int(op)
     if outs is None:
-        outs = [empty_layers(grid, A.axis, A.capacity + B.capacity) for A, B in zip(As, Bs)]
+        outs = [empty_layers(grid, A.axis, A.capacity + B.capacity, A.packed) for A, B in zip(As, Bs)]
     if ws is None:
         ws = torch.empty(boolean_many_workspace_size(grid.res, count), dtype=torch.uint8, device="cuda")
     if infos is None:
@@ -387,7 +409,7 @@ class LearnedPlan:
     fixed `layers` per ray (the baseline without the network)."""
 
     def __init__(self, nv: int, nt: int, grid: Grid, capacities, slab_samples: int, axis="all", net=None,
-                 layers: int = 2, margin: float = 0.25, feature_stride: Optional[int] = None):
+                 layers: int = 2, margin: float = 0.25, feature_stride: Optional[int] = None, packed: bool = False):
         self.grid = grid
         self.axes = _axes(axis)
         self.cax = _lib.AXIS_ALL if len(self.axes) == 3 else self.axes[0]
@@ -396,7 +418,7 @@ class LearnedPlan:
                               device="cuda")
         self.info = new_info()
         self.n_over = torch.zeros(1, dtype=torch.int32, device="cuda")
-        self.outs = [empty_layers(grid, a, int(c)) for a, c in zip(self.axes, capacities)]
+        self.outs = [empty_layers(grid, a, int(c), packed) for a, c in zip(self.axes, capacities)]
         self._arr = (_CLayers * len(self.axes))(*[o.c() for o in self.outs])
         self._g = grid.c()
         self.net, self.layers = net, int(layers)
@@ -426,7 +448,7 @@ class LearnedPlan:
 def sample_learned(verts, tris, grid: Grid, axis="all", net=None, layers: int = 2, margin: float = 0.25,
                    feature_stride: Optional[int] = None, slab_samples: Optional[int] = None,
                    capacity_hint: Optional[int] = None,
-                   stream=None):
+                   stream=None, packed: bool = False):
     """One-traversal sampling (identical output to sample()).  Output arrays
     are sized by capacity_hint per image (default: 3 * res^2 / 2); a call
     that needs more raises LDNIError(LDNI_ECAPACITY)."""
@@ -436,10 +458,31 @@ def sample_learned(verts, tris, grid: Grid, axis="all", net=None, layers: int = 
     n_img = len(axes)
     cap = capacity_hint if capacity_hint is not None else max(16, 3 * grid.res * grid.res // 2)
     slab = slab_samples if slab_samples is not None else n_img * grid.res * grid.res * 4
-    plan = LearnedPlan(v.shape[0], t.shape[0], grid, [cap] * n_img, slab, axis, net, layers, margin, feature_stride)
+    plan = LearnedPlan(v.shape[0], t.shape[0], grid, [cap] * n_img, slab, axis, net, layers, margin, feature_stride,
+                       packed)
     plan.run(v, t, stream)
     outs = plan.finish()
     return outs if n_img > 1 else outs[0]
+
+
+# ---- approximate normals (Section 3 item 1) -------------------------------------
+
+def encode_normals8(nx: torch.Tensor, ny: torch.Tensor, nz: torch.Tensor, stream=None) -> torch.Tensor:
+    """Packed 8-bit codes (int32 tensor of words) of FP32 normals."""
+    n = nx.numel()
+    w = torch.empty(n, dtype=torch.int32, device="cuda")
+    _lib.check(_lib.load().ldni_normals_encode8(nx.data_ptr(), ny.data_ptr(), nz.data_ptr(), n, w.data_ptr(),
+                                                _stream_ptr(stream)), "ldni_normals_encode8")
+    return w
+
+
+def decode_normals8(w: torch.Tensor, stream=None):
+    """Unit FP32 normals (nx, ny, nz) from packed words."""
+    n = w.numel()
+    out = [torch.empty(n, dtype=torch.float32, device="cuda") for _ in range(3)]
+    _lib.check(_lib.load().ldni_normals_decode8(w.data_ptr(), n, out[0].data_ptr(), out[1].data_ptr(),
+                                                out[2].data_ptr(), _stream_ptr(stream)), "ldni_normals_decode8")
+    return tuple(out)
 
 
 # ---- grid-node classification (Section 5.1, Step 1) -----------------------------
@@ -625,7 +668,7 @@ def union_chain(parts: Sequence[LDNI], eps: float = 0.0, capacity: Optional[int]
     once run() has completed (its .n is set by finish())."""
     grid, axis = parts[0].grid, parts[0].axis
     cap = capacity if capacity is not None else int(sum(p.capacity for p in parts))
-    bufs = [empty_layers(grid, axis, cap), empty_layers(grid, axis, cap)]
+    bufs = [empty_layers(grid, axis, cap, parts[0].packed), empty_layers(grid, axis, cap, parts[0].packed)]
     ws = torch.empty(boolean_workspace_size(grid.res), dtype=torch.uint8, device="cuda")
     info = new_info()
 
