@@ -344,6 +344,93 @@ def _node_classify(ldni, lib, U, flush, reps):
             "kernels": nl}
 
 
+def _contouring(ldni, lib, U, flush, reps):
+    """Contouring Steps 2-3 (Section 5.1) of the union's three images: node
+    signs (Step 1), active cells, edge rules, flooding and one QEF per
+    cluster, one CUDA graph replay per measurement, L2 flushed before each."""
+    import ctypes
+    import torch
+    grid = U[0].grid
+    res = grid.res
+    inside = ldni.classify_nodes(U)
+    cells = ldni.contour_cells(U, inside=inside)  # sizes and the reference
+    bound = int(min((res - 1) ** 3, 4 * sum(L.n for L in U) + 6 * (res - 1) ** 2 + 64))
+    ws = torch.empty(ldni.contour_workspace_size(res, bound), dtype=torch.uint8, device="cuda")
+    out = torch.empty(bound * ldni.CELL_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+    info = ldni.new_info()
+    arr = (ldni._CLayers * 3)(*[L.c() for L in U])
+    g = grid.c()
+    nodes_out = torch.empty_like(inside)
+    sz = ctypes.c_size_t(0)
+    lib.ldni_classify_nodes_workspace_size(res, ctypes.byref(sz))
+    nws = torch.empty(sz.value, dtype=torch.uint8, device="cuda")
+
+    def run():
+        ldni.classify_nodes(U, out=nodes_out, ws=nws, info=info, sync=False)
+        lib.ldni_contour_cells(arr, ctypes.byref(g), nodes_out.data_ptr(), bound, out.data_ptr(), bound,
+                               info.data_ptr(), ws.data_ptr(), ws.numel(),
+                               ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    gr, nl = _capture(lib, run)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        gr.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    m = len(cells)
+    same = out[:m * ldni.CELL_DTYPE.itemsize].cpu().numpy().tobytes() == cells.tobytes()
+    ms = float(np.median(ts))
+    return {"workload": f"node signs and cell vertices of the union's three {res}^2 images ({(res - 1) ** 3} cells)",
+            "ms": ms, "cells_with_vertices": int(m), "vertices": int(cells["nvert"].sum()),
+            "cells_per_s": (res - 1) ** 3 / (ms * 1e-3), "graph_equals_eager": bool(same), "kernels": nl}
+
+
+def _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush, reps):
+    """The bench step with approximate 8-bit normals (Section 3 item 1): one
+    word per sample instead of three FP32 normals.  Same learned one-pass
+    sampling, three-image union with the resident knot and volumes, as one
+    CUDA graph; L2 flushed before each replay."""
+    import torch
+    res = grid.res
+    K8 = ldni.sample(kv, kt, grid, "all", check_odd=True, packed=True)
+    lp = ldni.LearnedPlan(vt.shape[0], tt.shape[0], grid, n_sphere, slab_samples=3 * res * res * 4, net=net,
+                          margin=args.margin, feature_stride=32, packed=True)
+    bws = torch.empty(ldni.boolean_many_workspace_size(res, 3), dtype=torch.uint8, device="cuda")
+    vws = torch.empty(ldni.volume_many_workspace_size(res, 3), dtype=torch.uint8, device="cuda")
+    binfo = torch.zeros(3, 4, dtype=torch.int64, device="cuda")
+    vinfo = torch.zeros(3, 4, dtype=torch.int64, device="cuda")
+    U8 = [ldni.empty_layers(grid, a, lp.outs[a].capacity + K8[a].capacity, packed=True) for a in range(3)]
+    vols = torch.zeros(3, dtype=torch.float64, device="cuda")
+
+    def step():
+        lp.run(vt, tt)
+        ldni.boolean_many(lp.outs, K8, "union", outs=U8, ws=bws, infos=binfo, sync=False)
+        ldni.volume_many(U8, out=vols, ws=vws, infos=vinfo, sync=False)
+
+    g, nl = _capture(lib, step)
+    ts = []
+    for _ in range(reps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    lp.finish()
+    ok = all(ldni.info_decode(binfo[j])["status"] == 0 for j in range(3))
+    ms = float(np.median(ts))
+    return {"workload": f"the bench step with 8-bit normals: learned one-pass sampling at {res}^2, "
+                        "three-image union, volumes", "ms": ms, "rays_per_s": 3 * res * res / (ms * 1e-3),
+            "bytes_per_sample": 12, "bytes_per_sample_fp32_normals": 20, "status_ok": bool(ok), "kernels": nl}
+
+
 def _offsetting(ldni, lib, U, flush, reps):
     """Offsetting by sphere unions (Section 4.2), one CUDA graph replay per
     measurement, L2 flushed before each: the flower at 128^2 by 2.5 pixels
@@ -521,6 +608,8 @@ def run_ours(args):
     learned["train"] = train_meta
     next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
     next_rows.update(_offsetting(ldni, lib, U, flush, 10))
+    next_rows["contour_cells"] = _contouring(ldni, lib, U, flush, 10)
+    next_rows["step_packed_normals"] = _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush, 20)
     other = _other_workloads(ldni, lib, flush, 5)
 
     # timed region: K graph replays, per-step events, L2 flushed between steps

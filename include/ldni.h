@@ -409,6 +409,54 @@ int ldni_normals_encode8(const float *nx, const float *ny, const float *nz, int6
  * rounded to nearest. */
 int ldni_normals_decode8(const uint32_t *w, int64_t n, float *nx, float *ny, float *nz, void *stream);
 
+/* ---- contouring, Steps 2-3 (Section 5.1) ------------------------------- */
+
+/* One cell (i, j, k) of the node grid that yields a vertex: its corners are
+ * nodes (i + di, j + dj, k + dk), corner c = di + 2 dj + 4 dk. */
+typedef struct {
+    int64_t cell;    /* i + (res - 1) (j + (res - 1) k) */
+    uint32_t labels; /* 4 bits per corner c at bit 4c: its cluster (= vertex), 0xF inside */
+    uint32_t npts;   /* 8 bits per vertex g at bit 8g: Hermite points fitted (saturating at 255) */
+    int32_t nvert;   /* 1 .. 4 */
+    int32_t pad_;
+    float v[12];     /* vertex g at v[3g], v[3g + 1], v[3g + 2] (x, y, z) */
+} ldni_cell_t;
+
+/* Workspace bytes for ldni_contour_cells at resolution res (2 .. 2048) with
+ * room for max_active cells next to an edge that holds a sample or joins
+ * nodes of different sign. */
+int ldni_contour_workspace_size(int32_t res, int64_t max_active, size_t *bytes_host);
+
+/*
+ * Steps 2 and 3 of the contouring of Section 5.1.  The edge (t, t + 1)
+ * along axis a between grid nodes lies on the ray of image a through its two
+ * other node indices and holds the samples with c_a(t) <= d < c_a(t + 1)
+ * (node coordinates as in ldni_classify_nodes).  Edge types follow the end
+ * signs (inside: from ldni_classify_nodes) and the samples: intersect
+ * (signs differ, samples), none-intersect, empty (same sign, none),
+ * complex.  Rule 1: a complex edge keeps its first and last samples; Rule
+ * 2: an intersect edge keeps, of the samples whose normal's a-component
+ * points from the inside end to the outside end (all samples if none), the
+ * one nearest the edge's midpoint (the earlier on a tie).  In every cell the
+ * outside corners joined by empty edges form clusters, numbered by their
+ * lowest corner; a cluster takes the kept sample of each intersect edge at
+ * one of its corners and, of each complex edge between outside corners, the
+ * sample nearer each corner (a single sample goes to the nearer corner).
+ * Each cluster that meets an intersect, none-intersect or complex edge gets
+ * a vertex at x = m + (A^T A)^+ (A^T b - A^T A m) over its Hermite points p
+ * (rows of A: the normals n; b = n . p; m: the points' mean), eigenvalues of
+ * A^T A below 0.01 of the largest dropped, in FP64; with no points, at the
+ * mean of its corners (npts 0).
+ *   L: host array of the three images x, y, z (FP32 normals); inside: the
+ *   node bits; cells: device array of `capacity` records, written in
+ *   ascending cell order.  info->n[0] = cells with a vertex; beyond capacity
+ *   they are dropped (LDNI_ST_CAPACITY); more than max_active active cells
+ *   also set LDNI_ST_CAPACITY.  No host synchronisation.
+ */
+int ldni_contour_cells(const ldni_layers_t *L, const ldni_grid_t *grid, const uint32_t *inside, int64_t max_active,
+                       ldni_cell_t *cells, int64_t capacity, ldni_info_t *info, void *ws, size_t ws_bytes,
+                       void *stream);
+
 /* ---- offsetting (Section 4.2) ------------------------------------------ */
 
 /* Workspace bytes for ldni_offset of a solid whose three images hold n[0],
@@ -516,7 +564,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -84,7 +84,9 @@ def _regularise(L, a, idx, s_lo, s_hi, c, t):
     return "complex", idx
 
 
-def _qef(P, N):
+def _qef(P, N, ratios=None):
+    """The QEF minimum; ratios, if a list, receives the eigenvalues of A^T A
+    over the largest (how near each is to the 0.01 cut)."""
     P = np.asarray(P, np.float64)
     N = np.asarray(N, np.float64)
     m = P.mean(0)
@@ -92,6 +94,8 @@ def _qef(P, N):
     Atb = N.T @ np.einsum("ij,ij->i", N, P)
     lam, V = np.linalg.eigh(AtA)
     top = lam.max()
+    if ratios is not None:
+        ratios.extend((lam / top).tolist() if top > 0 else [0.0, 0.0, 0.0])
     inv = np.where(lam >= QEF_TRUNC * top, 1.0 / np.where(lam > 0, lam, 1.0), 0.0) if top > 0 else np.zeros(3)
     return m + V @ (inv * (V.T @ (Atb - AtA @ m)))
 
@@ -175,18 +179,19 @@ def cell(Ls, inside, c, res, i, j, k):
                 pts[labels[q]].append(point(a, kept[0], iu, iv))
     if not any(surface):
         return None
-    verts, npts = [], []
+    verts, npts, rat = [], [], []
     for g in range(len(roots)):
+        rat.append([])
         if pts[g]:
             P = [p for p, _ in pts[g]]
             N = [n for _, n in pts[g]]
-            verts.append(_qef(P, N))
+            verts.append(_qef(P, N, rat[-1]))
         else:
             cs = [q for q in range(8) if labels[q] == g]
             verts.append(np.mean([[c[0][i + (q & 1)], c[1][j + ((q >> 1) & 1)], c[2][k + (q >> 2)]]
                                   for q in cs], axis=0).astype(np.float64))
         npts.append(len(pts[g]))
-    return {"labels": labels, "vertices": np.array(verts), "points": npts}
+    return {"labels": labels, "vertices": np.array(verts), "points": npts, "ratios": rat}
 
 
 def contour(Ls, inside, origin, width, res, cells=None):

@@ -41,6 +41,11 @@ class Layers(ctypes.Structure):
                 ("capacity", ctypes.c_int64), ("nrm8", ctypes.c_void_p)]
 
 
+class Cell(ctypes.Structure):
+    _fields_ = [("cell", ctypes.c_int64), ("labels", ctypes.c_uint32), ("npts", ctypes.c_uint32),
+                ("nvert", ctypes.c_int32), ("pad_", ctypes.c_int32), ("v", ctypes.c_float * 12)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("bool_tile_rays", ctypes.c_int32), ("bool_stage_samples", ctypes.c_int32),
                 ("tri_blocks_per_sm", ctypes.c_int32), ("bool_split", ctypes.c_int32)]
@@ -98,6 +103,8 @@ SIGNATURES = {
     "ldni_volume_many": (ctypes.c_int, [_I32, _P, _P, _P, _P, _P, _SZ, _P]),
     "ldni_normals_encode8": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, _P]),
     "ldni_normals_decode8": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P, _P]),
+    "ldni_contour_workspace_size": (ctypes.c_int, [_I32, ctypes.c_int64, ctypes.POINTER(_SZ)]),
+    "ldni_contour_cells": (ctypes.c_int, [_P, _P, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P, _SZ, _P]),
     "ldni_offset_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.c_float, ctypes.c_float, ctypes.POINTER(_SZ)]),
     "ldni_offset": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),

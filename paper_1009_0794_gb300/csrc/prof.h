@@ -41,7 +41,8 @@ enum KernelId : int {
     K_ORDER = 25,
     K_OFFSET = 26,
     K_CODEC = 27,
-    K_NUM = 28
+    K_CONTOUR = 28,
+    K_NUM = 29
 };
 
 struct ProfState {

@@ -574,6 +574,57 @@ def unpack_nodes(words: torch.Tensor, res: int) -> np.ndarray:
     return bits.reshape(res, res, -1)[:, :, :res].astype(bool)
 
 
+# ---- contouring, Steps 2-3 (Section 5.1) ----------------------------------------
+
+CELL_DTYPE = np.dtype([("cell", "<i8"), ("labels", "<u4"), ("npts", "<u4"), ("nvert", "<i4"), ("pad_", "<i4"),
+                       ("v", "<f4", (4, 3))])
+
+
+def contour_workspace_size(res: int, max_active: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_contour_workspace_size(int(res), int(max_active), ctypes.byref(sz)),
+               "ldni_contour_workspace_size")
+    return int(sz.value)
+
+
+def contour_cells(Ls: Sequence[LDNI], inside: Optional[torch.Tensor] = None, max_active: Optional[int] = None,
+                  stream=None) -> np.ndarray:
+    """Cell vertices of Steps 2-3 of the contouring (Section 5.1) from the x,
+    y and z images of one solid: a NumPy structured array (CELL_DTYPE) of the
+    cells that yield a vertex, in ascending cell order.  inside: the node
+    bits of classify_nodes (computed when not given).  One readback at the
+    end; a first bound on the active cells that proves too small is raised
+    once."""
+    lib = _lib.load()
+    grid = Ls[0].grid
+    if len(Ls) != 3 or any(L.grid != grid for L in Ls) or [L.axis for L in Ls] != [0, 1, 2]:
+        raise _lib.LDNIError(-1, "contour_cells needs the x, y and z images of one grid")
+    if inside is None:
+        inside = classify_nodes(Ls, stream=stream)
+    res = grid.res
+    n3 = (res - 1) ** 3
+    bound = int(max_active) if max_active else min(n3, 4 * sum(L.n for L in Ls) + 6 * (res - 1) ** 2 + 64)
+    arr = (_CLayers * 3)(*[L.c() for L in Ls])
+    g = grid.c()
+    info = new_info()
+    for attempt in range(2):
+        bound = max(1, min(bound, n3, 2 ** 31 - 1))
+        ws = torch.empty(contour_workspace_size(res, bound), dtype=torch.uint8, device="cuda")
+        out = torch.empty(bound * CELL_DTYPE.itemsize, dtype=torch.uint8, device="cuda")
+        info.zero_()
+        _lib.check(lib.ldni_contour_cells(arr, ctypes.byref(g), inside.data_ptr(), bound, out.data_ptr(), bound,
+                                          info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream)),
+                   "ldni_contour_cells")
+        meta = info_decode(info)
+        if meta["status"] & _lib.ST_CAPACITY and attempt == 0 and bound < n3:
+            bound = min(n3, 4 * bound)
+            continue
+        _raise_status(meta["status"], "ldni_contour_cells")
+        m = int(meta["n"][0])
+        return out[:m * CELL_DTYPE.itemsize].cpu().numpy().view(CELL_DTYPE)
+    raise _lib.LDNIError(-9, "ldni_contour_cells")
+
+
 # ---- adjoint -------------------------------------------------------------------
 
 def depth_vjp(verts: torch.Tensor, tris: torch.Tensor, L: LDNI, grad_depth: torch.Tensor,
