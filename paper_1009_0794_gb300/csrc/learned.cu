@@ -338,8 +338,10 @@ __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restri
         }
         float3 n;
         face_normal(T.p[0], T.p[1], T.p[2], n.x, n.y, n.z);
-        // coalesced: the gather looks normals up by triangle (w: the packed 8-bit normal)
-        o.nrm[t] = make_float4(n.x, n.y, n.z, __uint_as_float(encode_normal8(n.x, n.y, n.z)));
+        // coalesced: the gather looks normals up by triangle (w: the packed
+        // 8-bit normal, when the images take packed normals)
+        const float w8 = pick3(o.ny, ax_lo) ? 0.0f : __uint_as_float(encode_normal8(n.x, n.y, n.z));
+        o.nrm[t] = make_float4(n.x, n.y, n.z, w8);
         if (ax_lo <= 0 && 0 <= ax_hi) onepass_axis<0>(T, t, n, g.res, o, big_q, qcap, big_n);
         if (ax_lo <= 1 && 1 <= ax_hi) onepass_axis<1>(T, t, n, g.res, o, big_q, qcap, big_n);
         if (ax_lo <= 2 && 2 <= ax_hi) onepass_axis<2>(T, t, n, g.res, o, big_q, qcap, big_n);

@@ -1,6 +1,6 @@
 // Enclosed volume seen by one LDNI: h^2 times the summed lengths of the
 // inside ranges d[2k] .. d[2k+1] of every ray (odd-to-even ranges are inside,
-// Section 2 after Proposition 1).
+// Section 2 after Proposition 1).  Rays with an odd count are skipped.
 //
 // GB300 executes FP64 at a small fraction of its FP32 rate, so the per-ray
 // work stays in FP32: each difference d[2k+1] - d[2k] is split exactly into
@@ -17,7 +17,7 @@ namespace ldni {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kRaysPerThread = 4;
+constexpr int kBlockRays = 4096;                      // rays per block
 
 // The images of one call (blockIdx.y = image), all at one resolution.
 struct VolJobs {
@@ -28,6 +28,12 @@ struct VolJobs {
     ldni_info_t *info[LDNI_MAX_IMAGES];
 };
 
+// One block per kBlockRays rays.  When all of its rays are even, their
+// samples [off[R0], off[R1]) are whole inside ranges one after another (a
+// ray's ranges start at even positions from its first sample), so the block
+// reads them as a contiguous run of (d[2m], d[2m + 1]) pairs, 8-byte loads,
+// with no per-ray bookkeeping.  A block with an odd ray walks its rays one by
+// one and skips the odd ones.
 __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const __grid_constant__ VolJobs J,
                                                           double *partials_all, unsigned *done_all, double h2) {
     const int job = blockIdx.y;
@@ -39,39 +45,45 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
     ldni_info_t *info = J.info[job];
     __shared__ DF sh[kThreads / 32];
     __shared__ bool s_last;
+    __shared__ int s_odd;
+    if (threadIdx.x == 0) s_odd = 0;
+    __syncthreads();
+    const long long R0 = (long long)blockIdx.x * kBlockRays, R1 = min(R0 + kBlockRays, nrays);
+    // parity of every ray of the block: all its offsets even or odd alike
+    int odd = 0;
+    for (long long p = R0 + threadIdx.x; p <= R1; p += kThreads) odd |= (off[p] ^ off[R0]) & 1;
+    if (odd) s_odd = 1;
+    __syncthreads();
     DF acc{0.0f, 0.0f};
-    const long long span = (long long)kThreads * kRaysPerThread;
-    for (long long p0 = blockIdx.x * span + threadIdx.x; p0 < nrays; p0 += (long long)gridDim.x * span) {
-        // kRaysPerThread independent rays: their loads are all in flight together
-        long long b[kRaysPerThread], e[kRaysPerThread];
-#pragma unroll
-        for (int r = 0; r < kRaysPerThread; ++r) {
-            const long long p = p0 + (long long)r * kThreads;
-            b[r] = p < nrays ? off[p] : 0;
-            e[r] = p < nrays ? off[p + 1] : 0;
+    if (!s_odd) {
+        const long long s0 = off[R0], s1 = min((long long)off[R1], cap);
+        const bool aligned = (s0 & 1) == 0;  // 8-byte pairs when the run starts on an even sample
+        for (long long k = s0 + 2LL * threadIdx.x; k + 1 < s1; k += 2LL * kThreads) {
+            float lo, hi;
+            if (aligned) {
+                const float2 v = *reinterpret_cast<const float2 *>(d + k);
+                lo = v.x;
+                hi = v.y;
+            } else {
+                lo = d[k];
+                hi = d[k + 1];
+            }
+            DF diff;
+            two_sum(hi, -lo, diff.hi, diff.lo);
+            acc = df_add(acc, diff);
         }
-#pragma unroll
-        for (int r = 0; r < kRaysPerThread; ++r) {
-            if ((e[r] - b[r]) & 1) {
+    } else {
+        for (long long p = R0 + threadIdx.x; p < R1; p += kThreads) {
+            const long long b = off[p];
+            long long e = off[p + 1];
+            if ((e - b) & 1) {
                 atomicAdd(&info->odd_rays, 1u);
                 set_status(info, LDNI_ST_ODD);
-                e[r] = b[r];
+                continue;
             }
-            if (e[r] > cap) e[r] = cap;
-        }
-        float lo[kRaysPerThread], hi[kRaysPerThread];
-#pragma unroll
-        for (int r = 0; r < kRaysPerThread; ++r) {  // first inside range of every ray
-            const bool has = e[r] - b[r] >= 2;
-            lo[r] = has ? d[b[r]] : 0.0f;
-            hi[r] = has ? d[b[r] + 1] : 0.0f;
-        }
-#pragma unroll
-        for (int r = 0; r < kRaysPerThread; ++r) {
-            DF diff;
-            two_sum(hi[r], -lo[r], diff.hi, diff.lo);
-            acc = df_add(acc, diff);
-            for (long long k = b[r] + 2; k + 1 < e[r]; k += 2) {  // further ranges (multi-layer rays)
+            if (e > cap) e = cap;
+            for (long long k = b; k + 1 < e; k += 2) {
+                DF diff;
                 two_sum(d[k + 1], -d[k], diff.hi, diff.lo);
                 acc = df_add(acc, diff);
             }
@@ -93,9 +105,7 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
 }
 
 int volume_blocks(long long nrays) {
-    long long b = (nrays + (long long)kThreads * kRaysPerThread - 1) / ((long long)kThreads * kRaysPerThread);
-    const long long lim = (long long)num_sms() * 2;  // few blocks: each ends with a reduction and a fence
-    if (b > lim) b = lim;
+    const long long b = (nrays + kBlockRays - 1) / kBlockRays;
     return (int)(b > 0 ? b : 1);
 }
 

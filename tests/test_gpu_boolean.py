@@ -108,6 +108,27 @@ def test_volume_deterministic_and_inclusion_exclusion(ldni):
         assert vU + vI == pytest.approx(vA + vB, rel=1e-12)
 
 
+def test_volume_multilayer_and_odd_rays_skipped(ldni):
+    """Multi-layer rays, and an open mesh whose odd rays the volume skips
+    (their blocks take the ray-by-ray path): the value equals the oracle's
+    on the same image with the odd rays emptied."""
+    grid = ldni.Grid.cube(O3, 1.0, 150)
+    for mesh in (M.flower(96, 96), M.torus_knot(n_ring=128, n_side=16)):
+        for L in ldni.sample(*mesh, grid, "all"):
+            assert ldni.volume(L) == pytest.approx(oracle.volume(L.numpy(), grid.h), rel=1e-12)
+    v, t = M.icosphere(6, r=0.35)
+    for a in range(3):
+        L = ldni.sample(v, t[7:], grid, a)
+        got = float(ldni.volume(L, sync=False).item())
+        X = L.numpy()
+        cnt = np.diff(X["offsets"])
+        assert (cnt % 2).sum() > 0
+        keep = np.repeat(cnt % 2 == 0, cnt)
+        cnt2 = np.where(cnt % 2 == 0, cnt, 0)
+        Y = {"offsets": np.concatenate([[0], np.cumsum(cnt2)]), "depth": X["depth"][keep]}
+        assert got == pytest.approx(oracle.volume(Y, grid.h), rel=1e-12)
+
+
 def test_odd_operand_rejected(ldni):
     v, t = M.icosphere(4, r=0.35)
     grid = ldni.Grid.cube(O3, 1.0, 64)
