@@ -45,7 +45,7 @@ def _stamp() -> str:
     h = hashlib.sha256()
     for f in _sources() + _headers():
         with open(f, "rb") as fh:
-            h.update(f.encode())
+            h.update(os.path.relpath(f, ROOT).encode())  # the same on every checkout
             h.update(fh.read())
     h.update(" ".join(ARCH + NVCC_FLAGS).encode())
     return h.hexdigest()
