@@ -209,49 +209,120 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
     return table.get(kid, 0.0)
 
 
-def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps):
-    """The same step through the public API, inputs copied from pinned host
-    memory and the united LDNIs plus volumes copied back, every step."""
+def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, net=None, margin=0.25,
+            capacities=None):
+    """The same step through the public API (a LearnedPlan with the step's
+    network, boolean_many, volume_many), the mesh copied from pinned host
+    memory and the united LDNIs plus volumes copied back, every step.
+
+    The host never waits for the step it has just queued: the sizes and
+    status words of step k are copied to pinned memory behind its kernels
+    and read at step k + 1, when step k has finished; step k's results are
+    then copied back on one stream while step k + 1 computes, and step
+    k + 1's mesh is copied in on another while step k computes (two input
+    and two result buffers).  The timed region runs from the first input
+    copy to the last result copy of e2e_steps steps."""
     import torch
     hv = torch.from_numpy(sv).pin_memory()
     ht = torch.from_numpy(st).pin_memory()
-    host = None
-    vol_host = torch.empty(3, dtype=torch.float64, pin_memory=True)
+    cap = [int(c) for c in capacities] if capacities else [3 * grid.res * grid.res // 2] * 3
+    plan = ldni.LearnedPlan(len(sv), len(st), grid, cap, slab_samples=3 * grid.res * grid.res * 4, net=net,
+                            margin=margin, feature_stride=32)
+    U = [[ldni.empty_layers(grid, a, cap[a] + K[a].capacity) for a in range(3)] for _ in range(2)]
+    vol_dev = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in range(2)]
+    binfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(2)]
+    vinfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(2)]
+    meta_host = [torch.empty(10, 4, dtype=torch.int64, pin_memory=True) for _ in range(2)]
+    host = [[[torch.empty(u.offsets.numel(), dtype=torch.int32, pin_memory=True)]
+             + [torch.empty(u.capacity, dtype=torch.float32, pin_memory=True) for _ in range(4)]
+             + [torch.empty(u.capacity, dtype=torch.int32, pin_memory=True)] for u in Ub] for Ub in U]
+    vol_host = [torch.empty(3, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+    copy_stream = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    copied = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in copied:
+        e.record()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    d2h = 0
-    for rep in range(2 + e2e_steps):
-        if rep == 2:
-            torch.cuda.synchronize()
-            e0.record()
-            h0 = time.perf_counter()
-        dv = hv.to(dev, non_blocking=True)
-        dt_ = ht.to(dev, non_blocking=True)
-        A = ldni.sample(dv, dt_, grid, "all")
-        vol_dev = torch.zeros(3, dtype=torch.float64, device=dev)
-        res = ldni.boolean_many(A, K, "union", ws=bws)
-        ldni.volume_many(res, out=vol_dev, ws=vws, sync=False)
-        if host is None:
-            host = [[torch.empty(Ua.offsets.numel(), dtype=torch.int32, pin_memory=True)]
-                    + [torch.empty(max(Ua.n, 1) * 2, dtype=torch.float32, pin_memory=True) for _ in range(4)]
-                    + [torch.empty(max(Ua.n, 1) * 2, dtype=torch.int32, pin_memory=True)] for Ua in res]
-        d2h = 0
-        for Ua, hb in zip(res, host):
-            n = Ua.n
-            for s_, h_ in zip([Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]], hb):
-                h_[:s_.numel()].copy_(s_, non_blocking=True)
-                d2h += s_.numel() * s_.element_size()
-        vol_host.copy_(vol_dev, non_blocking=True)
-        d2h += vol_dev.numel() * 8
+    d2h = [0, 0]
+
+    def copy_back(j):
+        """Step j's results to the host (after its sizes are known)."""
+        ready[j].synchronize()
+        m = meta_host[j]
+        words = m[:, 3].tolist()
+        st = 0
+        for r in (0, 1, 2, 3, 4, 5, 9):  # status bits of the volumes, unions and sampling
+            st |= int(words[r]) & 0xffffffff
+        if st:
+            raise RuntimeError(f"e2e step status {st:#x}")
+        nbytes = 0
+        with torch.cuda.stream(copy_stream):
+            for a, (Ua, hb) in enumerate(zip(U[j], host[j])):
+                n = int(m[3 + a, 0])
+                for s_, h_ in zip([Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]], hb):
+                    h_[:s_.numel()].copy_(s_, non_blocking=True)
+                    nbytes += s_.numel() * s_.element_size()
+            vol_host[j].copy_(vol_dev[j], non_blocking=True)
+            nbytes += vol_dev[j].numel() * 8
+            copied[j].record(copy_stream)
+        d2h[j] = nbytes
+
+    dvs = [torch.empty_like(hv, device=dev) for _ in range(2)]
+    dts = [torch.empty_like(ht, device=dev) for _ in range(2)]
+    in_stream = torch.cuda.Stream()
+    in_ready = [torch.cuda.Event(), torch.cuda.Event()]
+    used = [torch.cuda.Event(), torch.cuda.Event()]
+    for e in used:
+        e.record()
+
+    def copy_in(k):
+        """The mesh for a step into input buffer k, on its own stream."""
+        with torch.cuda.stream(in_stream):
+            in_stream.wait_event(used[k])  # the step that read buffer k has finished reading it
+            dvs[k].copy_(hv, non_blocking=True)
+            dts[k].copy_(ht, non_blocking=True)
+            in_ready[k].record(in_stream)
+
+    def run(nsteps):
+        """nsteps whole steps: every input copied in, every result copied back."""
+        copy_in(0)
+        for rep in range(nsteps):
+            k = rep % 2
+            if rep + 1 < nsteps:
+                copy_in(k ^ 1)  # the next step's mesh arrives while this step computes
+            torch.cuda.current_stream().wait_event(in_ready[k])
+            plan.run(dvs[k], dts[k])
+            used[k].record()
+            torch.cuda.current_stream().wait_event(copied[k])  # this result buffer's last copy-back is done
+            ldni.boolean_many(plan.outs, K, "union", ws=bws, outs=U[k], infos=binfo[k], sync=False)
+            ldni.volume_many(U[k], out=vol_dev[k], ws=vws, infos=vinfo[k], sync=False)
+            m = meta_host[k]  # rows: volume infos, union infos, sampling status (row 9)
+            m[0:3].copy_(vinfo[k], non_blocking=True)
+            m[3:6].copy_(binfo[k], non_blocking=True)
+            m[9:10].copy_(plan.info.view(1, 4), non_blocking=True)
+            ready[k].record()
+            if rep > 0:
+                copy_back(k ^ 1)
+        copy_back((nsteps - 1) % 2)
+        torch.cuda.current_stream().wait_stream(copy_stream)
+        torch.cuda.current_stream().wait_stream(in_stream)
+
+    run(3)  # warm-up
+    torch.cuda.synchronize()
+    # timed: e2e_steps steps from the first input copy to the last result copy
+    e0.record()
+    h0 = time.perf_counter()
+    run(e2e_steps)
     e1.record()
     torch.cuda.synchronize()
     wall = 1e3 * (time.perf_counter() - h0) / e2e_steps
     ms = e0.elapsed_time(e1) / e2e_steps
     return {"value": ws * rays_per_step / (ms * 1e-3), "unit": "rays/s",
-            "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(d2h),
+            "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(max(d2h)),
             "ms_per_step": ms, "wall_ms_per_step": wall, "steps": e2e_steps,
-            "api": "paper_1009_0794_gb300.sample / boolean_many / volume_many (exact sizing: one count readback "
-                   "per call)"}
+            "api": "paper_1009_0794_gb300 LearnedPlan.run / boolean_many / volume_many, sizes and status read "
+                   "one step later; the copy-back of a step overlaps the next step"}
 
 
 def _capacity_net(args):
@@ -660,7 +731,8 @@ def run_ours(args):
 
     # end to end through the public API from pinned host buffers
     e2e = None if args.no_e2e else run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step,
-                                           max(3, min(steps, 20)))
+                                           max(3, min(steps, 20)), net=net, margin=args.margin,
+                                           capacities=n_sphere)
 
     if rank != 0:
         if dist:
