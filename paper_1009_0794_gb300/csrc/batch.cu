@@ -127,17 +127,9 @@ __device__ __forceinline__ void batch_axis(const ldni_batch_item_t &it, int m, c
         S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(cnt + (long long)j * res + i, 1); });
         return;
     }
-    const unsigned long long msk = hit_mask(S);
-    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
-    for (int y = 0; y < S.h; ++y) {
-        unsigned long long r = (msk >> (y * S.w)) & row_mask;
-        while (r) {
-            const int x = __ffsll((long long)r) - 1;
-            r &= r - 1;
-            const int i = S.i0 + x, j = S.j0 + y;
-            batch_emit<true>(it, A, (long long)j * res + i, S.depth(i, j), t, n, cnt, info);
-        }
-    }
+    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
+        batch_emit<true>(it, A, (long long)j * res + i, S.depth_from(e0, e1, e2), t, n, cnt, info);
+    });
 }
 
 template <bool kFill>

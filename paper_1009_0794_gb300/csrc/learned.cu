@@ -311,17 +311,9 @@ __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const floa
         enqueue_big(big_q, qcap, big_n, t * 4 + A, (long long)S.w * S.h);
         return;
     }
-    const unsigned long long m = hit_mask(S);
-    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
-    for (int y = 0; y < S.h; ++y) {
-        unsigned long long r = (m >> (y * S.w)) & row_mask;
-        while (r) {
-            const int x = __ffsll((long long)r) - 1;
-            r &= r - 1;
-            const int i = S.i0 + x, j = S.j0 + y;
-            onepass_hit(A, (long long)j * res + i, S.depth(i, j), t, n, S.exiting, o);
-        }
-    }
+    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
+        onepass_hit(A, (long long)j * res + i, S.depth_from(e0, e1, e2), t, n, S.exiting, o);
+    });
 }
 
 __global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restrict__ verts,
@@ -412,17 +404,9 @@ __device__ __forceinline__ void redo_axis(const TriView &T, int t, const float3 
     }
     Setup32 S;
     if (setup_axis<A>(T, res, S) != kSmall) return;  // big triangles: redo_big
-    const unsigned long long m = hit_mask(S);
-    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
-    for (int y = 0; y < S.h; ++y) {
-        unsigned long long r = (m >> (y * S.w)) & row_mask;
-        while (r) {
-            const int x = __ffsll((long long)r) - 1;
-            r &= r - 1;
-            const int i = S.i0 + x, j = S.j0 + y;
-            redo_hit(A, (long long)j * res + i, S.depth(i, j), t, o, n, info);
-        }
-    }
+    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
+        redo_hit(A, (long long)j * res + i, S.depth_from(e0, e1, e2), t, o, n, info);
+    });
 }
 
 __device__ __forceinline__ void redo_big_block(const float *__restrict__ verts, const int *__restrict__ tris, int nv,

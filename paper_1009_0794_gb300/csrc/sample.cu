@@ -86,18 +86,9 @@ __device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &
         S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(o.count[A] + (long long)j * res + i, 1); });
         return;
     }
-    // fill: crossings first, then one store group per crossing (fewer live registers)
-    const unsigned long long m = hit_mask(S);
-    const unsigned long long row_mask = S.w >= 64 ? ~0ull : ((1ull << S.w) - 1);
-    for (int y = 0; y < S.h; ++y) {
-        unsigned long long r = (m >> (y * S.w)) & row_mask;
-        while (r) {
-            const int x = __ffsll((long long)r) - 1;
-            r &= r - 1;
-            const int i = S.i0 + x, j = S.j0 + y;
-            emit<true>(S.depth(i, j), A, t, (long long)j * res + i, n, o, info);
-        }
-    }
+    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
+        emit<true>(S.depth_from(e0, e1, e2), A, t, (long long)j * res + i, n, o, info);
+    });
 }
 
 // One thread per triangle; big triangles are queued (count pass) for big_pass.

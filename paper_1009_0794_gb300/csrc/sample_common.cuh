@@ -79,26 +79,15 @@ struct Setup32 {
         edges(i, j, e0, e1, e2);
         return depth_from(e0, e1, e2);
     }
-    // visit every crossed pixel centre of the box: f(i, j, e0, e1, e2)
+    // visit every crossed pixel centre of the box: f(i, j, e0, e1, e2), with
+    // the biased edge functions at that centre.  A box of at most 2 x 2
+    // pixel centres (nearly every triangle of a mesh finer than the pixel
+    // grid) is tested without a loop, so that the lanes of a warp, whose
+    // boxes differ, run the same instructions; a larger box builds its hit
+    // mask first and then visits the mask's bits.  Either way the crossings
+    // come in row-major order.
     template <class F>
-    __device__ __forceinline__ void for_each_hit(F &&f) const {
-        int r0, r1, r2;
-        edges(i0, j0, r0, r1, r2);
-        const int s0 = -(v1 - v0) * kSubpix, s1 = -(v2 - v1) * kSubpix, s2 = -(v0 - v2) * kSubpix;
-        const int t0 = (u1 - u0) * kSubpix, t1 = (u2 - u1) * kSubpix, t2 = (u0 - u2) * kSubpix;
-        for (int y = 0; y < h; ++y) {
-            int e0 = r0, e1 = r1, e2 = r2;
-            for (int x = 0; x < w; ++x) {
-                if ((e0 > 0) & (e1 > 0) & (e2 > 0)) f(i0 + x, j0 + y, e0, e1, e2);
-                e0 += s0;
-                e1 += s1;
-                e2 += s2;
-            }
-            r0 += t0;
-            r1 += t1;
-            r2 += t2;
-        }
-    }
+    __device__ __forceinline__ void for_each_hit(F &&f) const;
 };
 
 // 64-bit form for triangles too large for Setup32.
@@ -188,6 +177,42 @@ __device__ __forceinline__ unsigned long long hit_mask(const Setup32 &S) {
         r2 += t2;
     }
     return m;
+}
+
+template <class F>
+__device__ __forceinline__ void Setup32::for_each_hit(F &&f) const {
+    if (w <= 2 && h <= 2) {
+        // Edge functions one step beyond the box stay within int32: see kSmallExtent.
+        int r0, r1, r2;
+        edges(i0, j0, r0, r1, r2);
+        const int s0 = -(v1 - v0) * kSubpix, s1 = -(v2 - v1) * kSubpix, s2 = -(v0 - v2) * kSubpix;
+        const int t0 = (u1 - u0) * kSubpix, t1 = (u2 - u1) * kSubpix, t2 = (u0 - u2) * kSubpix;
+        const unsigned w2 = w == 2, h2 = h == 2;
+        const unsigned c00 = (r0 > 0) & (r1 > 0) & (r2 > 0);
+        const unsigned c10 = w2 & (r0 + s0 > 0) & (r1 + s1 > 0) & (r2 + s2 > 0);
+        const unsigned c01 = h2 & (r0 + t0 > 0) & (r1 + t1 > 0) & (r2 + t2 > 0);
+        const unsigned c11 = w2 & h2 & (r0 + s0 + t0 > 0) & (r1 + s1 + t1 > 0) & (r2 + s2 + t2 > 0);
+        unsigned m = c00 | (c10 << 1) | (c01 << 2) | (c11 << 3);  // bit x + 2 y
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int x = b & 1, y = b >> 1;
+            f(i0 + x, j0 + y, r0 + x * s0 + y * t0, r1 + x * s1 + y * t1, r2 + x * s2 + y * t2);
+        }
+        return;
+    }
+    const unsigned long long m = hit_mask(*this);
+    const unsigned long long row_mask = w >= 64 ? ~0ull : ((1ull << w) - 1);
+    for (int y = 0; y < h; ++y) {
+        unsigned long long r = (m >> (y * w)) & row_mask;
+        while (r) {
+            const int x = __ffsll((long long)r) - 1;
+            r &= r - 1;
+            int e0, e1, e2;
+            edges(i0 + x, j0 + y, e0, e1, e2);
+            f(i0 + x, j0 + y, e0, e1, e2);
+        }
+    }
 }
 
 // 64-bit setup of image a for a queued big triangle; false when parallel.
