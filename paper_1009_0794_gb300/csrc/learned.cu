@@ -210,31 +210,43 @@ __global__ void __launch_bounds__(kCapWarps * 32) capacity_kernel(int ntiles, lo
     const bool valid = k < ntiles * naxes;
     const int a = ax_lo + (valid ? k / ntiles : 0), tile = valid ? k % ntiles : 0;
     if (W) {
-        // copy in 32-bit words (pairs of inputs of one unit; rows have an even length)
+        // copy in 32-bit words (pairs of inputs of one unit; rows have an even length), every load of
+        // the thread issued before the first store
+        constexpr int kWords = kMlpWeights / 2, kPer = (kWords + kCapWarps * 32 - 1) / (kCapWarps * 32);
         const bool w_aligned = (reinterpret_cast<uintptr_t>(W) & 3) == 0;
         const unsigned *W2 = reinterpret_cast<const unsigned *>(W);
         const unsigned short *W1 = reinterpret_cast<const unsigned short *>(W);
-        for (int q = threadIdx.x; q < kMlpWeights / 2; q += blockDim.x) {
-            const unsigned v = w_aligned ? W2[q] : ((unsigned)W1[2 * q] | ((unsigned)W1[2 * q + 1] << 16));
-            const int i = 2 * q;
-            int dst;
-            if (i < kW1) {
-                dst = (i / kMlpIn) * kRow0 + (i % kMlpIn) / 2;
-            } else if (i < kW3) {
-                const int base = i < kW2 ? kW1 : kW2, r = i - base;
-                dst = (i < kW2 ? kS1 : kS2) + (r / kMlpHidden) * kRowH + (r % kMlpHidden) / 2;
-            } else {
-                dst = kS3 + (i - kW3) / 2;
-            }
-            sw[dst] = v;
+        unsigned v[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int q = (int)threadIdx.x + r * kCapWarps * 32;
+            v[r] = q >= kWords ? 0u
+                               : (w_aligned ? W2[q] : ((unsigned)W1[2 * q] | ((unsigned)W1[2 * q + 1] << 16)));
         }
-        for (int i = threadIdx.x; i < kMlpBiases; i += blockDim.x) sb[i] = b[i];
+        const float bias = threadIdx.x < kMlpBiases ? b[threadIdx.x] : 0.0f;
         float *x = act[pr][0];
         if (valid && half == 0 && lane == 0) {
             const long long p0 = (long long)tile << kTileBits;
             const float frac = (float)min((long long)kTilePix, nrays - p0) / (float)kTilePix;
             normalise_features(pick3(o.feat, a) + (long long)tile * kRawFeat, frac, x);
         }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int q = (int)threadIdx.x + r * kCapWarps * 32;
+            if (q >= kWords) continue;
+            const int i = 2 * q;
+            int dst;
+            if (i < kW1) {
+                dst = (i / kMlpIn) * kRow0 + (i % kMlpIn) / 2;
+            } else if (i < kW3) {
+                const int base = i < kW2 ? kW1 : kW2, rr = i - base;
+                dst = (i < kW2 ? kS1 : kS2) + (rr / kMlpHidden) * kRowH + (rr % kMlpHidden) / 2;
+            } else {
+                dst = kS3 + (i - kW3) / 2;
+            }
+            sw[dst] = v[r];
+        }
+        if (threadIdx.x < kMlpBiases) sb[threadIdx.x] = bias;
     }
     __syncthreads();
     if (!W) {
@@ -316,7 +328,7 @@ __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const floa
     });
 }
 
-__global__ void __launch_bounds__(kThreads) onepass_kernel(const float *__restrict__ verts,
+__global__ void __launch_bounds__(kThreads, 5) onepass_kernel(const float *__restrict__ verts,
                                                            const int *__restrict__ tris, int nt, int nv, GridDev g,
                                                            int ax_lo, int ax_hi, LImg o, int *big_q, long long qcap,
                                                            int *big_n,
@@ -810,8 +822,10 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
                     ntiles, N, ax_lo, naxes, o, W, B, margin, fixed_layers,
                     reinterpret_cast<unsigned long long *>(w.any_over + 2)));  // 8-byte aligned, cleared
     if (nt > 0) {
+        // as many blocks as stay resident (five per SM at the kernel's register bound)
+        const int op_blocks = (int)min((long long)grid_blocks(nt), (long long)num_sms() * 5);
         LDNI_LAUNCH(K_ONEPASS, s,
-                    onepass_kernel<<<grid_blocks(nt), kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
+                    onepass_kernel<<<op_blocks, kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
                                                                         o, w.big_q, w.qcap, w.big_n, info));
         LDNI_LAUNCH(K_ONEPASS_BIG, s,
                     onepass_big<<<5 * num_sms(), kThreads, 0, s>>>(verts, tris, (int)nv, g, o, w.big_q, w.qcap,
@@ -835,10 +849,13 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     rc = csr_scan(cnt, off, naxes, N, w.scan_words, info, ax_lo, s, nullptr, &ver);
     if (rc != LDNI_OK) return rc;
     if (nt > 0) {
+            // the triangle sweep on as many blocks as stay resident (every block
+        // exits at once when no tile overflowed), the big-triangle queue on a
+        // few more
+        const int tri_blocks = (int)min((long long)grid_blocks(nt), (long long)num_sms() * 4);
         LDNI_LAUNCH(K_REDO, s,
-                    // a small grid: the launch is usually a no-op (no tile overflowed)
-                    redo_kernel<<<num_sms() + num_sms() / 2, kThreads, 0, s>>>(
-                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o, w.big_q, w.qcap, w.big_n, num_sms(), info));
+                    redo_kernel<<<tri_blocks + num_sms() / 2, kThreads, 0, s>>>(
+                        verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi, o, w.big_q, w.qcap, w.big_n, tri_blocks, info));
     }
     LDNI_LAUNCH(K_GATHER, s,
                 gather_kernel<<<dim3(grid_blocks(N), naxes), kThreads, 0, s>>>(N, ax_lo, o, info, overflow_tiles));
