@@ -210,7 +210,7 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
 
 
 def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, net=None, margin=0.25,
-            capacities=None):
+            capacities=None, nbuf=2, nstreams=1, flat=True, union_capacities=None):
     """The same step through the public API (a LearnedPlan with the step's
     network, boolean_many, volume_many), the mesh copied from pinned host
     memory and the united LDNIs plus volumes copied back, every step.
@@ -220,31 +220,43 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
     and read at step k + 1, when step k has finished; step k's results are
     then copied back on one stream while step k + 1 computes, and step
     k + 1's mesh is copied in on another while step k computes (two input
-    and two result buffers).  The timed region runs from the first input
-    copy to the last result copy of e2e_steps steps."""
+    and nbuf result buffers; the copy-back of each image on one of
+    nstreams copy streams).  flat: the three result images live in one
+    allocation, each with room for union_capacities[a] samples (from a
+    sizing call of the same workload; default n_A + n_B, the most a union
+    can have), and come back with one copy of it, unused room included.  The
+    timed region runs from the first input copy to the last result copy of
+    e2e_steps steps."""
     import torch
     hv = torch.from_numpy(sv).pin_memory()
     ht = torch.from_numpy(st).pin_memory()
     cap = [int(c) for c in capacities] if capacities else [3 * grid.res * grid.res // 2] * 3
     plan = ldni.LearnedPlan(len(sv), len(st), grid, cap, slab_samples=3 * grid.res * grid.res * 4, net=net,
                             margin=margin, feature_stride=32)
-    U = [[ldni.empty_layers(grid, a, cap[a] + K[a].capacity) for a in range(3)] for _ in range(2)]
-    vol_dev = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in range(2)]
-    binfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(2)]
-    vinfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(2)]
-    meta_host = [torch.empty(10, 4, dtype=torch.int64, pin_memory=True) for _ in range(2)]
-    host = [[[torch.empty(u.offsets.numel(), dtype=torch.int32, pin_memory=True)]
-             + [torch.empty(u.capacity, dtype=torch.float32, pin_memory=True) for _ in range(4)]
-             + [torch.empty(u.capacity, dtype=torch.int32, pin_memory=True)] for u in Ub] for Ub in U]
-    vol_host = [torch.empty(3, dtype=torch.float64, pin_memory=True) for _ in range(2)]
-    copy_stream = torch.cuda.Stream()
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
-    copied = [torch.cuda.Event(), torch.cuda.Event()]
-    for e in copied:
-        e.record()
+    if flat:
+        ucap = [int(c) for c in union_capacities] if union_capacities else [cap[a] + K[a].n for a in range(3)]
+        UF = [ldni.empty_layers_flat(grid, range(3), ucap) for _ in range(nbuf)]
+        U = [u for u, _ in UF]
+        flat_host = [torch.empty(f.numel(), dtype=torch.uint8, pin_memory=True) for _, f in UF]
+    else:
+        U = [[ldni.empty_layers(grid, a, cap[a] + K[a].capacity) for a in range(3)] for _ in range(nbuf)]
+    vol_dev = [torch.zeros(3, dtype=torch.float64, device=dev) for _ in range(nbuf)]
+    binfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(nbuf)]
+    vinfo = [torch.zeros(3, 4, dtype=torch.int64, device=dev) for _ in range(nbuf)]
+    meta_host = [torch.empty(10, 4, dtype=torch.int64, pin_memory=True) for _ in range(nbuf)]
+    host = [] if flat else [[[torch.empty(u.offsets.numel(), dtype=torch.int32, pin_memory=True)]
+                             + [torch.empty(u.capacity, dtype=torch.float32, pin_memory=True) for _ in range(4)]
+                             + [torch.empty(u.capacity, dtype=torch.int32, pin_memory=True)] for u in Ub] for Ub in U]
+    vol_host = [torch.empty(3, dtype=torch.float64, pin_memory=True) for _ in range(nbuf)]
+    copy_streams = [torch.cuda.Stream() for _ in range(nstreams)]
+    ready = [torch.cuda.Event() for _ in range(nbuf)]
+    copied = [[torch.cuda.Event() for _ in range(nstreams)] for _ in range(nbuf)]
+    for ev in copied:
+        for e in ev:
+            e.record()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    d2h = [0, 0]
+    d2h = [0] * nbuf
 
     def copy_back(j):
         """Step j's results to the host (after its sizes are known)."""
@@ -257,15 +269,25 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
         if st:
             raise RuntimeError(f"e2e step status {st:#x}")
         nbytes = 0
-        with torch.cuda.stream(copy_stream):
-            for a, (Ua, hb) in enumerate(zip(U[j], host[j])):
+        if flat:
+            cs = copy_streams[0]
+            cs.wait_event(ready[j])
+            with torch.cuda.stream(cs):
+                flat_host[j].copy_(UF[j][1], non_blocking=True)
+                nbytes += UF[j][1].numel()
+        for a, (Ua, hb) in enumerate(() if flat else zip(U[j], host[j])):
+            cs = copy_streams[a % nstreams]
+            cs.wait_event(ready[j])
+            with torch.cuda.stream(cs):
                 n = int(m[3 + a, 0])
                 for s_, h_ in zip([Ua.offsets, Ua.depth[:n], Ua.nx[:n], Ua.ny[:n], Ua.nz[:n], Ua.tri[:n]], hb):
                     h_[:s_.numel()].copy_(s_, non_blocking=True)
                     nbytes += s_.numel() * s_.element_size()
+        with torch.cuda.stream(copy_streams[0]):
             vol_host[j].copy_(vol_dev[j], non_blocking=True)
             nbytes += vol_dev[j].numel() * 8
-            copied[j].record(copy_stream)
+        for cs, e in zip(copy_streams, copied[j]):
+            e.record(cs)
         d2h[j] = nbytes
 
     dvs = [torch.empty_like(hv, device=dev) for _ in range(2)]
@@ -284,28 +306,35 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
             dts[k].copy_(ht, non_blocking=True)
             in_ready[k].record(in_stream)
 
+    def compute(k, r):
+        """One step's launches on the current stream: input buffer k, result buffer r."""
+        plan.run(dvs[k], dts[k])
+        used[k].record()
+        for e in copied[r]:  # the result buffer's last copy-back is done
+            torch.cuda.current_stream().wait_event(e)
+        ldni.boolean_many(plan.outs, K, "union", ws=bws, outs=U[r], infos=binfo[r], sync=False)
+        ldni.volume_many(U[r], out=vol_dev[r], ws=vws, infos=vinfo[r], sync=False)
+        m = meta_host[r]  # rows: volume infos, union infos, sampling status (row 9)
+        m[0:3].copy_(vinfo[r], non_blocking=True)
+        m[3:6].copy_(binfo[r], non_blocking=True)
+        m[9:10].copy_(plan.info.view(1, 4), non_blocking=True)
+
     def run(nsteps):
         """nsteps whole steps: every input copied in, every result copied back."""
         copy_in(0)
         for rep in range(nsteps):
-            k = rep % 2
+            k = rep % 2  # input buffer
+            r = rep % nbuf  # result buffer
             if rep + 1 < nsteps:
                 copy_in(k ^ 1)  # the next step's mesh arrives while this step computes
             torch.cuda.current_stream().wait_event(in_ready[k])
-            plan.run(dvs[k], dts[k])
-            used[k].record()
-            torch.cuda.current_stream().wait_event(copied[k])  # this result buffer's last copy-back is done
-            ldni.boolean_many(plan.outs, K, "union", ws=bws, outs=U[k], infos=binfo[k], sync=False)
-            ldni.volume_many(U[k], out=vol_dev[k], ws=vws, infos=vinfo[k], sync=False)
-            m = meta_host[k]  # rows: volume infos, union infos, sampling status (row 9)
-            m[0:3].copy_(vinfo[k], non_blocking=True)
-            m[3:6].copy_(binfo[k], non_blocking=True)
-            m[9:10].copy_(plan.info.view(1, 4), non_blocking=True)
-            ready[k].record()
+            compute(k, r)
+            ready[r].record()
             if rep > 0:
-                copy_back(k ^ 1)
-        copy_back((nsteps - 1) % 2)
-        torch.cuda.current_stream().wait_stream(copy_stream)
+                copy_back((rep - 1) % nbuf)
+        copy_back((nsteps - 1) % nbuf)
+        for cs in copy_streams:
+            torch.cuda.current_stream().wait_stream(cs)
         torch.cuda.current_stream().wait_stream(in_stream)
 
     run(3)  # warm-up
@@ -321,8 +350,11 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
     return {"value": ws * rays_per_step / (ms * 1e-3), "unit": "rays/s",
             "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(max(d2h)),
             "ms_per_step": ms, "wall_ms_per_step": wall, "steps": e2e_steps,
-            "api": "paper_1009_0794_gb300 LearnedPlan.run / boolean_many / volume_many, sizes and status read "
-                   "one step later; the copy-back of a step overlaps the next step"}
+            "api": "paper_1009_0794_gb300 LearnedPlan.run / boolean_many / volume_many into empty_layers_flat "
+                   "images, sizes and status read one step later; the copy-back of a step overlaps the next step",
+            "result_buffers": nbuf, "copy_streams": nstreams,
+            "copy_back": "one copy of the three union images' single allocation per step" if flat else
+                         "one copy per array, used samples only"}
 
 
 def _capacity_net(args):
@@ -732,7 +764,7 @@ def run_ours(args):
     # end to end through the public API from pinned host buffers
     e2e = None if args.no_e2e else run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step,
                                            max(3, min(steps, 20)), net=net, margin=args.margin,
-                                           capacities=n_sphere)
+                                           capacities=n_sphere, union_capacities=n_union)
 
     if rank != 0:
         if dist:

@@ -178,6 +178,31 @@ def empty_layers(grid: Grid, axis: int, capacity: int, packed: bool = False) -> 
                 nrm8=i(capacity) if packed else None)
 
 
+def empty_layers_flat(grid: Grid, axes: Sequence[int], capacities: Sequence[int], packed: bool = False):
+    """Device buffers of several images carved from one allocation (every
+    array 256-byte aligned), so that a caller can move all of them with a
+    single copy.  Returns (images, the flat uint8 tensor behind them)."""
+    N = grid.res * grid.res
+    plan = []  # (element count, dtype) per array, in allocation order
+    for cap in capacities:
+        nc = 0 if packed else int(cap)
+        plan.append([(N + 1, torch.int32), (int(cap), torch.float32), (nc, torch.float32), (nc, torch.float32),
+                     (nc, torch.float32), (int(cap), torch.int32)] + ([(int(cap), torch.int32)] if packed else []))
+    align = lambda b: (b + 255) // 256 * 256
+    total = sum(align(4 * k) for arrs in plan for k, _ in arrs)
+    flat = torch.empty(max(total, 256), dtype=torch.uint8, device="cuda")
+    at = 0
+    out = []
+    for axis, arrs in zip(axes, plan):
+        views = []
+        for k, dt in arrs:
+            views.append(flat[at:at + 4 * k].view(dt))
+            at += align(4 * k)
+        nrm8 = views[6] if packed else None
+        out.append(LDNI(grid, int(axis), *views[:6], 0, nrm8=nrm8))
+    return out, flat
+
+
 def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=None,
            check_odd: bool = False, packed: bool = False) -> Union[LDNI, List[LDNI]]:
     """Sample a closed mesh into LDNIs (Section 3, Definitions 1-4); packed:

@@ -203,6 +203,27 @@ def test_many_images_in_one_call(ldni, split):
         tune.set(**prev)
 
 
+def test_results_in_one_allocation(ldni):
+    """Outputs carved from one allocation (empty_layers_flat) hold the same
+    bits as separately allocated ones, and one copy of the allocation brings
+    all of them to the host."""
+    (fv, ft), (kv, kt) = M.flower(64, 64), M.torus_knot(n_ring=96, n_side=12)
+    LA, LB = _pairs(ldni, (fv, ft), (kv, kt), 96)
+    outs, flat = ldni.empty_layers_flat(LA[0].grid, range(3), [A.n + B.n for A, B in zip(LA, LB)])
+    assert flat.data_ptr() % 256 == 0
+    for X in outs:
+        for t in (X.offsets, X.depth, X.nx, X.ny, X.nz, X.tri):
+            assert t.data_ptr() % 256 == 0
+            assert flat.data_ptr() <= t.data_ptr() and t.data_ptr() + 4 * t.numel() <= flat.data_ptr() + flat.numel()
+    got = ldni.boolean_many(LA, LB, "union", outs=outs)
+    host = flat.cpu()  # every image with one copy
+    for a in range(3):
+        ref = ldni.boolean(LA[a], LB[a], "union").numpy()
+        assert bit_equal(got[a].numpy(), ref)
+        off = (got[a].offsets.data_ptr() - flat.data_ptr())
+        assert np.array_equal(host[off:off + 4 * got[a].offsets.numel()].view(torch.int32).numpy(), ref["offsets"])
+
+
 def _ldni_from_rays(ldni, grid, rays, seed):
     """An LDNI whose ray p holds the sorted depths rays[p] (other rays empty),
     with seeded unit normals and distinct triangle ids."""
