@@ -47,7 +47,9 @@ def _stamp() -> str:
         with open(f, "rb") as fh:
             h.update(os.path.relpath(f, ROOT).encode())  # the same on every checkout
             h.update(fh.read())
-    h.update(" ".join(ARCH + NVCC_FLAGS).encode())
+    # include directories relative to the repository, like the file names
+    flags = [os.path.relpath(f, ROOT) if os.path.isabs(f) else f for f in NVCC_FLAGS]
+    h.update(" ".join(ARCH + flags).encode())
     return h.hexdigest()
 
 

@@ -82,3 +82,22 @@ def test_tuning_knobs_validate_on_host():
     assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and (t.bool_tile_rays, t.tri_blocks_per_sm) == (512, 4)
     assert lib.ldni_set_tuning(None) == 0
     assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 256
+
+
+def test_build_stamp_is_the_same_in_another_checkout(tmp_path):
+    """The stamp that names a build's sources (and keys the recorded ncu
+    traffic) depends on the sources and flags, not on where the repository
+    sits: a copy of the tree elsewhere gives the same stamp."""
+    import importlib.util
+    import shutil
+    from paper_1009_0794_gb300 import build
+    root = os.path.dirname(os.path.dirname(os.path.abspath(build.__file__)))
+    pkg_copy = tmp_path / "elsewhere" / "paper_1009_0794_gb300"
+    shutil.copytree(os.path.join(root, "paper_1009_0794_gb300", "csrc"), pkg_copy / "csrc")
+    shutil.copytree(os.path.join(root, "include"), tmp_path / "elsewhere" / "include")
+    shutil.copy(build.__file__, pkg_copy / "build.py")
+    spec = importlib.util.spec_from_file_location("build_copy", pkg_copy / "build.py")
+    copy = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(copy)
+    assert copy.ROOT != build.ROOT
+    assert copy._stamp() == build._stamp()
