@@ -624,7 +624,28 @@ def _other_workloads(ldni, lib, flush, reps):
     parts = cplan.finish()
     chains = [ldni.union_chain([parts[k][a] for k in range(64)]) for a in range(3)]
     ms_c, nl_c = timed(lambda: [run() for run, _ in chains])
-    return {"batch_256": {"workload": f"256 meshes, {tris} triangles, resolutions 64..512, three images each, "
+    # the adjoint of the volume (Section 2's volume, differentiated per kept crossing) on the 200,000-
+    # triangle noisy icosphere at 512^2: one launch per image into one gradient buffer
+    av, at = meshgen.icosphere(100, r=0.35, noise=0.03, noise_kind="octave", seed=12)
+    agrid = ldni.Grid.cube(o, 1.0, 512)
+    avt = torch.from_numpy(av).cuda()
+    att = torch.from_numpy(at).cuda()
+    AL = ldni.sample(avt, att, agrid, "all")
+    grad = torch.zeros(len(av), 3, dtype=torch.float32, device="cuda")
+
+    def adjoint():
+        grad.zero_()
+        for L in AL:
+            ldni.volume_grad(avt, att, L, 1.0, grad_verts=grad)
+
+    ms_a, nl_a = timed(adjoint)
+    n_a = sum(L.n for L in AL)
+    ab_a = sum(8.0 * L.n + 12.0 * len(at) + 24.0 * len(av) for L in AL)  # tri_id + depth, mesh, gradient
+    return {"adjoint_200k_512": {"workload": f"volume gradient of the {len(at)}-triangle noisy icosphere at 512^2, "
+                                             f"three images, {n_a} kept crossings", "ms": ms_a,
+                                 "crossings_per_s": n_a / (ms_a * 1e-3), "algorithmic_bytes": ab_a,
+                                 "gbs": ab_a / (ms_a * 1e-3) / 1e9, "kernels": nl_a},
+            "batch_256": {"workload": f"256 meshes, {tris} triangles, resolutions 64..512, three images each, "
                                       "one batch call", "ms": ms_b, "rays_per_s": rays / (ms_b * 1e-3),
                           "meshes_per_s": 256 / (ms_b * 1e-3), "kernels": nl_b},
             "union_chain_64": {"workload": "64 translated 20,000-triangle tori at 512^2: 63 unions per image, "
