@@ -810,7 +810,7 @@ def run_ours(args):
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tj = _json.load(fh)
         name = lib.ldni_kernel_name(dominant).decode()
-        if name in tj and tj[name].get("source_hash") == _source_hash():
+        if name in tj and tj[name].get("source_hash") == _source_hash(tj[name].get("unit")):
             traffic = tj[name]["bytes_per_launch"]
             ncu_note = {k: tj[name][k] for k in ("alu_pipe_pct", "issue_active_pct", "dram_pct") if k in tj[name]}
             ncu_note["from"] = "profiles/traffic.json (ncu --set full of this kernel, same sources)"
@@ -856,9 +856,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def _source_hash() -> str:
+def _source_hash(unit=None) -> str:
+    """The build stamp, or with `unit` (a csrc file name) the stamp of that
+    translation unit and every header."""
     from paper_1009_0794_gb300 import build as b
-    return b._stamp()[:16]
+    return b._stamp(None if unit is None else [unit])[:16]
 
 
 def main():

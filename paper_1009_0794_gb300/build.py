@@ -41,9 +41,13 @@ def _headers():
     return sorted(hs)
 
 
-def _stamp() -> str:
+def _stamp(units=None) -> str:
+    """Hash of the sources (every .cu file, or only `units`, file names in
+    csrc), every header and the flags: it names the build, and, per unit,
+    the code of the kernels a recorded profile was taken from."""
     h = hashlib.sha256()
-    for f in _sources() + _headers():
+    srcs = _sources() if units is None else sorted(os.path.join(CSRC, u) for u in units)
+    for f in srcs + _headers():
         with open(f, "rb") as fh:
             h.update(os.path.relpath(f, ROOT).encode())  # the same on every checkout
             h.update(fh.read())

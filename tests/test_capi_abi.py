@@ -101,3 +101,4 @@ def test_build_stamp_is_the_same_in_another_checkout(tmp_path):
     spec.loader.exec_module(copy)
     assert copy.ROOT != build.ROOT
     assert copy._stamp() == build._stamp()
+    assert copy._stamp(["learned.cu"]) == build._stamp(["learned.cu"]) != build._stamp()
