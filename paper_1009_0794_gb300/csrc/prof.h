@@ -57,6 +57,14 @@ struct ProfState {
 ProfState &prof_state();
 std::atomic<uint64_t> &launch_counter();
 
+// Inside a stream capture the record becomes a graph node that fires on
+// every replay (external record); outside one it is an ordinary record.
+inline unsigned record_flags(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess) cs = cudaStreamCaptureStatusNone;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+}
+
 inline int prof_begin(int id, cudaStream_t s) {
     launch_counter().fetch_add(1, std::memory_order_relaxed);
     ProfState &P = prof_state();
@@ -65,14 +73,13 @@ inline int prof_begin(int id, cudaStream_t s) {
     if (!P.begin[slot] || !P.end[slot]) return -1;
     P.next++;
     if (P.ids) P.ids[slot] = id;
-    // External: inside a stream capture the record becomes a graph node that fires on every replay
-    cudaEventRecordWithFlags(P.begin[slot], s, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(P.begin[slot], s, record_flags(s));
     return slot;
 }
 
 inline void prof_end(int slot, cudaStream_t s) {
     if (slot < 0) return;
-    cudaEventRecordWithFlags(prof_state().end[slot], s, cudaEventRecordExternal);
+    cudaEventRecordWithFlags(prof_state().end[slot], s, record_flags(s));
 }
 
 }  // namespace ldni
