@@ -61,6 +61,14 @@ def whole_job_rate(world: int, units_per_step: float, steps: int, max_ms: float)
     return world * units_per_step * steps / (max_ms * 1e-3)
 
 
+# Slab slots per ray of the one-pass sampler (workspace only: a tile touches
+# only the slots it reserves).  Tiles reserve in whatever order their
+# blocks run, and those that no longer fit are redone exactly; eight layers
+# per ray leave room for every capacity the network gives the bench mesh, so
+# that no tile's place depends on that order.
+SLAB_LAYERS = 8
+
+
 def _meshes():
     import meshgen
     return meshgen.scale_sphere(), meshgen.torus_knot(2, 3, 0.25, 0.1, 0.035, 256, 32)
@@ -231,7 +239,7 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
     hv = torch.from_numpy(sv).pin_memory()
     ht = torch.from_numpy(st).pin_memory()
     cap = [int(c) for c in capacities] if capacities else [3 * grid.res * grid.res // 2] * 3
-    plan = ldni.LearnedPlan(len(sv), len(st), grid, cap, slab_samples=3 * grid.res * grid.res * 4, net=net,
+    plan = ldni.LearnedPlan(len(sv), len(st), grid, cap, slab_samples=SLAB_LAYERS * 3 * grid.res * grid.res, net=net,
                             margin=margin, feature_stride=32)
     if flat:
         ucap = [int(c) for c in union_capacities] if union_capacities else [cap[a] + K[a].n for a in range(3)]
@@ -501,7 +509,7 @@ def _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush, re
     import torch
     res = grid.res
     K8 = ldni.sample(kv, kt, grid, "all", check_odd=True, packed=True)
-    lp = ldni.LearnedPlan(vt.shape[0], tt.shape[0], grid, n_sphere, slab_samples=3 * res * res * 4, net=net,
+    lp = ldni.LearnedPlan(vt.shape[0], tt.shape[0], grid, n_sphere, slab_samples=SLAB_LAYERS * 3 * res * res, net=net,
                           margin=args.margin, feature_stride=32, packed=True)
     bws = torch.empty(ldni.boolean_many_workspace_size(res, 3), dtype=torch.uint8, device="cuda")
     vws = torch.empty(ldni.volume_many_workspace_size(res, 3), dtype=torch.uint8, device="cuda")
@@ -687,7 +695,7 @@ def run_ours(args):
     n_sphere = [L.n for L in A0]
     plan = ldni.SamplePlan(len(sv), len(st), grid, n_sphere)
     net, train_meta = _capacity_net(args)
-    lplan = ldni.LearnedPlan(len(sv), len(st), grid, n_sphere, slab_samples=3 * RES * RES * 4, net=net,
+    lplan = ldni.LearnedPlan(len(sv), len(st), grid, n_sphere, slab_samples=SLAB_LAYERS * 3 * RES * RES, net=net,
                              margin=args.margin, feature_stride=32)
     main_plan = lplan if args.mode == "learned1" else plan
     bws = torch.empty(ldni.boolean_many_workspace_size(RES, 3), dtype=torch.uint8, device=dev)

@@ -114,8 +114,8 @@ __device__ __forceinline__ void feature_axis(const TriView &T, bool valid, float
         if ((threadIdx.x & 31) == 0) {
             float *f = pick3(o.feat, A) + (long long)t * kRawFeat;
             atomicAdd(f + 0, (float)__popc(grp) * w);
-            atomicAdd(f + 1, ar);
-            atomicAdd(f + 2, an);
+            atomicAdd(reinterpret_cast<unsigned *>(f + 1), to_fixed(ar, kAreaFix));
+            atomicAdd(reinterpret_cast<unsigned *>(f + 2), to_fixed(an, kNormalFix));
 #pragma unroll
             for (int k = 0; k < 8; ++k)
                 if (bins[k]) atomicAdd(f + 3 + k, (float)bins[k] * w);

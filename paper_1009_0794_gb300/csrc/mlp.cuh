@@ -21,7 +21,15 @@ constexpr int kW0 = 0, kW1 = kMlpHidden * kMlpIn, kW2 = kW1 + kMlpHidden * kMlpH
 constexpr int kB0 = 0, kB1 = kMlpHidden, kB2 = 2 * kMlpHidden, kB3 = 3 * kMlpHidden;
 
 // Raw tile feature accumulators (features kernel) and their normalised form.
+// Every accumulator adds with an order-independent result, so the features,
+// the capacities and a network trained on them are the same run to run:
+// the count and the histogram bins add whole numbers (exact in FP32 below
+// 2^24), and the area and the |n_a| sum are kept as unsigned fixed-point
+// words (1/16 pixel, 1/256) in their float slots.
 constexpr int kRawFeat = 11;  // count, area, sum |n_a|, 8-bin depth histogram
+constexpr float kAreaFix = 16.0f, kNormalFix = 256.0f;
+
+__device__ __forceinline__ unsigned to_fixed(float x, float scale) { return __float2uint_rn(x * scale); }
 
 // x[0] log1p(count), x[1] log1p(area in pixels), x[2] mean |n_a|,
 // x[3..10] depth histogram / count, x[11] fraction of the tile inside the image
@@ -29,8 +37,8 @@ __device__ __forceinline__ void normalise_features(const float *raw, float npix_
     const float c = raw[0];
     const float inv = c > 0.0f ? 1.0f / c : 0.0f;
     x[0] = log1pf(c);
-    x[1] = log1pf(raw[1]);
-    x[2] = raw[2] * inv;
+    x[1] = log1pf((float)__float_as_uint(raw[1]) * (1.0f / kAreaFix));
+    x[2] = (float)__float_as_uint(raw[2]) * (1.0f / kNormalFix) * inv;
 #pragma unroll
     for (int k = 0; k < 8; ++k) x[3 + k] = raw[3 + k] * inv;
     x[11] = npix_frac;
