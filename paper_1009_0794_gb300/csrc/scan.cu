@@ -150,38 +150,83 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
 }
 
 // ---- two-launch form: the kernels ------------------------------------------------
+//
+// Each kernel meets at one barrier: warps reduce or scan with shuffles and
+// leave one value per warp (and per slice) in shared memory, which every
+// thread then adds up itself.
+
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ long long warp_sum(long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ long long warp_inclusive(long long x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
 
 __global__ void __launch_bounds__(kThreads) scan_sums(AxisPtrs ap, long long N, int nchunk, long long *sums) {
-    __shared__ long long sh[kThreads / 32 + 1];
+    __shared__ long long sh[kWarps];
     const int a = blockIdx.y, c = blockIdx.x;
     const long long base = (long long)c * kChunk;
     int4 v[kSlices];
     long long tsum[kSlices];
     load_chunk(ap.counts[a], base, N, v, tsum);
     verify_chunk(ap, a, c, base, N, v);
-    long long total;
-    block_exclusive_scan<kThreads>(tsum[0] + tsum[1] + tsum[2] + tsum[3], sh, &total);
-    if (threadIdx.x == 0) sums[(size_t)a * nchunk + c] = total;
+    const long long ws = warp_sum(tsum[0] + tsum[1] + tsum[2] + tsum[3]);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = ws;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long total = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) total += sh[w];
+        sums[(size_t)a * nchunk + c] = total;
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) scan_prefix(AxisPtrs ap, long long N, int nchunk, const long long *sums,
                                                         ldni_info_t *info, int info_base) {
-    __shared__ long long sh[kThreads / 32 + 1];
+    __shared__ long long sh[kSlices + 1][kWarps];  // per slice: warp totals; last row: warp sums of `before`
     const int a = blockIdx.y, c = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)c * kChunk;
     int4 v[kSlices];
     long long tsum[kSlices];
     load_chunk(ap.counts[a], base, N, v, tsum);
-    long long before = 0;  // sum of the chunk sums before c
+    long long before = 0;  // this thread's share of the chunk sums before c
     for (int k = threadIdx.x; k < c; k += kThreads) before += sums[(size_t)a * nchunk + k];
-    long long b0;
-    block_exclusive_scan<kThreads>(before, sh, &b0);
+    long long incl[kSlices];
+#pragma unroll
+    for (int m = 0; m < kSlices; ++m) incl[m] = warp_inclusive(tsum[m], lane);
+    before = warp_sum(before);
+    if (lane == 31) {
+#pragma unroll
+        for (int m = 0; m < kSlices; ++m) sh[m][warp] = incl[m];
+    }
+    if (lane == 0) sh[kSlices][warp] = before;
+    __syncthreads();
+    long long b0 = 0;  // offset of the chunk's first ray
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) b0 += sh[kSlices][w];
     long long excl[kSlices];
-    long long carry = 0;
+    long long carry = 0;  // rays of the slices before m
 #pragma unroll
     for (int m = 0; m < kSlices; ++m) {
-        long long tot;
-        excl[m] = carry + block_exclusive_scan<kThreads>(tsum[m], sh, &tot);
+        long long lead = 0, tot = 0;  // warps before this one in slice m; the whole slice
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const long long t = sh[m][w];
+            tot += t;
+            if (w < warp) lead += t;
+        }
+        excl[m] = carry + lead + incl[m] - tsum[m];
         carry += tot;
     }
     int *out = ap.offsets[a];
