@@ -10,7 +10,10 @@
  * Conventions shared by every call
  *  - All data pointers are DEVICE pointers (CUDA global memory of the current
  *    device) unless a parameter says "host".  The caller owns every buffer;
- *    the library allocates nothing and keeps no device state between calls.
+ *    the library allocates nothing and keeps no device state between calls,
+ *    with one exception: the static scratch array of ldni_boolean_static
+ *    (4 MiB + 8.5 KiB on every GPU that loads the library, for res <= 1024;
+ *    calls of that entry point that overlap on the GPU race on it).
  *  - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
  *    NULL = legacy default stream).  Host-side validation errors are returned
  *    immediately; conditions found on the device (capacity exceeded, odd
@@ -361,9 +364,12 @@ int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t
  * The paper has no counterpart; this is a deployment variant.
  * Scratch: one static device array of 4 MiB + 8.5 KiB in the library, held by
  * every GPU that loads the library until the process exits.  Limit: res <=
- * 1024, else LDNI_ETOOLARGE.  The first call on a device looks up that
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  No call allocates or frees memory.
+ * 1024, else LDNI_ETOOLARGE.  The first call in a CUDA context (the
+ * device's primary context, another context of that device, or the primary
+ * context made again after cudaDeviceReset) looks up that array's device
+ * address in the context (cudaGetSymbolAddress) and caches it per context;
+ * make that first call before any stream capture.  No call allocates or
+ * frees memory.
  * All calls share the array: calls whose work overlaps on the GPU (two
  * streams, or two host threads) race and corrupt each other's results;
  * serialise them.  Each call writes every scratch word it reads, so the

@@ -22,6 +22,8 @@
 #include <climits>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "dfloat.cuh"
 #include "ldni_host.h"
 #include "lookback.cuh"
@@ -1000,25 +1002,73 @@ constexpr size_t kStaticScratchBytes =
 
 static __device__ __align__(256) unsigned char g_bool_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
-void *g_static_ptr[kMaxDevices] = {nullptr};
+// The array's device address belongs to a CUDA context, not to a device
+// ordinal: a non-primary context of the same device, or the primary context
+// made again after cudaDeviceReset, has its own copy of the array.  Addresses
+// are therefore cached per context, keyed by the driver's context id, which
+// no later context of the process reuses.  The two driver calls are reached
+// through the runtime, so the library links no driver library.
+using CtxGetCurrentFn = CUresult(CUDAAPI *)(CUcontext *);
+using CtxGetIdFn = CUresult(CUDAAPI *)(CUcontext, unsigned long long *);
 
-// Device address of the static scratch on the current device.  The host-side
-// symbol is only a stand-in, so the address is looked up once per device.
-int static_scratch(void **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LDNI_ECUDA;
-    std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_bool_static_scratch) != cudaSuccess || !p) {
+constexpr int kMaxContexts = 64;
+std::mutex g_static_mu;
+struct StaticEntry {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+StaticEntry g_static[kMaxContexts] = {};
+int g_static_n = 0;
+CtxGetCurrentFn g_ctx_current = nullptr;
+CtxGetIdFn g_ctx_id = nullptr;
+
+// Id of the calling thread's current context; false when there is none or
+// the driver cannot say.  Holds g_static_mu.
+bool current_context_id(unsigned long long *id) {
+    if (!g_ctx_current || !g_ctx_id) {
+        void *f0 = nullptr, *f1 = nullptr;
+        cudaDriverEntryPointQueryResult q0, q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f0, 12000, cudaEnableDefault, &q0) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            q0 != cudaDriverEntryPointSuccess || q1 != cudaDriverEntryPointSuccess || !f0 || !f1) {
             cudaGetLastError();
-            return LDNI_ECUDA;
+            return false;
         }
-        g_static_ptr[dev] = p;
+        g_ctx_current = reinterpret_cast<CtxGetCurrentFn>(f0);
+        g_ctx_id = reinterpret_cast<CtxGetIdFn>(f1);
     }
-    *out = g_static_ptr[dev];
+    CUcontext ctx = nullptr;
+    if (g_ctx_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the static scratch in the current context.  The
+// host-side symbol is only a stand-in, so the address is looked up once per
+// context (cudaGetSymbolAddress also makes the device's primary context
+// current when the thread has none yet).
+int static_scratch(void **out) {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    unsigned long long id = 0;
+    const bool known = current_context_id(&id);
+    if (known)
+        for (int k = 0; k < g_static_n; ++k)
+            if (g_static[k].ctx_id == id) {
+                *out = g_static[k].ptr;
+                return LDNI_OK;
+            }
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_bool_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return LDNI_ECUDA;
+    }
+    if (known || current_context_id(&id)) {  // the lookup may have made the context
+        int slot = -1;
+        for (int k = 0; k < g_static_n && slot < 0; ++k)
+            if (g_static[k].ctx_id == id) slot = k;
+        if (slot < 0) slot = g_static_n < kMaxContexts ? g_static_n++ : (int)(id % kMaxContexts);
+        g_static[slot] = StaticEntry{id, p};
+    }
+    *out = p;
     return LDNI_OK;
 }
 
