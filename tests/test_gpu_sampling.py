@@ -1,6 +1,8 @@
 """CUDA sampling through the C ABI against the FP64 oracle (Definitions 1-4,
 Remark 1, Section 3).  Counts and triangle ids bit-exact, depths within
 1e-5 of the cube diagonal, normals within 1e-5."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -121,19 +123,48 @@ def test_open_mesh_reports_odd_rays(ldni):
         ldni.sample(v, t_open, grid, 2, check_odd=True)
 
 
+def _guarded_layers(ldni, grid, axis, cap, guard, fill):
+    """Output arrays of one image carved from a single allocation, with
+    `guard` words of `fill` before, between and after them."""
+    N = grid.res * grid.res
+    sizes = [N + 1, cap, cap, cap, cap, cap]  # offsets, depth, nx, ny, nz, tri
+    backing = torch.full((sum(sizes) + guard * (len(sizes) + 1),), fill, dtype=torch.int32, device="cuda")
+    views, guards, at = [], [backing[:guard]], guard
+    for k in sizes:
+        views.append(backing[at:at + k])
+        guards.append(backing[at + k:at + k + guard])
+        at += k + guard
+    f = lambda t: t.view(torch.float32)
+    L = ldni.LDNI(grid, axis, views[0], f(views[1]), f(views[2]), f(views[3]), f(views[4]), views[5], 0)
+    return L, guards
+
+
 def test_capacity_overflow_flagged_not_written(ldni):
+    """Outputs of half the needed size, each array fenced by guard words in
+    the same allocation: the overflow is reported and no write lands outside
+    the arrays."""
     A, _ = M.pr1_pair()
     grid = ldni.Grid.cube(O3, 1.0, 64)
     exact = ldni.sample(*A, grid, "all")
     caps = [L.n for L in exact]
-    plan = ldni.SamplePlan(len(A[0]), len(A[1]), grid, [c // 2 for c in caps])
-    guard = [torch.full((1024,), 7.0, device="cuda") for _ in range(2)]
+    lib = ldni._lib.load()
     vt = torch.from_numpy(A[0]).cuda()
     tt = torch.from_numpy(A[1]).cuda()
-    plan.run(vt, tt)
-    with pytest.raises(ldni.LDNIError):
-        plan.finish()
-    assert all(float(g.min()) == 7.0 == float(g.max()) for g in guard)
+    fill = 0x7F5A5A5A
+    outs, guards = zip(*[_guarded_layers(ldni, grid, a, caps[a] // 2, 1024, fill) for a in range(3)])
+    arr = (ldni._CLayers * 3)(*[o.c() for o in outs])
+    ws = torch.empty(ldni.sample_workspace_size(len(A[0]), len(A[1]), 64), dtype=torch.uint8, device="cuda")
+    info = ldni.new_info()
+    g = grid.c()
+    rc = lib.ldni_sample(vt.data_ptr(), vt.shape[0], tt.data_ptr(), tt.shape[0], ctypes.byref(g), 3, 0, arr,
+                         info.data_ptr(), ws.data_ptr(), ws.numel(), None)
+    assert rc == 0
+    meta = ldni.info_decode(info)
+    assert meta["status"] & ldni._lib.ST_CAPACITY
+    assert [meta["n"][a] for a in range(3)] == caps  # the sizes needed
+    for gs in guards:
+        for gd in gs:
+            assert bool((gd == fill).all())
     plan2 = ldni.SamplePlan(len(A[0]), len(A[1]), grid, caps)
     plan2.run(vt, tt)
     outs = plan2.finish()
