@@ -2,10 +2,12 @@
 
 Workload (one GPU): the 1,310,720-triangle noisy geodesic sphere (frequency
 256, r 0.35, 4-octave radial noise of amplitude 0.05) sampled into the three
-1024^2 LDNIs (exact two-pass), united per axis with a resident LDNI set of a
-(2,3) torus-knot tube (16,384 triangles, sampled once before timing), and
-the volume of each united image.  One step = that whole pass over all rays
-of the three images; value = 3 * 1024^2 rays / step time.
+1024^2 LDNIs (one-pass sampling with the learned per-tile capacity by
+default, --mode exact2 for the exact two-pass form), united per axis with a
+resident LDNI set of a (2,3) torus-knot tube (16,384 triangles, sampled once
+before timing), and the volume of each united image (from the same Boolean
+call).  One step = that whole pass over all rays of the three images;
+value = 3 * 1024^2 rays / step time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -220,7 +222,7 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
 def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, net=None, margin=0.25,
             capacities=None, nbuf=2, nstreams=1, flat=True, union_capacities=None):
     """The same step through the public API (a LearnedPlan with the step's
-    network, boolean_many, volume_many), the mesh copied from pinned host
+    network, boolean_many with the union volumes), the mesh copied from pinned host
     memory and the united LDNIs plus volumes copied back, every step.
 
     The host never waits for the step it has just queued: the sizes and
@@ -320,8 +322,7 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
         used[k].record()
         for e in copied[r]:  # the result buffer's last copy-back is done
             torch.cuda.current_stream().wait_event(e)
-        ldni.boolean_many(plan.outs, K, "union", ws=bws, outs=U[r], infos=binfo[r], sync=False)
-        ldni.volume_many(U[r], out=vol_dev[r], ws=vws, infos=vinfo[r], sync=False)
+        ldni.boolean_many(plan.outs, K, "union", ws=bws, outs=U[r], infos=binfo[r], sync=False, vols=vol_dev[r])
         m = meta_host[r]  # rows: volume infos, union infos, sampling status (row 9)
         m[0:3].copy_(vinfo[r], non_blocking=True)
         m[3:6].copy_(binfo[r], non_blocking=True)
@@ -358,7 +359,7 @@ def run_e2e(ldni, dev, grid, sv, st, K, bws, vws, ws, rays_per_step, e2e_steps, 
     return {"value": ws * rays_per_step / (ms * 1e-3), "unit": "rays/s",
             "h2d_bytes_per_step": int(sv.nbytes + st.nbytes), "d2h_bytes_per_step": int(max(d2h)),
             "ms_per_step": ms, "wall_ms_per_step": wall, "steps": e2e_steps,
-            "api": "paper_1009_0794_gb300 LearnedPlan.run / boolean_many / volume_many into empty_layers_flat "
+            "api": "paper_1009_0794_gb300 LearnedPlan.run / boolean_many (with the union volumes) into empty_layers_flat "
                    "images, sizes and status read one step later; the copy-back of a step overlaps the next step",
             "result_buffers": nbuf, "copy_streams": nstreams,
             "copy_back": "one copy of the three union images' single allocation per step" if flat else
@@ -520,8 +521,7 @@ def _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush, re
 
     def step():
         lp.run(vt, tt)
-        ldni.boolean_many(lp.outs, K8, "union", outs=U8, ws=bws, infos=binfo, sync=False)
-        ldni.volume_many(U8, out=vols, ws=vws, infos=vinfo, sync=False)
+        ldni.boolean_many(lp.outs, K8, "union", outs=U8, ws=bws, infos=binfo, sync=False, vols=vols)
 
     g, nl = _capture(lib, step)
     ts = []
@@ -708,8 +708,8 @@ def run_ours(args):
 
     def step():
         main_plan.run(vt, tt)
-        ldni.boolean_many(main_plan.outs, K, "union", outs=U, ws=bws, infos=binfo, sync=False)
-        ldni.volume_many(U, out=vols, ws=vws, infos=vinfo, sync=False)
+        # the union's volumes come out of the same call (summed while its sizes are counted)
+        ldni.boolean_many(main_plan.outs, K, "union", outs=U, ws=bws, infos=binfo, sync=False, vols=vols)
 
     import ctypes
     for w in range(max(args.warmup, 3)):

@@ -145,6 +145,10 @@ typedef struct {
 /* Human-readable text for a return code (static storage, never NULL). */
 const char *ldni_strerror(int code);
 
+/* Text of the CUDA error behind the calling thread's most recent
+ * LDNI_ECUDA (static storage, never NULL; "no CUDA error" before any). */
+const char *ldni_last_cuda_error(void);
+
 /* Library version as major*10000 + minor*100 + patch. */
 int ldni_version(void);
 

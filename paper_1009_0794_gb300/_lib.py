@@ -16,6 +16,7 @@ _lock = threading.Lock()
 _lib = None
 
 LDNI_OK = 0
+LDNI_ECUDA = -6
 AXIS_ALL = 3
 MODE_EXACT2 = 0
 MODE_LEARNED1 = 1
@@ -62,7 +63,13 @@ INFO_BYTES = 32  # ldni_info_t: int64 n[3]; uint32 status; uint32 odd_rays
 class LDNIError(RuntimeError):
     def __init__(self, code: int, what: str):
         self.code = code
-        super().__init__(f"{what}: {strerror(code)} ({code})")
+        detail = ""
+        if code == LDNI_ECUDA:
+            try:
+                detail = ": " + load().ldni_last_cuda_error().decode()
+            except Exception:
+                detail = ""
+        super().__init__(f"{what}: {strerror(code)} ({code}){detail}")
 
 
 _P = ctypes.c_void_p
@@ -76,6 +83,7 @@ _PL = ctypes.POINTER(Layers)
 SIGNATURES = {
     "ldni_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "ldni_version": (ctypes.c_int, []),
+    "ldni_last_cuda_error": (ctypes.c_char_p, []),
     "ldni_grid_from_bbox": (ctypes.c_int, [_P, _I32, _PG]),
     "ldni_sample_workspace_size": (ctypes.c_int, [_I64, _I64, _I32, _I32, ctypes.POINTER(_SZ)]),
     "ldni_sample": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _I32, _PL, _P, _P, _SZ, _P]),

@@ -353,9 +353,9 @@ extern "C" int ldni_sample_batch(const ldni_batch_item_t *items_dev, const ldni_
         chunks += 3 * ((N + kScanChunk - 1) / kScanChunk);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(w.counts, 0, w.counts_bytes, s) != cudaSuccess) return LDNI_ECUDA;
-    if (cudaMemsetAsync(w.words, 0, w.words_bytes, s) != cudaSuccess) return LDNI_ECUDA;
-    if (cudaMemsetAsync(infos, 0, sizeof(ldni_info_t) * (size_t)count, s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.counts, 0, w.counts_bytes, s))) return rc_;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.words, 0, w.words_bytes, s))) return rc_;
+    if (int rc_ = cuda_check(cudaMemsetAsync(infos, 0, sizeof(ldni_info_t) * (size_t)count, s))) return rc_;
     LDNI_LAUNCH(K_BATCH, s, setup_kernel<<<1, kThreads, 0, s>>>(items_dev, count, w.T));
     if (tris > 0) {
         LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<false><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,

@@ -13,10 +13,12 @@
 // pass over the output.
 //
 // Three forms share that merge:
-//   - one launch per image (bool_tiled): a block counts its tile of rays,
-//     scans, finds its first output slot by decoupled look-back and writes;
+//   - one launch per image (bool_tiled): a block stages its tile's sample
+//     arrays in shared memory with bulk copies, counts its rays, scans,
+//     finds its first output slot by decoupled look-back and writes;
 //   - three launches per image (bool_count, bool_scan_tiles, bool_write):
-//     no block ever waits for another;
+//     no block ever waits for another; the result's volume, when asked for,
+//     is summed by the count pass and finished by the tile scan;
 //   - the two-pass form behind ldni_boolean_static (bool_pass + csr_scan).
 // Launch shapes are chosen by the tuning knobs (ldni_set_tuning).
 #include <climits>
@@ -24,6 +26,7 @@
 
 #include <cuda.h>
 
+#include "bulk.cuh"
 #include "dfloat.cuh"
 #include "ldni_host.h"
 #include "lookback.cuh"
@@ -302,40 +305,48 @@ __global__ void __launch_bounds__(kThreads) bool_pass(long long nrays, Side A, S
 //
 // One block owns a tile of kR * 256 consecutive rays; thread t owns the kR
 // consecutive rays t*kR .. t*kR + kR - 1, so one block scan orders the tile
-// and offsets move as vectors.  The depths of the tile's samples are
-// contiguous in both operands (CSR rows in ray order): the block copies the
-// two ranges into shared memory with coalesced loads and merges from there.
-// It then
-//   1. counts every ray's output samples,
+// and offsets move as vectors.  The samples of the tile are contiguous in
+// both operands (CSR rows in ray order): one thread copies the two ranges of
+// every sample array (depths, normals, triangle ids) into shared memory with
+// asynchronous bulk copies, the depths on one barrier and the rest on
+// another, so the normals are still landing while the block merges.  The
+// block then
+//   1. counts every ray's output samples from the staged depths,
 //   2. scans the counts, obtains the tile's first output slot by decoupled
 //      look-back and writes the tile's CSR offsets,
 //   3. merges again, recording for each output sample its source (operand
-//      and index) in shared memory,
-//   4. writes the tile's output samples in order: depth from shared memory,
-//      normal and triangle id gathered from the source; consecutive threads
-//      write consecutive samples.
+//      and index) in shared memory, and sums the result's inside lengths
+//      when the volume is asked for,
+//   4. writes the tile's output samples in order from shared memory;
+//      consecutive threads write consecutive samples.
 // A tile whose two ranges exceed the shared-memory budget (or a budget of 0)
-// merges every ray from global memory instead; results are the same.
-constexpr int kStageUnroll = 8;  // staged loads in flight per thread
-constexpr int kGather = 4;       // output samples gathered per thread and step
+// merges every ray from global memory instead; results are the same.  When
+// an array does not start on a 16-byte boundary, the staging uses plain
+// loads instead of bulk copies.
+constexpr int kStageUnroll = 8;  // staged loads in flight per thread (plain staging)
+constexpr int kGather = 4;       // output samples written per thread and step
 
 __device__ __forceinline__ int clamp_local(long long x, long long cap_rel) {  // x >= 0
     return cap_rel < 0 ? 0 : (int)min(x, cap_rel);
 }
 
-// Copy n floats from global to shared memory, kStageUnroll loads in flight per thread.
-__device__ __forceinline__ void stage_range(const float *__restrict__ src, int n, float *dst) {
+// Copy elements [g0, g1) of a 4-byte array to dst[i - floor4(g0)] with plain
+// loads, kStageUnroll in flight per thread.
+__device__ __forceinline__ void stage_plain(const uint32_t *__restrict__ src, long long g0, long long g1,
+                                            uint32_t *dst) {
+    const long long s = g0 & ~3ll;
+    const int n = (int)(g1 - g0), off = (int)(g0 - s);
     for (int k0 = threadIdx.x; k0 < n; k0 += kBoolThreads * kStageUnroll) {
-        float v[kStageUnroll];
+        uint32_t v[kStageUnroll];
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
             const int k = k0 + u * kBoolThreads;
-            v[u] = k < n ? src[k] : 0.0f;
+            v[u] = k < n ? src[g0 + k] : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kStageUnroll; ++u) {
             const int k = k0 + u * kBoolThreads;
-            if (k < n) dst[k] = v[u];
+            if (k < n) dst[off + k] = v[u];
         }
     }
 }
@@ -370,6 +381,18 @@ __device__ __forceinline__ void store_rows(int *dst, long long p0, int q, int nr
     }
 }
 
+// The staged copy of one operand's tile range: array k (0 depth, then the
+// normal arrays, last the triangle ids) at arr(k), element i of the range
+// (tile-local) at arr(k)[off + i].
+struct StagedSide {
+    uint32_t *base;  // array k at base + k * stride
+    int stride;
+    int narr;  // 5 (FP32 normals) or 3 (packed normals)
+    int off;
+    __device__ __forceinline__ uint32_t *arr(int k) const { return base + k * stride; }
+    __device__ __forceinline__ const float *d() const { return reinterpret_cast<const float *>(base) + off; }
+};
+
 template <int kR>
 struct TileIn {
     int la[kR + 1], lb[kR + 1];  // rows q0 .. q0 + kR, tile-local and clamped to capacity
@@ -377,13 +400,25 @@ struct TileIn {
     long long ga0, gb0;          // first kept sample of the tile
     int LA, LB;                  // kept samples of the tile
     bool staged;
+    StagedSide sa, sb;
 };
 
-// Rows of this thread's rays, the tile's sample ranges and, if they fit the
-// budget, their depths in shared memory.  Ends with a barrier.
+__device__ __forceinline__ const uint32_t *side_array(const Side &S, int k, int narr) {
+    if (k == 0) return reinterpret_cast<const uint32_t *>(S.d);
+    if (k == narr - 1) return reinterpret_cast<const uint32_t *>(S.tri);
+    return reinterpret_cast<const uint32_t *>(k == 1 ? S.nx : (k == 2 ? S.ny : S.nz));
+}
+
+// Rows of this thread's rays and the tile's sample ranges; if they fit the
+// budget, the staging of every sample array is started: depths complete on
+// bars[0], the other arrays on bars[1] (bulk copies when `bulk`, else plain
+// loads, complete on return).  Ends with a barrier after which the depths
+// are in shared memory (or the tile is not staged).  False when a bounded
+// wait gave up (LDNI_ST_TIMEOUT recorded).
 template <int kR>
-__device__ __forceinline__ void tile_prologue(const Side &A, const Side &B, long long p_begin, int nr, int budget,
-                                              float *sd, long long *sh4, TileIn<kR> &T, ldni_info_t *info) {
+__device__ __forceinline__ bool tile_prologue(const Side &A, const Side &B, long long p_begin, int nr, int budget,
+                                              bool bulk, uint32_t *stage, uint64_t *bars, long long *sh4,
+                                              TileIn<kR> &T, ldni_info_t *info) {
     const int q0 = threadIdx.x * kR;
     int ra[kR + 1], rb[kR + 1];
     load_rows<kR>(A.off, p_begin, q0, nr, ra);
@@ -391,6 +426,10 @@ __device__ __forceinline__ void tile_prologue(const Side &A, const Side &B, long
     if (threadIdx.x == 0) {
         sh4[0] = ra[0];
         sh4[1] = rb[0];
+        if (bulk) {
+            mbar_init(bars, 1);
+            mbar_init(bars + 1, 1);
+        }
     }
     if (q0 < nr && q0 + kR >= nr) {  // this thread holds the tile's end row
 #pragma unroll
@@ -416,20 +455,60 @@ __device__ __forceinline__ void tile_prologue(const Side &A, const Side &B, long
         if (k < kR && q0 + k < nr && (((ra[k + 1] - ra[k]) | (rb[k + 1] - rb[k])) & 1)) T.odd |= 1u << k;
     }
     if (threadIdx.x == 0 && (endA > A.cap || endB > B.cap)) set_status(info, LDNI_ST_CAPACITY);
-    T.staged = budget > 0 && (long long)T.LA + T.LB <= budget;
-    if (T.staged) {
-        stage_range(A.d + T.ga0, T.LA, sd);
-        stage_range(B.d + T.gb0, T.LB, sd + T.LA);
+    const int narr = A.ny ? 5 : 3;
+    T.sa.narr = T.sb.narr = narr;
+    T.sa.off = (int)(T.ga0 & 3);
+    T.sb.off = (int)(T.gb0 & 3);
+    const int SA = (T.sa.off + T.LA + 3) & ~3, SB = (T.sb.off + T.LB + 3) & ~3;  // words per staged array
+    T.staged = budget > 0 && SA + SB <= budget;
+    if (!T.staged) return true;  // block-uniform
+    T.sa.base = stage;
+    T.sa.stride = SA;
+    T.sb.base = stage + narr * SA;
+    T.sb.stride = SB;
+    const long long ga1 = T.ga0 + T.LA, gb1 = T.gb0 + T.LB;
+    if (bulk) {
+        if (threadIdx.x == 0) {
+            const uint32_t bA = (uint32_t)max(0ll, ((ga1 & ~3ll) - (T.ga0 & ~3ll)) * 4);
+            const uint32_t bB = (uint32_t)max(0ll, ((gb1 & ~3ll) - (T.gb0 & ~3ll)) * 4);
+            mbar_arrive_expect(bars, bA + bB);
+            bulk_range4(T.sa.arr(0), A.d, T.ga0, ga1, bars);
+            bulk_range4(T.sb.arr(0), B.d, T.gb0, gb1, bars);
+            mbar_arrive_expect(bars + 1, (uint32_t)(narr - 1) * (bA + bB));
+            for (int k = 1; k < narr; ++k) {
+                bulk_range4(T.sa.arr(k), side_array(A, k, narr), T.ga0, ga1, bars + 1);
+                bulk_range4(T.sb.arr(k), side_array(B, k, narr), T.gb0, gb1, bars + 1);
+            }
+        }
+        // the at most three elements past each body, by plain loads (threads 4 (2k + s) .. + 3)
+        const int grp = threadIdx.x >> 2;
+        if (grp < 2 * narr) {
+            const int k = grp >> 1;
+            const bool sb = grp & 1;
+            const long long g0 = sb ? T.gb0 : T.ga0, g1 = sb ? gb1 : ga1;
+            const long long e = g1 & ~3ll, i = e + (threadIdx.x & 3);
+            if (i < g1 && i >= g0) (sb ? T.sb : T.sa).arr(k)[i - (g0 & ~3ll)] = side_array(sb ? B : A, k, narr)[i];
+        }
+    } else {
+        for (int k = 0; k < narr; ++k) {
+            stage_plain(side_array(A, k, narr), T.ga0, ga1, T.sa.arr(k));
+            stage_plain(side_array(B, k, narr), T.gb0, gb1, T.sb.arr(k));
+        }
     }
-    __syncthreads();
+    __syncthreads();  // plain loads visible
+    if (!bulk) return true;
+    const bool landed = mbar_wait(bars, 0);
+    if (__syncthreads_and(landed)) return true;  // the same answer in every thread
+    if (threadIdx.x == 0) set_status(info, LDNI_ST_TIMEOUT);
+    return false;
 }
 
 // Output counts of this thread's rays (and the odd-count check).
 template <int kR>
 __device__ __forceinline__ int tile_counts(const TileIn<kR> &T, const Side &A, const Side &B, int op, float eps,
-                                           int nr, const float *sd, int (&cnt)[kR], ldni_info_t *info) {
+                                           int nr, int (&cnt)[kR], ldni_info_t *info) {
     const int q0 = threadIdx.x * kR;
-    const float *sA = sd, *sB = sd + T.LA;
+    const float *sA = T.sa.d(), *sB = T.sb.d();
     int mine = 0;
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
@@ -453,11 +532,12 @@ __device__ __forceinline__ int tile_counts(const TileIn<kR> &T, const Side &A, c
 
 // CSR offsets of this thread's rays, then the tile's output samples from
 // output slot `base` on (this thread's first sample is at base + excl).
+// vacc gains the inside lengths of this thread's rays when want_vol.
 template <int kR>
-__device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, const Side &B, int op, float eps,
+__device__ __forceinline__ bool tile_emit(const TileIn<kR> &T, const Side &A, const Side &B, int op, float eps,
                                           const Out &o, long long p_begin, int nr, const int (&cnt)[kR], int excl,
-                                          long long base, long long total, const float *sd, int *pick,
-                                          ldni_info_t *info) {
+                                          long long base, long long total, int *pick, bool bulk, uint64_t *bars,
+                                          bool want_vol, DF &vacc, ldni_info_t *info) {
     const int q0 = threadIdx.x * kR;
     {
         int w[kR];
@@ -480,13 +560,16 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
                                           [&](bool pb, long long pi, bool cb, long long ci, int m) {
                                               emit_global(pb, pi, A, B, op, o, at + m, info);
                                               emit_global(cb, ci, A, B, op, o, at + m + 1, info);
+                                              if (want_vol)
+                                                  vacc = df_add(vacc, df_diff((cb ? B.d : A.d)[ci],
+                                                                              (pb ? B.d : A.d)[pi]));
                                           });
             }
             run += cnt[k];
         }
-        return;  // block-uniform: no barrier follows on this path
+        return true;  // block-uniform: no barrier follows on this path
     }
-    const float *sA = sd, *sB = sd + T.LA;
+    const float *sA = T.sa.d(), *sB = T.sb.d();
     {
         int run = excl;
 #pragma unroll
@@ -497,39 +580,45 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
                                     [&](bool pb, int pi, bool cb, int ci, int m) {
                                         pick[at + m] = pb ? (int)(0x80000000u | (unsigned)pi) : pi;
                                         pick[at + m + 1] = cb ? (int)(0x80000000u | (unsigned)ci) : ci;
+                                        if (want_vol) vacc = df_add(vacc, df_diff((cb ? sB : sA)[ci], (pb ? sB : sA)[pi]));
                                     });
             }
             run += cnt[k];
         }
     }
+    bool ok = true;
+    if (bulk && !mbar_wait(bars + 1, 0)) {
+        set_status(info, LDNI_ST_TIMEOUT);
+        ok = false;
+    }
     __syncthreads();
     const int tot = (int)total;
-    const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
+    const bool inv = op == LDNI_OP_DIFF;
+    const bool three = T.sa.narr == 5;
+    const int kt = T.sa.narr - 1;
     for (int k0 = threadIdx.x; k0 < tot; k0 += kBoolThreads * kGather) {
-        float d[kGather], x[kGather], y[kGather], z[kGather];
-        int t[kGather];
+        uint32_t d[kGather], x[kGather], y[kGather], z[kGather], t[kGather];
 #pragma unroll
         for (int u = 0; u < kGather; ++u) {
             const int k = k0 + u * kBoolThreads;
             if (k < tot) {
                 const int code = pick[k];
-                const int i = code & 0x7fffffff;
                 const bool fb = code < 0;
-                const long long g = (fb ? T.gb0 : T.ga0) + i;
-                d[u] = fb ? sB[i] : sA[i];
-                x[u] = (fb ? B.nx : A.nx)[g];
-                y[u] = o.ny ? (fb ? B.ny : A.ny)[g] : 0.0f;
-                z[u] = o.ny ? (fb ? B.nz : A.nz)[g] : 0.0f;
-                t[u] = (fb ? B.tri : A.tri)[g];
+                const int stride = fb ? T.sb.stride : T.sa.stride;
+                const uint32_t *src = (fb ? T.sb.base : T.sa.base) + (code & 0x7fffffff) + (fb ? T.sb.off : T.sa.off);
+                d[u] = src[0];
+                x[u] = src[stride];
+                y[u] = three ? src[2 * stride] : 0u;
+                z[u] = three ? src[3 * stride] : 0u;
+                t[u] = src[kt * stride];
                 if (fb) {
-                    if (o.ny) {
-                        x[u] *= sg;
-                        y[u] *= sg;
-                        z[u] *= sg;
-                    } else if (sg < 0.0f) {
-                        x[u] = __uint_as_float(__float_as_uint(x[u]) ^ kInvert8);
+                    if (inv) {  // FP32: negate; packed: every code q -> 255 - q
+                        const uint32_t m = three ? 0x80000000u : kInvert8;
+                        x[u] ^= m;
+                        y[u] ^= three ? m : 0u;
+                        z[u] ^= three ? m : 0u;
                     }
-                    t[u] = (int)((unsigned)t[u] | 0x80000000u);
+                    t[u] |= 0x80000000u;
                 }
             }
         }
@@ -542,34 +631,44 @@ __device__ __forceinline__ void tile_emit(const TileIn<kR> &T, const Side &A, co
                 set_status(info, LDNI_ST_CAPACITY);
                 continue;
             }
-            o.d[at] = d[u];
-            o.nx[at] = x[u];
-            if (o.ny) {
-                o.ny[at] = y[u];
-                o.nz[at] = z[u];
+            o.d[at] = __uint_as_float(d[u]);
+            o.nx[at] = __uint_as_float(x[u]);
+            if (three) {
+                o.ny[at] = __uint_as_float(y[u]);
+                o.nz[at] = __uint_as_float(z[u]);
             }
-            o.tri[at] = t[u];
+            o.tri[at] = (int)t[u];
         }
     }
+    return ok;
 }
 
 // Tickets run over all jobs' tiles in order: ticket t is tile t % tpj of job
-// t / tpj; each job has its own look-back words (words + job * tpj).
+// t / tpj; each job has its own look-back words (words + job * tpj); word
+// tpj * njobs is the ticket counter, the next one counts finished tiles.
+// With volumes asked for, each tile leaves its summed inside lengths in
+// tile_vol[ticket], and the block that finishes last adds every job's
+// partials in a fixed order.
 template <int kR>
 __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __grid_constant__ BoolJobs J, int op,
                                                            float eps, unsigned long long *words, int tpj, int njobs,
-                                                           int budget) {
+                                                           int budget, bool bulk, double *tile_vol, double h2) {
     constexpr int kRays = kR * kBoolThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *sd = reinterpret_cast<float *>(smem_raw);  // [budget] A depths, then B depths
-    int *pick = reinterpret_cast<int *>(sd + budget);  // [budget] source of every output sample
+    const int narr = J.A[0].ny ? 5 : 3;
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem_raw);      // [narr][budget] words
+    int *pick = reinterpret_cast<int *>(stage + narr * budget);    // [budget] source of every output sample
+    __shared__ __align__(8) uint64_t bars[2];
     __shared__ long long sh[kBoolThreads / 32 + 1];
     __shared__ long long sh4[4];
     __shared__ int s_tile;
     __shared__ long long s_base;
+    __shared__ DF s_df[kBoolThreads / 32];
+    __shared__ bool s_last;
     if (threadIdx.x == 0) s_tile = (int)atomicAdd(words + (size_t)tpj * njobs, 1ull);
     __syncthreads();
-    const int job = s_tile / tpj, tile = s_tile - job * tpj;
+    const int ticket = s_tile;
+    const int job = ticket / tpj, tile = ticket - job * tpj;
     const Side &A = J.A[job];
     const Side &B = J.B[job];
     const Out &o = J.o[job];
@@ -577,9 +676,12 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
     const long long p_begin = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p_begin);
     TileIn<kR> T;
-    tile_prologue<kR>(A, B, p_begin, nr, budget, sd, sh4, T, info);
+    const bool ok = tile_prologue<kR>(A, B, p_begin, nr, budget, bulk, stage, bars, sh4, T, info);
     int cnt[kR];
-    const int mine = tile_counts<kR>(T, A, B, op, eps, nr, sd, cnt, info);
+    const int mine = ok ? tile_counts<kR>(T, A, B, op, eps, nr, cnt, info) : 0;
+    if (!ok)
+#pragma unroll
+        for (int k = 0; k < kR; ++k) cnt[k] = 0;
     long long total;
     const int excl = (int)block_exclusive_scan<kBoolThreads>(mine, sh, &total);
     if (threadIdx.x < 32) {
@@ -589,7 +691,28 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
     __syncthreads();
     const long long base = s_base;
     if (tile == tpj - 1 && threadIdx.x == 0) finish_output(o, N, base + total, info);
-    tile_emit<kR>(T, A, B, op, eps, o, p_begin, nr, cnt, excl, base, total, sd, pick, info);
+    const bool want_vol = tile_vol != nullptr;
+    DF vacc{0.0f, 0.0f};
+    if (ok) tile_emit<kR>(T, A, B, op, eps, o, p_begin, nr, cnt, excl, base, total, pick, bulk, bars, want_vol, vacc,
+                          info);
+    else if (T.staged && bulk)  // a copy may still be landing: give it a bounded while before the block ends
+        mbar_wait(bars + 1, 0);
+    if (!want_vol) return;  // block-uniform
+    const DF tsum = df_block_sum<kBoolThreads>(vacc, s_df);
+    if (threadIdx.x == 0) {
+        tile_vol[ticket] = (double)tsum.hi + (double)tsum.lo;
+        __threadfence();
+        s_last = atomicAdd(words + (size_t)tpj * njobs + 1, 1ull) == (unsigned long long)(tpj * njobs - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;  // block-uniform
+    __threadfence();
+    double *shd = reinterpret_cast<double *>(smem_raw);  // the stage is no longer needed
+    for (int j = 0; j < njobs; ++j) {
+        const double v = fixed_order_sum<kBoolThreads>(tile_vol + (size_t)j * tpj, tpj, shd);
+        if (threadIdx.x == 0) *J.vol[j] = v * h2;
+        __syncthreads();
+    }
 }
 
 // ---- three launches per image -----------------------------------------------
@@ -604,7 +727,8 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 // before the launch).
 template <int kR>
 __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const __grid_constant__ BoolJobs J, int op,
-                                                              float eps, unsigned long long *tile_total, int tpj) {
+                                                              float eps, unsigned long long *tile_total, int tpj,
+                                                              float2 *warp_vol) {
     constexpr int kRays = kR * kBoolThreads;
     const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
     const Side &A = J.A[job];
@@ -642,17 +766,33 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
     }
     int cnt[kR];
     int mine = 0;
+    // inside lengths of the result (its volume, when asked for): each kept interval [x, y] adds
+    // y - x as an exact pair of floats, summed in double-float (FP32 arithmetic: this GPU's FP64
+    // rate would double the pass)
+    const bool want_vol = warp_vol != nullptr;
+    DF len{0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         if (kind[k] == 3) {
             const long long a = min((long long)ra[k], A.cap), b = min((long long)rb[k], B.cap);
             const int na = (int)(min((long long)ra[k + 1], A.cap) - a), nb = (int)(min((long long)rb[k + 1], B.cap) - b);
-            cnt[k] = merge_core<int>(A.d + a, 0, na, B.d + b, 0, nb, op, eps, NoEmit{});
+            const float *dA = A.d + a, *dB = B.d + b;
+            if (want_vol)
+                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int) {
+                    len = df_add(len, df_diff((cb ? dB : dA)[ci], (pb ? dB : dA)[pi]));
+                });
+            else
+                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, NoEmit{});
         } else if (kind[k] == 4) {
             int src[4];
             cnt[k] = two_two(op, eps, d0[k], d1[k], e0[k], e1[k], src);
+            if (want_vol) {
+                const float dd[4] = {d0[k], d1[k], e0[k], e1[k]};
+                for (int m = 0; m < cnt[k]; m += 2) len = df_add(len, df_diff(dd[src[m + 1]], dd[src[m]]));
+            }
         } else {
             cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
+            if (want_vol && cnt[k]) len = df_add(len, df_diff(d1[k], d0[k]));
         }
         mine += cnt[k];
     }
@@ -660,13 +800,20 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, w);
     if ((threadIdx.x & 31) == 0 && mine) atomicAdd(tile_total + blockIdx.x, (unsigned long long)mine);  // job * tpj + tile
+    if (!want_vol) return;  // block-uniform
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)  // a fixed tree
+        len = df_add(len, DF{__shfl_down_sync(0xffffffffu, len.hi, w), __shfl_down_sync(0xffffffffu, len.lo, w)});
+    if ((threadIdx.x & 31) == 0)
+        warp_vol[(size_t)blockIdx.x * (kBoolThreads / 32) + (threadIdx.x >> 5)] = make_float2(len.hi, len.lo);
 }
 
 // Pass 2: exclusive prefix of the tile totals (one block of 1024 threads,
 // kPer consecutive totals per thread and round).
 __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total_all, int ntiles,
                                                         long long *tile_pre_all, long long N,
-                                                        const __grid_constant__ BoolJobs J) {
+                                                        const __grid_constant__ BoolJobs J, const float2 *warp_vol,
+                                                        double h2) {
     constexpr int kPer = 4;
     const int job = blockIdx.x;  // one block per job
     const unsigned long long *tile_total = tile_total_all + (size_t)job * ntiles;
@@ -691,34 +838,34 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
         carry += tot;
     }
     if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
-}
-
-// One output sample; inv: the normal inverted (FP32: negated; packed: every
-// code q -> 255 - q).
-__device__ __forceinline__ void put_sample(const Out &o, long long at, float d, float x, float y, float z, int t,
-                                           bool inv, ldni_info_t *info) {
-    if (at >= o.cap) {
-        set_status(info, LDNI_ST_CAPACITY);
-        return;
+    if (warp_vol) {  // the volume: the count pass's warp partials of this job in a fixed order
+        __shared__ DF shdf[1024 / 32];
+        constexpr int kWarps = kBoolThreads / 32;
+        const float2 *wv = warp_vol + (size_t)job * ntiles * kWarps;
+        const int n = ntiles * kWarps;
+        DF acc{0.0f, 0.0f};
+        for (int k0 = threadIdx.x; k0 < n; k0 += 1024 * 4) {
+            float2 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = k0 + u * 1024 < n ? __ldcg(wv + k0 + u * 1024) : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc = df_add(acc, DF{v[u].x, v[u].y});
+        }
+        const DF t = df_block_sum<1024>(acc, shdf);
+        if (threadIdx.x == 0) *J.vol[job] = ((double)t.hi + (double)t.lo) * h2;
     }
-    o.d[at] = d;
-    if (o.ny) {
-        const float f = inv ? -1.0f : 1.0f;
-        o.nx[at] = f * x;
-        o.ny[at] = f * y;
-        o.nz[at] = f * z;
-    } else {
-        o.nx[at] = __uint_as_float(__float_as_uint(x) ^ (inv ? kInvert8 : 0u));
-    }
-    o.tri[at] = t;
 }
 
 // Pass 3: offsets from the counts and the tile's prefix, then the samples of
-// every ray at its offset.
+// every ray at its offset.  A ray that keeps the pair of one operand (kinds 1
+// and 2, most rays of solids with few layers) is a plain copy: the thread
+// first loads the pairs of all its such rays into registers and only then
+// stores them, so their loads are in flight together instead of one ray's
+// loads waiting behind the previous ray's stores.  The other rays run the
+// general merge afterwards.
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const __grid_constant__ BoolJobs J, int op,
-                                                              float eps, const long long *tile_pre, int tpj,
-                                                              double *tile_vol) {
+__global__ void __launch_bounds__(kBoolThreads, 6) bool_write(long long N, const __grid_constant__ BoolJobs J, int op,
+                                                              float eps, const long long *tile_pre, int tpj) {
     constexpr int kRays = kR * kBoolThreads;
     __shared__ long long sh[kBoolThreads / 32 + 1];
     const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
@@ -729,17 +876,17 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
     const long long p0 = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p0);
     const int q0 = threadIdx.x * kR;
+    const long long tile_base = tile_pre[blockIdx.x];  // = job * tpj + tile
     int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
     load_rows<kR>(A.off, p0, q0, nr, ra);
     load_rows<kR>(B.off, p0, q0, nr, rb);
     load_rows<kR>(o.off, p0, q0, nr, cnt);  // pass 1's counts (cnt[kR] unused)
-#pragma unroll
-    for (int k = 0; k < kR; ++k)
-        if (q0 + k >= nr) cnt[k] = 0;
-    const long long tile_base = tile_pre[blockIdx.x];  // = job * tpj + tile
     int mine = 0;
 #pragma unroll
-    for (int k = 0; k < kR; ++k) mine += cnt[k];
+    for (int k = 0; k < kR; ++k) {
+        if (q0 + k >= nr) cnt[k] = 0;
+        mine += cnt[k];
+    }
     long long total;
     const long long base = tile_base + block_exclusive_scan<kBoolThreads>(mine, sh, &total);
     {
@@ -753,80 +900,85 @@ __global__ void __launch_bounds__(kBoolThreads, 5) bool_write(long long N, const
         store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, w);
     }
     const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;
-    const float sg = op == LDNI_OP_DIFF ? -1.0f : 1.0f;
-    const bool want_vol = J.vol[job] != nullptr;
-    DF vacc{0.0f, 0.0f};  // inside lengths of the written result (when its volume is asked for)
+    const bool three = o.ny != nullptr;
+    const bool inv = op == LDNI_OP_DIFF;
+    // the kept pairs of one operand: every load first, then every store
+    int kind[kR];
+    float d0[kR], d1[kR];
+    uint32_t x0[kR], x1[kR], y0[kR], y1[kR], z0[kR], z1[kR];
+    int t0[kR], t1[kR];
+#pragma unroll
+    for (int k = 0; k < kR; ++k) {
+        kind[k] = cnt[k] > 0 ? (clamp ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k])) : 0;
+        const bool pair = kind[k] == 1 || kind[k] == 2;
+        const Side &S = kind[k] == 2 ? B : A;
+        const long long i = kind[k] == 2 ? rb[k] : ra[k];
+        const uint32_t *X = reinterpret_cast<const uint32_t *>(S.nx);
+        const uint32_t *Y = reinterpret_cast<const uint32_t *>(S.ny);
+        const uint32_t *Z = reinterpret_cast<const uint32_t *>(S.nz);
+        d0[k] = pair ? S.d[i] : 0.0f;
+        d1[k] = pair ? S.d[i + 1] : 0.0f;
+        x0[k] = pair ? X[i] : 0u;
+        x1[k] = pair ? X[i + 1] : 0u;
+        y0[k] = pair && three ? Y[i] : 0u;
+        y1[k] = pair && three ? Y[i + 1] : 0u;
+        z0[k] = pair && three ? Z[i] : 0u;
+        z1[k] = pair && three ? Z[i + 1] : 0u;
+        t0[k] = pair ? S.tri[i] : 0;
+        t1[k] = pair ? S.tri[i + 1] : 0;
+    }
+    {
+        const uint32_t flip = !inv ? 0u : (three ? 0x80000000u : kInvert8);  // an inverted normal
+        long long at = base;
+#pragma unroll
+        for (int k = 0; k < kR; ++k) {
+            if (kind[k] == 1 || kind[k] == 2) {
+                const bool fb = kind[k] == 2;
+                const uint32_t f = fb ? flip : 0u;
+                const int tb = fb ? (int)0x80000000u : 0;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const long long a2 = at + h;
+                    if (a2 >= o.cap) {
+                        set_status(info, LDNI_ST_CAPACITY);
+                        continue;
+                    }
+                    o.d[a2] = h ? d1[k] : d0[k];
+                    o.nx[a2] = __uint_as_float((h ? x1[k] : x0[k]) ^ f);
+                    if (three) {
+                        o.ny[a2] = __uint_as_float((h ? y1[k] : y0[k]) ^ f);
+                        o.nz[a2] = __uint_as_float((h ? z1[k] : z0[k]) ^ f);
+                    }
+                    o.tri[a2] = (h ? t1[k] : t0[k]) | tb;
+                }
+            }
+            at += cnt[k];
+        }
+    }
     long long at = base;
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
-        if (cnt[k] > 0) {
-            const int kind = clamp ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k]);
-            if (kind == 4) {
-                const long long a0 = ra[k], b0 = rb[k];
-                int src[4];
-                const float dd[4] = {A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1]};
-                const int c = two_two(op, eps, dd[0], dd[1], dd[2], dd[3], src);
-                for (int m = 0; m < c; ++m) {
-                    const bool fb = src[m] >= 2;
-                    emit_global(fb, (fb ? b0 : a0) + (src[m] & 1), A, B, op, o, at + m, info);
-                }
-                if (want_vol)
-                    for (int m = 0; m < c; m += 2) vacc = df_add(vacc, df_diff(dd[src[m + 1]], dd[src[m]]));
-            } else if (kind == 3) {
-                const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
-                const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
-                const int nb = (int)(min((long long)rb[k + 1], B.cap) - b0);
-                const long long at0 = at;
-                merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
-                    emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
-                    emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
-                    if (want_vol)
-                        vacc = df_add(vacc, df_diff((cb ? B.d + b0 : A.d + a0)[ci], (pb ? B.d + b0 : A.d + a0)[pi]));
-                });
-            } else {  // a kept pair of one operand: copy both samples
-                const bool fa = kind == 1;
-                const int i = fa ? ra[k] : rb[k];
-                const float *sd = (fa ? A.d : B.d) + i, *sx = (fa ? A.nx : B.nx) + i;
-                const float *sy = fa ? A.ny : B.ny, *sz = fa ? A.nz : B.nz;
-                const int *st = (fa ? A.tri : B.tri) + i;
-                const float e0 = sd[0], e1 = sd[1];
-                const float x0 = sx[0], x1 = sx[1];
-                const float y0 = sy ? sy[i] : 0.0f, y1 = sy ? sy[i + 1] : 0.0f;
-                const float z0 = sz ? sz[i] : 0.0f, z1 = sz ? sz[i + 1] : 0.0f;
-                int t0 = st[0], t1 = st[1];
-                const bool inv = !fa && sg < 0.0f;
-                if (!fa) {
-                    t0 = (int)((unsigned)t0 | 0x80000000u);
-                    t1 = (int)((unsigned)t1 | 0x80000000u);
-                }
-                put_sample(o, at, e0, x0, y0, z0, t0, inv, info);
-                put_sample(o, at + 1, e1, x1, y1, z1, t1, inv, info);
-                if (want_vol) vacc = df_add(vacc, df_diff(e1, e0));
+        if (kind[k] == 4) {
+            const long long a0 = ra[k], b0 = rb[k];
+            int src[4];
+            const float dd[4] = {A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1]};
+            const int c = two_two(op, eps, dd[0], dd[1], dd[2], dd[3], src);
+            for (int m = 0; m < c; ++m) {
+                const bool fb = src[m] >= 2;
+                emit_global(fb, (fb ? b0 : a0) + (src[m] & 1), A, B, op, o, at + m, info);
             }
+        } else if (kind[k] == 3) {
+            const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
+            const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
+            const int nb = (int)(min((long long)rb[k + 1], B.cap) - b0);
+            const long long at0 = at;
+            merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
+                emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
+                emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
+            });
         }
         at += cnt[k];
     }
-    if (!want_vol) return;  // block-uniform
-    // volume of the result: one partial per warp, no block-wide wait
-    // (bool_vol_finish adds them in a fixed order)
-#pragma unroll
-    for (int o2 = 16; o2 > 0; o2 >>= 1) {
-        const DF y{__shfl_down_sync(0xffffffffu, vacc.hi, o2), __shfl_down_sync(0xffffffffu, vacc.lo, o2)};
-        vacc = df_add(vacc, y);
-    }
-    if ((threadIdx.x & 31) == 0)
-        tile_vol[(size_t)blockIdx.x * (kBoolThreads / 32) + (threadIdx.x >> 5)] = (double)vacc.hi + (double)vacc.lo;
-}
-
-// The volume of each result: its tiles' partials added in a fixed order (one
-// block per job).
-__global__ void __launch_bounds__(kBoolThreads) bool_vol_finish(const __grid_constant__ BoolJobs J,
-                                                                const double *tile_vol, int tpj, double h2) {
-    __shared__ double sh_sum[kBoolThreads];
-    const int job = blockIdx.x;
-    constexpr int kWarps = kBoolThreads / 32;
-    const double sum = fixed_order_sum<kBoolThreads>(tile_vol + (size_t)job * tpj * kWarps, tpj * kWarps, sh_sum);
-    if (threadIdx.x == 0) *J.vol[job] = sum * h2;
 }
 
 // ---- host side ------------------------------------------------------------------
@@ -874,8 +1026,24 @@ bool layers_ok(const ldni_layers_t *L, bool need) {
 }
 
 constexpr int kMinTileRays = 256;  // the workspace is sized for the smallest tile
+constexpr int kMaxDynSmem = 220 * 1024;  // dynamic shared memory of one Boolean block, at most
 
 size_t bool_ws_words(long long N) { return (size_t)((N + kMinTileRays - 1) / kMinTileRays); }
+
+// bulk copies need every staged array to start on a 16-byte boundary
+bool bulk_aligned(const BoolJobs &J, int njobs, bool rows) {
+    bool ok = true;
+    for (int j = 0; j < njobs; ++j) {
+        for (const Side *S : {&J.A[j], &J.B[j]}) {
+            for (const void *p : {(const void *)S->d, (const void *)S->nx, (const void *)S->ny, (const void *)S->nz,
+                                  (const void *)S->tri})
+                ok &= (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+            if (rows) ok &= (reinterpret_cast<uintptr_t>(S->off) & 15) == 0;
+        }
+        if (rows) ok &= (reinterpret_cast<uintptr_t>(J.o[j].off) & 15) == 0;
+    }
+    return ok;
+}
 
 template <int kR>
 int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, void *ws, int budget, bool split,
@@ -883,30 +1051,39 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
     constexpr int kRays = kR * kBoolThreads;
     const int tpj = (int)((N + kRays - 1) / kRays);
     const int nblocks = tpj * njobs;
+    // staged arrays per sample (depth, normals, id) plus the output sources, within the
+    // shared memory a block can have
+    const int narr = J.A[0].ny ? 5 : 3;
+    unsigned long long *words = static_cast<unsigned long long *>(ws);
     if (!split) {
-        unsigned long long *words = static_cast<unsigned long long *>(ws);
-        if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * ((size_t)nblocks + 1), s) != cudaSuccess)
-            return LDNI_ECUDA;
-        const size_t smem = 8 * (size_t)budget;  // staged depths + output sources
-        if (smem > 48 * 1024 &&
-            cudaFuncSetAttribute(bool_tiled<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-            return LDNI_ECUDA;
+        const int per = 4 * (narr + 1);
+        budget = min(budget, (kMaxDynSmem / per) & ~3);
+        const bool bulk = bulk_aligned(J, njobs, false);
+        // (the block that sums the volumes last reuses the stage for kBoolThreads doubles)
+        const size_t smem = max((size_t)per * (size_t)budget, J.vol[0] ? sizeof(double) * kBoolThreads : (size_t)0);
+        if (smem > 32 * 1024)  // beyond the default 48 KB with the static shared memory
+            if (int rc_ = cuda_check(
+                    cudaFuncSetAttribute(bool_tiled<kR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)))
+                return rc_;
+        // workspace: look-back words (one per tile) | ticket | finished tiles | tile volumes
+        double *tile_vol = J.vol[0] ? reinterpret_cast<double *>(words + nblocks + 2) : nullptr;
+        if (int rc_ = cuda_check(cudaMemsetAsync(words, 0, sizeof(unsigned long long) * ((size_t)nblocks + 2), s)))
+            return rc_;
         LDNI_LAUNCH(K_BOOL_FUSED, s,
-                    bool_tiled<kR><<<nblocks, kBoolThreads, smem, s>>>(N, J, op, eps, words, tpj, njobs, budget));
+                    bool_tiled<kR><<<nblocks, kBoolThreads, smem, s>>>(N, J, op, eps, words, tpj, njobs, budget, bulk,
+                                                                       tile_vol, h2));
         return cuda_status();
     }
     // workspace: tile totals (cleared) | tile prefixes | warp volumes (kBoolThreads / 32 per tile)
-    unsigned long long *tile_total = static_cast<unsigned long long *>(ws);
+    unsigned long long *tile_total = words;
     long long *tile_pre = reinterpret_cast<long long *>(tile_total + nblocks);
-    double *tile_vol = reinterpret_cast<double *>(tile_pre + nblocks);
-    if (cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s) != cudaSuccess)
-        return LDNI_ECUDA;
-    LDNI_LAUNCH(K_BOOL_COUNT, s, bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj));
-    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J));
-    LDNI_LAUNCH(K_BOOL_WRITE, s,
-                bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj, tile_vol));
-    if (J.vol[0]) LDNI_LAUNCH(K_VOL_PARTIAL, s, bool_vol_finish<<<njobs, kBoolThreads, 0, s>>>(J, tile_vol, tpj, h2));
+    float2 *warp_vol = J.vol[0] ? reinterpret_cast<float2 *>(tile_pre + nblocks) : nullptr;
+    if (int rc_ = cuda_check(cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s)))
+        return rc_;
+    LDNI_LAUNCH(K_BOOL_COUNT, s,
+                bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj, warp_vol));
+    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol, h2));
+    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
     return cuda_status();
 }
 
@@ -940,9 +1117,7 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int budget = tune.bool_stage_samples;
     const int rays = tune.bool_tile_rays;
-    // the volumes come from the three-launch form's write pass
-    const bool split = vols != nullptr ||
-                       (tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0);
+    const bool split = tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
     const double h = (double)grid->width / (double)grid->res;
     switch (rays) {
         case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, split, h * h, s);
@@ -1057,9 +1232,9 @@ int static_scratch(void **out) {
                 return LDNI_OK;
             }
     void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_bool_static_scratch) != cudaSuccess || !p) {
+    if (const cudaError_t e = cudaGetSymbolAddress(&p, g_bool_static_scratch); e != cudaSuccess || !p) {
         cudaGetLastError();
-        return LDNI_ECUDA;
+        return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol);
     }
     if (known || current_context_id(&id)) {  // the lookup may have made the context
         int slot = -1;

@@ -20,6 +20,20 @@ extern "C" const char *ldni_strerror(int code) {
     }
 }
 
+namespace ldni {
+namespace {
+thread_local cudaError_t g_last_cuda_error = cudaSuccess;
+}
+int cuda_fail(cudaError_t e) {
+    g_last_cuda_error = e;
+    return LDNI_ECUDA;
+}
+}  // namespace ldni
+
+extern "C" const char *ldni_last_cuda_error(void) {
+    return ldni::g_last_cuda_error == cudaSuccess ? "no CUDA error" : cudaGetErrorString(ldni::g_last_cuda_error);
+}
+
 extern "C" int ldni_version(void) { return 100; }
 
 extern "C" int ldni_grid_from_bbox(const float *bbox, int32_t res, ldni_grid_t *grid) {

@@ -525,8 +525,8 @@ extern "C" int ldni_contour_cells(const ldni_layers_t *L, const ldni_grid_t *gri
     const float h = grid->width / (float)res;
     const float *o = grid->origin;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(w.act, 0, w.act_bytes, s) != cudaSuccess) return LDNI_ECUDA;
-    if (cudaMemsetAsync(w.tinfo, 0, sizeof(ldni_info_t), s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.act, 0, w.act_bytes, s))) return rc_;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.tinfo, 0, sizeof(ldni_info_t), s))) return rc_;
     const long long N = (long long)res * res;
     LDNI_LAUNCH(K_CONTOUR, s,
                 mark_signs<<<(unsigned)((nw + kThreads - 1) / kThreads), kThreads, 0, s>>>(inside, res, W, w.act, Wc));

@@ -67,10 +67,18 @@ inline GridDev make_grid(const ldni_grid_t *g) {
     return d;
 }
 
+// Records e as the calling thread's last CUDA failure (ldni_last_cuda_error)
+// and returns LDNI_ECUDA.
+int cuda_fail(cudaError_t e);
+
+// LDNI_ECUDA when a launch or an earlier asynchronous call failed, else LDNI_OK.
 inline int cuda_status() {
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? LDNI_OK : LDNI_ECUDA;
+    return e == cudaSuccess ? LDNI_OK : cuda_fail(e);
 }
+
+// cudaSuccess -> LDNI_OK, anything else recorded -> LDNI_ECUDA
+inline int cuda_check(cudaError_t e) { return e == cudaSuccess ? LDNI_OK : cuda_fail(e); }
 
 inline int num_sms() {
     static int sms = 0;

@@ -808,8 +808,8 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     o.slab_cap = w.slab_cap;
     o.any_over = w.any_over;
 
-    if (cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
-    if (overflow_tiles && cudaMemsetAsync(overflow_tiles, 0, sizeof(int32_t), s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s))) return rc_;
+    if (overflow_tiles) if (int rc_ = cuda_check(cudaMemsetAsync(overflow_tiles, 0, sizeof(int32_t), s))) return rc_;
     if (mlp && nt > 0)
         LDNI_LAUNCH(K_FEATURES, s,
                     features_kernel<<<dim3(feature_blocks(nt, feature_stride), naxes), kThreads, 0, s>>>(
@@ -878,7 +878,7 @@ extern "C" int ldni_tile_features(const float *verts, int64_t nv, const int32_t 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     LImg o{};
     for (int k = 0; k < naxes; ++k) o.feat[ax_lo + k] = raw + (size_t)k * ntiles * kRawFeat;
-    if (cudaMemsetAsync(raw, 0, sizeof(float) * (size_t)naxes * ntiles * kRawFeat, s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(raw, 0, sizeof(float) * (size_t)naxes * ntiles * kRawFeat, s))) return rc_;
     if (nt > 0)
         LDNI_LAUNCH(K_FEATURES, s,
                     features_kernel<<<dim3(feature_blocks(nt, feature_stride), naxes), kThreads, 0, s>>>(

@@ -184,7 +184,7 @@ extern "C" int ldni_mlp_train_step(float *master_w, float *b, uint16_t *w_bf16, 
     const int outs[4] = {H, H, H, 1};
     const int woff[4] = {kW0, kW1, kW2, kW3};
     const int boff[4] = {kB0, kB1, kB2, kB3};
-    if (cudaMemsetAsync(loss, 0, sizeof(float), s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(loss, 0, sizeof(float), s))) return rc_;
     // forward
     const float *Ain = X;
     for (int l = 0; l < 4; ++l) {
@@ -213,9 +213,10 @@ extern "C" int ldni_mlp_train_step(float *master_w, float *b, uint16_t *w_bf16, 
             dZ = dA;
         }
     }
-    if (grad && cudaMemcpyAsync(grad, w.g, sizeof(float) * (kMlpWeights + kMlpBiases), cudaMemcpyDeviceToDevice, s) !=
-                    cudaSuccess)
-        return LDNI_ECUDA;
+    if (grad)
+        if (int rc_ = cuda_check(
+                cudaMemcpyAsync(grad, w.g, sizeof(float) * (kMlpWeights + kMlpBiases), cudaMemcpyDeviceToDevice, s)))
+            return rc_;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - powf(b1, (float)step), c2 = 1.0f - powf(b2, (float)step);
     LDNI_LAUNCH(K_MLP, s,

@@ -493,7 +493,7 @@ extern "C" int ldni_offset(const ldni_layers_t *H, const int64_t *n, const ldni_
     A.ntx = (res + kTile - 1) / kTile;
     const long long ntiles = (long long)A.ntx * A.ntx;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemsetAsync(w.tcnt[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.tcnt[0], 0, w.clear_bytes, s))) return rc_;
     const unsigned rblocks = (unsigned)((N + kThreads - 1) / kThreads);
     const unsigned sblocks = (unsigned)((S + kThreads - 1) / kThreads);
     LDNI_LAUNCH(K_OFFSET, s, off_centres<<<dim3(rblocks, 3), kThreads, 0, s>>>(A));
@@ -507,7 +507,7 @@ extern "C" int ldni_offset(const ldni_layers_t *H, const int64_t *n, const ldni_
         if (rc != LDNI_OK) return rc;
     }
     // the counts become the fill cursors
-    if (cudaMemsetAsync(w.tcnt[0], 0, w.clear_bytes, s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.tcnt[0], 0, w.clear_bytes, s))) return rc_;
     if (S > 0) LDNI_LAUNCH(K_OFFSET, s, off_bin<true><<<dim3(sblocks, 3), kThreads, 0, s>>>(A));
     const unsigned wblocks = (unsigned)((N + kOffWarps - 1) / kOffWarps);
     LDNI_LAUNCH(K_OFFSET, s, off_rays<false><<<dim3(wblocks, 3), kOffWarps * 32, 0, s>>>(A, info));

@@ -260,7 +260,7 @@ int grid_blocks(long long work) {
 }
 
 int run_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const Call &C, ldni_info_t *info) {
-    if (cudaMemsetAsync(C.w.count[0], 0, C.w.clear_bytes, C.s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(C.w.count[0], 0, C.w.clear_bytes, C.s))) return rc_;
     if (nt > 0) {
         LDNI_LAUNCH(K_COUNT_TRI, C.s,
                     tri_pass<false><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g,

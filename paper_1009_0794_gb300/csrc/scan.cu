@@ -292,8 +292,7 @@ int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long
         return cuda_status();
     }
     unsigned long long *words = reinterpret_cast<unsigned long long *>(partials);
-    if (cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(nchunk + 1) * naxes, s) != cudaSuccess)
-        return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(nchunk + 1) * naxes, s))) return rc_;
     LDNI_LAUNCH(K_SCAN_DOWN, s,
                 scan_lookback<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, words, info, info_base));
     return cuda_status();

@@ -145,7 +145,7 @@ extern "C" int ldni_volume_many(int32_t count, const ldni_layers_t *L, const ldn
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     double *partials = static_cast<double *>(ws);
     unsigned *done = reinterpret_cast<unsigned *>(partials + (size_t)nb * count);
-    if (cudaMemsetAsync(done, 0, sizeof(unsigned) * count, s) != cudaSuccess) return LDNI_ECUDA;
+    if (int rc_ = cuda_check(cudaMemsetAsync(done, 0, sizeof(unsigned) * count, s))) return rc_;
     const double h = (double)grid->width / (double)grid->res;
     LDNI_LAUNCH(K_VOL_PARTIAL, s, volume_kernel<<<dim3(nb, count), kThreads, 0, s>>>(N, J, partials, done, h * h));
     return cuda_status();
