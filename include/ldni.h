@@ -235,6 +235,23 @@ int ldni_get_tuning(ldni_tuning_t *tuning_host);
  * NULL restores the defaults. */
 int ldni_set_tuning(const ldni_tuning_t *tuning_host);
 
+/* ---- bounded device waits (no counterpart in the paper) ------------------ */
+
+/* Polls a bounded device wait (the decoupled look-back of the one-launch
+ * scans, Booleans and batches) makes before it gives up; it then records
+ * LDNI_ST_TIMEOUT in the call's info block and the kernel ends, so no kernel
+ * of the library waits forever.  Process-wide host state read when a call
+ * launches (a captured CUDA graph keeps the value it was captured with).
+ * polls 0 restores the default (2^22); negative is LDNI_EINVAL. */
+int ldni_set_wait_limit(int32_t polls);
+int32_t ldni_get_wait_limit(void);
+
+/* Self-test of the timeout path: one warp runs the bounded wait, with the
+ * current limit, on a word that nothing sets; info->status (device) gains
+ * LDNI_ST_TIMEOUT once the stream reaches that point.  Nothing else is
+ * touched, and the device stays usable. */
+int ldni_wait_selftest(ldni_info_t *info, void *stream);
+
 /* ---- batches ------------------------------------------------------------ */
 
 /* Workspace bytes for ldni_sample_batch over items_host[count]. */
@@ -383,6 +400,38 @@ int ldni_boolean_many(int32_t count, const ldni_layers_t *A, const ldni_layers_t
 int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
                         const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out, ldni_info_t *info,
                         void *stream);
+
+/* ---- chains of unions (Sections 4.1.1 and 4.2) -------------------------- */
+
+/* Workspace bytes for ldni_union_chain of nimg (1 .. 3) images at res. */
+int ldni_union_chain_workspace_size(int32_t res, int32_t nimg, size_t *bytes_host);
+
+/*
+ * out[j] = P[j][0] u P[j][1] u ... u P[j][count-1] for each image j, all on
+ * one grid: the repeated union of offsetting and sweeps (Section 4.2) and of
+ * any chain of Booleans on one grid (Section 4.1.1).  The result is the one
+ * the step-by-step chain of ldni_boolean calls gives,
+ *   acc = P[j][0];  acc = ldni_boolean(acc, P[j][k], LDNI_OP_UNION, eps)  (k = 1 ..),
+ * bit for bit: small-interval removal after every step, the accumulated
+ * sample kept where both flip at one depth, and tri_id bit 31 on every
+ * sample that entered through a part k >= 1.  Each ray carries its own
+ * accumulated samples from step to step (two passes over the rays and the
+ * CSR scan; no intermediate image is written).
+ *   parts_dev  : DEVICE array of nimg * count layers, image-major (part k of
+ *                image j at j * count + k), read by the kernels;
+ *   parts_host : the same array on the host (validation);
+ *   out        : host array of nimg layers with device buffers; the inputs
+ *                and the output share one normal format;
+ *   info       : device; n[j] = samples image j of the result needs (beyond
+ *                out[j].capacity they are dropped, LDNI_ST_CAPACITY).
+ * A ray whose accumulated result would need more than 64 samples at some
+ * step is left empty and reported (LDNI_ST_EVENTS); odd input rays set
+ * LDNI_ST_ODD.  No host synchronisation (capturable in a CUDA graph while the
+ * parts array and workspace outlive the graph).
+ */
+int ldni_union_chain(const ldni_layers_t *parts_dev, const ldni_layers_t *parts_host, int32_t count, int32_t nimg,
+                     const ldni_grid_t *grid, float eps, ldni_layers_t *out, ldni_info_t *info, void *ws,
+                     size_t ws_bytes, void *stream);
 
 /* ---- volume ----------------------------------------------------------- */
 
@@ -574,7 +623,7 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour, 29 chain). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -117,6 +117,11 @@ SIGNATURES = {
     "ldni_offset": (ctypes.c_int, [_P, _P, _P, ctypes.c_float, _I32, ctypes.c_float, _P, _P, _P, _SZ, _P]),
     "ldni_classify_nodes_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_classify_nodes": (ctypes.c_int, [_P, _P, _P, _P, _P, _SZ, _P]),
+    "ldni_union_chain_workspace_size": (ctypes.c_int, [_I32, _I32, ctypes.POINTER(_SZ)]),
+    "ldni_union_chain": (ctypes.c_int, [_P, _P, _I32, _I32, _PG, ctypes.c_float, _P, _P, _P, _SZ, _P]),
+    "ldni_set_wait_limit": (ctypes.c_int, [_I32]),
+    "ldni_get_wait_limit": (ctypes.c_int32, []),
+    "ldni_wait_selftest": (ctypes.c_int, [_P, _P]),
     "ldni_get_tuning": (ctypes.c_int, [_P]),
     "ldni_set_tuning": (ctypes.c_int, [_P]),
     "ldni_sample_batch_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_SZ)]),

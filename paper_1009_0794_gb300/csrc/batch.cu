@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(kThreads) batch_big(const ldni_batch_item_t *i
 // look-back of a chunk stops at the first chunk of its own image.
 __global__ void __launch_bounds__(kThreads) batch_scan(const ldni_batch_item_t *items, int count, Tables T,
                                                        const int *counts, unsigned long long *words,
-                                                       ldni_info_t *infos) {
+                                                       ldni_info_t *infos, int spin_limit) {
     __shared__ long long sh[kThreads / 32 + 1];
     __shared__ long long s_chunk, s_base;
     const long long nchunks = T.chunk_prefix[3 * count];
@@ -213,7 +213,7 @@ __global__ void __launch_bounds__(kThreads) batch_scan(const ldni_batch_item_t *
     const long long excl = block_exclusive_scan<kThreads>(mine, sh, &total);
     if (threadIdx.x < 32) {
         // image-local status words: chunk 0 of the image starts at prefix 0
-        const long long b = lookback_warp(words + T.chunk_prefix[img], (int)local, total, infos + m);
+        const long long b = lookback_warp(words + T.chunk_prefix[img], (int)local, total, infos + m, spin_limit);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
@@ -364,7 +364,8 @@ extern "C" int ldni_sample_batch(const ldni_batch_item_t *items_dev, const ldni_
                     batch_big<false><<<5 * num_sms(), kThreads, 0, s>>>(items_dev, w.T, w.counts, num_sms(), infos));
     }
     LDNI_LAUNCH(K_BATCH, s,
-                batch_scan<<<(unsigned)chunks, kThreads, 0, s>>>(items_dev, count, w.T, w.counts, w.words, infos));
+                batch_scan<<<(unsigned)chunks, kThreads, 0, s>>>(items_dev, count, w.T, w.counts, w.words, infos,
+                                                                  wait_limit()));
     if (tris > 0) {
         LDNI_LAUNCH(K_BATCH, s, batch_tri_pass<true><<<blocks_for(tris), kThreads, 0, s>>>(items_dev, count, w.T,
                                                                                             w.counts, infos));

@@ -30,6 +30,7 @@
 #include "dfloat.cuh"
 #include "ldni_host.h"
 #include "lookback.cuh"
+#include "merge.cuh"
 
 namespace ldni {
 namespace {
@@ -68,75 +69,8 @@ struct BoolJobs {
     Side B[kMaxJobs];
     Out o[kMaxJobs];
     ldni_info_t *info[kMaxJobs];
-    double *vol[kMaxJobs];  // optional: volume of each result (three-launch form only)
-};
-
-// Truth table of an operation: bit (2 inA + inB) = op(inA, inB).
-__device__ __forceinline__ unsigned op_table(int op) {
-    return op == LDNI_OP_UNION ? 0xEu : (op == LDNI_OP_INTER ? 0x8u : 0x4u);
-}
-
-// The merge of one ray over index ranges [a, ae) of dA and [b, be) of dB.
-// Every sample is read once.  emit(pend_from_b, pend_idx, cur_from_b,
-// cur_idx, m) is called for every kept interval (entering sample, leaving
-// sample) with m = samples so far.  A depth that equals nothing, itself
-// included (NaN, outside the method's inputs), is consumed on its own so the
-// walk always ends.
-template <class Idx, class PA, class PB, class EmitF>
-__device__ __forceinline__ int merge_core(PA dA, Idx a, Idx ae, PB dB, Idx b, Idx be, int op, float eps,
-                                          EmitF emit) {
-    const unsigned table = op_table(op);
-    unsigned state = 0;  // bit 1: inside A, bit 0: inside B
-    bool out = false;
-    bool pend_b = false;
-    Idx pend_i = 0;
-    float pend_d = 0.0f;
-    int m = 0;
-    float da = a < ae ? dA[a] : 0.0f;
-    float db = b < be ? dB[b] : 0.0f;
-    while (a < ae || b < be) {
-        const bool takeA = a < ae && (b >= be || !(db < da));
-        const float d = takeA ? da : db;
-        const Idx fa = a, fb = b;
-        while (a < ae && da == d) {
-            ++a;
-            da = a < ae ? dA[a] : 0.0f;
-        }
-        while (b < be && db == d) {
-            ++b;
-            db = b < be ? dB[b] : 0.0f;
-        }
-        if (a == fa && b == fb) {  // NaN guard
-            if (takeA) {
-                ++a;
-                da = a < ae ? dA[a] : 0.0f;
-            } else {
-                ++b;
-                db = b < be ? dB[b] : 0.0f;
-            }
-        }
-        const bool flipA = ((a - fa) & 1) != 0;
-        state ^= (flipA ? 2u : 0u) | (((b - fb) & 1) ? 1u : 0u);
-        const bool now = (table >> state) & 1u;
-        if (now == out) continue;
-        out = now;
-        const bool cur_b = !flipA;
-        const Idx cur_i = flipA ? fa : fb;
-        if (now) {
-            pend_b = cur_b;
-            pend_i = cur_i;
-            pend_d = d;
-        } else if (!(__fsub_rn(d, pend_d) < eps)) {
-            emit(pend_b, pend_i, cur_b, cur_i, m);
-            m += 2;
-        }
-    }
-    return m;
-}
-
-struct NoEmit {
-    template <class Idx>
-    __device__ __forceinline__ void operator()(bool, Idx, bool, Idx, int) const {}
+    double *vol[kMaxJobs];  // optional: volume of each result
+    bool packed;            // 8-bit normals (one word) instead of FP32 nx, ny, nz, for every image of the call
 };
 
 // One output sample at slot `at` from sample idx of A or B.
@@ -417,7 +351,7 @@ __device__ __forceinline__ const uint32_t *side_array(const Side &S, int k, int 
 // wait gave up (LDNI_ST_TIMEOUT recorded).
 template <int kR>
 __device__ __forceinline__ bool tile_prologue(const Side &A, const Side &B, long long p_begin, int nr, int budget,
-                                              bool bulk, uint32_t *stage, uint64_t *bars, long long *sh4,
+                                              int narr, bool bulk, uint32_t *stage, uint64_t *bars, long long *sh4,
                                               TileIn<kR> &T, ldni_info_t *info) {
     const int q0 = threadIdx.x * kR;
     int ra[kR + 1], rb[kR + 1];
@@ -455,7 +389,6 @@ __device__ __forceinline__ bool tile_prologue(const Side &A, const Side &B, long
         if (k < kR && q0 + k < nr && (((ra[k + 1] - ra[k]) | (rb[k + 1] - rb[k])) & 1)) T.odd |= 1u << k;
     }
     if (threadIdx.x == 0 && (endA > A.cap || endB > B.cap)) set_status(info, LDNI_ST_CAPACITY);
-    const int narr = A.ny ? 5 : 3;
     T.sa.narr = T.sb.narr = narr;
     T.sa.off = (int)(T.ga0 & 3);
     T.sb.off = (int)(T.gb0 & 3);
@@ -652,10 +585,11 @@ __device__ __forceinline__ bool tile_emit(const TileIn<kR> &T, const Side &A, co
 template <int kR>
 __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __grid_constant__ BoolJobs J, int op,
                                                            float eps, unsigned long long *words, int tpj, int njobs,
-                                                           int budget, bool bulk, double *tile_vol, double h2) {
+                                                           int budget, bool bulk, double *tile_vol, double h2,
+                                                           int spin_limit) {
     constexpr int kRays = kR * kBoolThreads;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int narr = J.A[0].ny ? 5 : 3;
+    const int narr = J.packed ? 3 : 5;
     uint32_t *stage = reinterpret_cast<uint32_t *>(smem_raw);      // [narr][budget] words
     int *pick = reinterpret_cast<int *>(stage + narr * budget);    // [budget] source of every output sample
     __shared__ __align__(8) uint64_t bars[2];
@@ -676,7 +610,7 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
     const long long p_begin = (long long)tile * kRays;
     const int nr = (int)min((long long)kRays, N - p_begin);
     TileIn<kR> T;
-    const bool ok = tile_prologue<kR>(A, B, p_begin, nr, budget, bulk, stage, bars, sh4, T, info);
+    const bool ok = tile_prologue<kR>(A, B, p_begin, nr, budget, narr, bulk, stage, bars, sh4, T, info);
     int cnt[kR];
     const int mine = ok ? tile_counts<kR>(T, A, B, op, eps, nr, cnt, info) : 0;
     if (!ok)
@@ -685,7 +619,7 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
     long long total;
     const int excl = (int)block_exclusive_scan<kBoolThreads>(mine, sh, &total);
     if (threadIdx.x < 32) {
-        const long long b = lookback_warp(words + (size_t)job * tpj, tile, total, info);
+        const long long b = lookback_warp(words + (size_t)job * tpj, tile, total, info, spin_limit);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
@@ -1015,10 +949,6 @@ Out out_of(const ldni_layers_t &L) {
     return Out{L.offsets, L.depth, x, y, z, L.tri_id, L.capacity};
 }
 
-bool same_format(const ldni_layers_t &A, const ldni_layers_t &B, const ldni_layers_t &o) {
-    return (A.nrm8 != nullptr) == (o.nrm8 != nullptr) && (B.nrm8 != nullptr) == (o.nrm8 != nullptr);
-}
-
 bool layers_ok(const ldni_layers_t *L, bool need) {
     if (!L || !L->offsets || L->capacity < 0) return false;
     if (need && !samples_ok(*L)) return false;
@@ -1053,7 +983,7 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
     const int nblocks = tpj * njobs;
     // staged arrays per sample (depth, normals, id) plus the output sources, within the
     // shared memory a block can have
-    const int narr = J.A[0].ny ? 5 : 3;
+    const int narr = J.packed ? 3 : 5;
     unsigned long long *words = static_cast<unsigned long long *>(ws);
     if (!split) {
         const int per = 4 * (narr + 1);
@@ -1071,7 +1001,7 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
             return rc_;
         LDNI_LAUNCH(K_BOOL_FUSED, s,
                     bool_tiled<kR><<<nblocks, kBoolThreads, smem, s>>>(N, J, op, eps, words, tpj, njobs, budget, bulk,
-                                                                       tile_vol, h2));
+                                                                       tile_vol, h2, wait_limit()));
         return cuda_status();
     }
     // workspace: tile totals (cleared) | tile prefixes | warp volumes (kBoolThreads / 32 per tile)
@@ -1099,10 +1029,17 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
         op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
         return LDNI_EINVAL;
     BoolJobs J{};
+    {
+        const ldni_layers_t *all[3 * kMaxJobs];
+        for (int j = 0; j < count; ++j) {
+            all[3 * j] = A + j;
+            all[3 * j + 1] = B + j;
+            all[3 * j + 2] = out + j;
+        }
+        if (!same_format(all, 3 * count, &J.packed)) return LDNI_EINVAL;
+    }
     for (int j = 0; j < count; ++j) {
-        if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true) ||
-            !same_format(A[j], B[j], out[j]))
-            return LDNI_EINVAL;
+        if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true)) return LDNI_EINVAL;
         J.A[j] = side_of(A[j]);
         J.B[j] = side_of(B[j]);
         J.o[j] = out_of(out[j]);
@@ -1253,7 +1190,9 @@ int static_scratch(void **out) {
 extern "C" int ldni_boolean_static(const ldni_layers_t *A, const ldni_grid_t *grid_a, const ldni_layers_t *B,
                                    const ldni_grid_t *grid_b, int32_t op, float eps, ldni_layers_t *out,
                                    ldni_info_t *info, void *stream) {
-    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !same_format(*A, *B, *out) ||
+    const ldni_layers_t *all[3] = {A, B, out};
+    bool packed = false;
+    if (!layers_ok(A, true) || !layers_ok(B, true) || !layers_ok(out, true) || !same_format(all, 3, &packed) ||
         !info || !grid_valid(grid_a) ||
         !grid_valid(grid_b) || op < LDNI_OP_UNION || op > LDNI_OP_DIFF || !(eps >= 0.0f))
         return LDNI_EINVAL;

@@ -1,8 +1,10 @@
 // Small C-ABI helpers: error strings, version, grid from a bounding box.
+#include <atomic>
 #include <cmath>
 #include <mutex>
 
 #include "ldni_host.h"
+#include "lookback.cuh"
 
 extern "C" const char *ldni_strerror(int code) {
     switch (code) {
@@ -88,8 +90,52 @@ extern "C" const char *ldni_kernel_name(int32_t id) {
                                              "sort_rays",  "bool_count", "bool_write", "volume",
                                              "unused",     "boolean",    "features",  "capacity",
                                              "layout",     "onepass",    "onepass_big", "redo",
-                                             "gather",     "mlp",        "adjoint",   "batch",      "nodes",     "order",     "offset",    "normals8",  "contour"};
+                                             "gather",     "mlp",        "adjoint",   "batch",      "nodes",     "order",     "offset",    "normals8",  "contour",   "chain"};
     return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
+}
+
+// ---- bounded device waits ------------------------------------------------------
+namespace ldni {
+namespace {
+std::atomic<int> g_wait_limit{kDefaultWaitPolls};
+
+// One warp polls, with the library's bounded wait, a shared word that nothing
+// sets; after `polls` polls it gives up and records LDNI_ST_TIMEOUT.
+__global__ void wait_selftest_kernel(ldni_info_t *info, int polls) {
+    __shared__ unsigned long long never_set;
+    if (threadIdx.x == 0) never_set = 0;
+    __syncwarp();
+    int spins = 0;
+    bool timed_out = false;
+    while (true) {
+        const bool missing = (*reinterpret_cast<volatile unsigned long long *>(&never_set) & ~kValueMask) == 0;
+        if (!__any_sync(0xffffffffu, missing)) break;
+        if (++spins > polls) {
+            timed_out = true;
+            break;
+        }
+        __nanosleep(32);
+    }
+    if (timed_out && threadIdx.x == 0) atomicOr(&info->status, LDNI_ST_TIMEOUT);
+}
+}  // namespace
+
+int wait_limit() { return g_wait_limit.load(); }
+}  // namespace ldni
+
+extern "C" int ldni_set_wait_limit(int32_t polls) {
+    if (polls < 0) return LDNI_EINVAL;
+    ldni::g_wait_limit.store(polls == 0 ? ldni::kDefaultWaitPolls : polls);
+    return LDNI_OK;
+}
+
+extern "C" int32_t ldni_get_wait_limit(void) { return ldni::g_wait_limit.load(); }
+
+extern "C" int ldni_wait_selftest(ldni_info_t *info, void *stream) {
+    if (!info) return LDNI_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    LDNI_LAUNCH(ldni::K_NONE, s, ldni::wait_selftest_kernel<<<1, 32, 0, s>>>(info, ldni::wait_limit()));
+    return ldni::cuda_status();
 }
 
 // ---- launch tuning -----------------------------------------------------------

@@ -35,6 +35,11 @@ struct Carver {
 // Launch knobs (ldni_set_tuning), copied at launch time.
 ldni_tuning_t current_tuning();
 
+// Polls a bounded device wait makes before it gives up (ldni_set_wait_limit),
+// passed to the kernels at launch time.
+constexpr int kDefaultWaitPolls = 1 << 22;
+int wait_limit();
+
 inline bool grid_valid(const ldni_grid_t *g) {
     return g && g->res >= 1 && g->res <= 8192 && g->width > 0.0f && g->width < 3.0e38f;
 }
@@ -42,6 +47,27 @@ inline bool grid_valid(const ldni_grid_t *g) {
 // The sample arrays of a layer are present (capacity 0 needs none).
 inline bool samples_ok(const ldni_layers_t &L) {
     return L.capacity == 0 || (L.depth && L.tri_id && (L.nrm8 || (L.nx && L.ny && L.nz)));
+}
+
+// Normal format of a layer: 1 packed 8-bit words, 0 FP32, -1 either (an
+// empty layer may come without any sample array).
+inline int layer_format(const ldni_layers_t &L) {
+    if (L.nrm8) return 1;
+    if (L.nx || L.capacity > 0) return 0;
+    return -1;
+}
+
+// The operands and outputs of one call share a format: *packed receives it.
+inline bool same_format(const ldni_layers_t *const *Ls, int n, bool *packed) {
+    int f = -1;
+    for (int k = 0; k < n; ++k) {
+        const int g = layer_format(*Ls[k]);
+        if (g < 0) continue;
+        if (f >= 0 && g != f) return false;
+        f = g;
+    }
+    *packed = f == 1;
+    return true;
 }
 
 // Normal arrays as the kernels take them: FP32 in x, y, z, or the packed

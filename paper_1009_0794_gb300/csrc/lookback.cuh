@@ -6,6 +6,7 @@
 // bounded: after kSpinLimit polls the block records LDNI_ST_TIMEOUT in the
 // call's info block and treats the missing word as zero, so the kernel always
 // terminates (the result is then flagged as invalid, never silently wrong).
+// The same bounded poll serves the self-test of ldni_wait_selftest.
 #pragma once
 
 #include <cstdint>
@@ -17,7 +18,8 @@ namespace ldni {
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagPrefix = 2ull << 62;
 constexpr unsigned long long kValueMask = (1ull << 62) - 1;
-constexpr int kSpinLimit = 1 << 22;
+// Polls of a look-back wait before it gives up: a kernel argument, from the
+// process-wide setting of ldni_set_wait_limit (default kDefaultWaitPolls).
 
 __device__ __forceinline__ unsigned long long ld_status(const unsigned long long *p) {
     return *reinterpret_cast<const volatile unsigned long long *>(p);
@@ -40,7 +42,7 @@ constexpr int kLookbackPerLane = 8;
 constexpr int kLookbackWindow = 32 * kLookbackPerLane;
 
 __device__ __forceinline__ long long lookback_warp(unsigned long long *status, int c, long long aggregate,
-                                                   ldni_info_t *info) {
+                                                   ldni_info_t *info, int spin_limit) {
     const int lane = threadIdx.x & 31;
     const unsigned long long agg = (unsigned long long)aggregate & kValueMask;
     if (c == 0) {
@@ -65,7 +67,7 @@ __device__ __forceinline__ long long lookback_warp(unsigned long long *status, i
 #pragma unroll
             for (int j = 0; j < kLookbackPerLane; ++j) missing |= (w[j] & ~kValueMask) == 0;
             if (!__any_sync(0xffffffffu, missing)) break;
-            if (++spins > kSpinLimit) {
+            if (++spins > spin_limit) {
                 timed_out = true;
                 break;
             }

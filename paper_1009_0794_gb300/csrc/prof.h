@@ -42,7 +42,8 @@ enum KernelId : int {
     K_OFFSET = 26,
     K_CODEC = 27,
     K_CONTOUR = 28,
-    K_NUM = 29
+    K_CHAIN = 29,
+    K_NUM = 30
 };
 
 struct ProfState {

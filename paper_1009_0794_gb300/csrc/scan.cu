@@ -86,7 +86,7 @@ __device__ __forceinline__ void verify_chunk(const AxisPtrs &ap, int a, int c, l
 
 __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long N, int nchunk,
                                                           unsigned long long *words, ldni_info_t *info,
-                                                          int info_base) {
+                                                          int info_base, int spin_limit) {
     __shared__ long long sh[kThreads / 32 + 1];
     __shared__ int s_chunk;
     __shared__ long long s_base;
@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
         carry += tot;
     }
     if (threadIdx.x < 32) {
-        const long long b = lookback_warp(status, c, carry, info);
+        const long long b = lookback_warp(status, c, carry, info, spin_limit);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
@@ -294,7 +294,8 @@ int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long
     unsigned long long *words = reinterpret_cast<unsigned long long *>(partials);
     if (int rc_ = cuda_check(cudaMemsetAsync(words, 0, sizeof(unsigned long long) * (size_t)(nchunk + 1) * naxes, s))) return rc_;
     LDNI_LAUNCH(K_SCAN_DOWN, s,
-                scan_lookback<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, words, info, info_base));
+                scan_lookback<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, words, info, info_base,
+                                                                        wait_limit()));
     return cuda_status();
 }
 

@@ -736,31 +736,62 @@ class BatchPlan:
         return self.outs
 
 
-def union_chain(parts: Sequence[LDNI], eps: float = 0.0, capacity: Optional[int] = None):
-    """acc = parts[0] u parts[1] u ... in order (Section 4.1 unions, the
-    repeated operation of Minkowski sums and sweeps, Section 4.2), all on one
-    grid.  Returns (run, result): run() enqueues the whole chain without host
-    synchronisation (capturable in a CUDA graph); result is the final LDNI
-    once run() has completed (its .n is set by finish())."""
-    grid, axis = parts[0].grid, parts[0].axis
-    cap = capacity if capacity is not None else int(sum(p.capacity for p in parts))
-    bufs = [empty_layers(grid, axis, cap, parts[0].packed), empty_layers(grid, axis, cap, parts[0].packed)]
-    ws = torch.empty(boolean_workspace_size(grid.res), dtype=torch.uint8, device="cuda")
+def union_chain_workspace_size(res: int, nimg: int) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_union_chain_workspace_size(int(res), int(nimg), ctypes.byref(sz)),
+               "ldni_union_chain_workspace_size")
+    return int(sz.value)
+
+
+def union_chain_many(parts_per_image: Sequence[Sequence[LDNI]], eps: float = 0.0,
+                     capacities: Optional[Sequence[int]] = None):
+    """For each image j (1 to 3, one grid): parts[j][0] u parts[j][1] u ...
+    in order (Section 4.1 unions, the repeated operation of offsetting and
+    sweeps, Section 4.2), equal to the step-by-step chain of boolean() calls
+    bit for bit, in one call (ldni_union_chain).  Returns (run, finish):
+    run() enqueues the chain without host synchronisation (capturable in a
+    CUDA graph); finish() checks the status and returns the result images
+    once run() has completed."""
+    lib = _lib.load()
+    nimg = len(parts_per_image)
+    count = len(parts_per_image[0])
+    if nimg < 1 or nimg > 3 or count < 1 or any(len(ps) != count for ps in parts_per_image):
+        raise _lib.LDNIError(-1, "union_chain")
+    grid = parts_per_image[0][0].grid
+    packed = parts_per_image[0][0].packed
+    if any(p.grid != grid for ps in parts_per_image for p in ps):
+        raise _lib.LDNIError(-2, "union_chain")
+    caps = list(capacities) if capacities else [sum(p.capacity for p in ps) for ps in parts_per_image]
+    outs = [empty_layers(grid, ps[0].axis, max(1, int(c)), packed) for ps, c in zip(parts_per_image, caps)]
+    host = (_CLayers * (nimg * count))(*[p.c() for ps in parts_per_image for p in ps])
+    dev = torch.frombuffer(bytearray(bytes(memoryview(host))), dtype=torch.uint8).cuda()
+    oarr = (_CLayers * nimg)(*[o.c() for o in outs])
+    ws = torch.empty(union_chain_workspace_size(grid.res, nimg), dtype=torch.uint8, device="cuda")
     info = new_info()
+    g = grid.c()
 
     def run(stream=None):
-        cur = parts[0]
-        for k in range(1, len(parts)):
-            out = bufs[k % 2]
-            boolean(cur, parts[k], "union", eps=eps, stream=stream, out=out, ws=ws, info=info, sync=False)
-            cur = out
+        _lib.check(lib.ldni_union_chain(dev.data_ptr(), host, count, nimg, ctypes.byref(g), float(eps), oarr,
+                                        info.data_ptr(), ws.data_ptr(), ws.numel(), _stream_ptr(stream)),
+                   "ldni_union_chain")
 
-    final = bufs[(len(parts) - 1) % 2] if len(parts) > 1 else parts[0]
-
-    def finish():
+    def finish() -> List[LDNI]:
         meta = info_decode(info)
-        _raise_status(meta["status"], "union_chain")
-        final.n = meta["n"][0] if len(parts) > 1 else parts[0].n
-        return final
+        _raise_status(meta["status"], "ldni_union_chain")
+        if meta["status"] & _lib.ST_EVENTS:
+            raise _lib.LDNIError(-4, "ldni_union_chain (a ray needs more than 64 samples)")
+        if meta["status"] & _lib.ST_ODD:
+            raise _lib.LDNIError(-3, "ldni_union_chain")
+        for j, o in enumerate(outs):
+            o.n = meta["n"][j]
+        return outs
 
+    run._keep = (host, dev, oarr, ws, info, g)  # alive as long as run is
     return run, finish
+
+
+def union_chain(parts: Sequence[LDNI], eps: float = 0.0, capacity: Optional[int] = None):
+    """acc = parts[0] u parts[1] u ... in order for one image (see
+    union_chain_many).  Returns (run, finish); finish() gives the result."""
+    run, fin = union_chain_many([parts], eps, [capacity] if capacity is not None else None)
+    return run, (lambda: fin()[0])

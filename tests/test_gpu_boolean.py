@@ -75,6 +75,16 @@ def test_empty_operands(ldni):
     assert ldni.boolean(LA, E, "inter").n == 0
     assert bit_equal(ldni.boolean(LA, E, "diff").numpy(), LA.numpy())
     assert ldni.boolean(E, E, "union").n == 0
+    # an empty first operand (no sample arrays at all): the result's normals still come from B
+    from paper_1009_0794_gb300 import tune
+    for op in ("union", "inter", "diff"):
+        for split in (0, 1):
+            prev = tune.set(bool_split=split)
+            try:
+                got = ldni.boolean(E, LA, op).numpy()
+            finally:
+                tune.set(**prev)
+            assert bit_equal(got, oracle.boolean(E.numpy(), LA.numpy(), op)), (op, split)
 
 
 def test_grid_mismatch_rejected(ldni):
