@@ -69,6 +69,7 @@ extern "C" {
 
 #define LDNI_MODE_EXACT2 0        /* exact two-pass: count, scan, fill, sort */
 #define LDNI_MODE_LEARNED1 1      /* one pass into learned per-tile capacity, exact redo of overflow */
+#define LDNI_MODE_BINNED2 2       /* exact two-pass with triangles binned to 16 x 16 pixel tiles */
 
 #define LDNI_OP_UNION 0
 #define LDNI_OP_INTER 1
@@ -182,9 +183,11 @@ int ldni_sample_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis
  *   tris   : device int32[nt][3], vertex indices, outward winding.
  *   grid   : host pointer to the cube.
  *   axis   : 0, 1, 2, or LDNI_AXIS_ALL (out then points to 3 layers x, y, z).
- *   mode   : LDNI_MODE_EXACT2 (this entry point) - count pass, scan, fill
- *            pass, per-ray sort; the paper's stencil-counted multi-pass
- *            rendering (Section 3, Appendix A) restated for CUDA.
+ *   mode   : LDNI_MODE_EXACT2 - count pass, scan, fill pass, per-ray sort;
+ *            the paper's stencil-counted multi-pass rendering (Section 3,
+ *            Appendix A) restated for CUDA; or LDNI_MODE_BINNED2 - the same
+ *            passes tile by tile (ldni_sample_binned_count, needs the binned
+ *            workspace), identical output.
  *   out    : host pointer to 1 or 3 ldni_layers_t with caller buffers.
  *   info   : device ldni_info_t; n[a] receives the sample count of image a.
  *   ws     : device workspace of at least ldni_sample_workspace_size bytes.
@@ -212,6 +215,32 @@ int ldni_sample_count(const float *verts, int64_t nv, const int32_t *tris, int64
 int ldni_sample_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
                      int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
                      void *stream);
+
+/* ---- exact two-pass sampling with tile binning ------------------------- */
+
+/* Bytes of device workspace of ldni_sample with LDNI_MODE_BINNED2 and of its
+ * two halves below; LDNI_ETOOLARGE beyond 2^31 / 16 triangles. */
+int ldni_sample_binned_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis, size_t *bytes_host);
+
+/*
+ * ldni_sample's result (identical bits) with a different traversal, for
+ * meshes whose triangles cover many pixels or whose rays hold many layers:
+ * a counting sort bins every (triangle, image) pair to the 16 x 16 pixel
+ * tiles its pixel box touches, and one block per tile stages the exact
+ * setup of its triangles (snapped, oriented edge functions; Remark 1's
+ * top-left rule) in shared memory while every thread - one pixel centre -
+ * tests them all.  A pixel counts its crossings in a register and writes them
+ * to its own slots, with no atomic per crossing.  Pairs whose box touches
+ * more than 16 tiles take the direct form's big-triangle path.  Both halves
+ * take the same arguments as ldni_sample_count / ldni_sample_fill, with the
+ * binned workspace; call count, size the arrays from info->n, then fill.
+ */
+int ldni_sample_binned_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                             const ldni_grid_t *grid, int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws,
+                             size_t ws_bytes, void *stream);
+int ldni_sample_binned_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                            int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes,
+                            void *stream);
 
 /* ---- launch tuning ---------------------------------------------------- */
 
@@ -623,7 +652,8 @@ int64_t ldni_profile_recorded(void);
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
- * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour, 29 chain). */
+ * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour, 29 chain, 30 bin,
+ * 31 tile). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

@@ -20,6 +20,7 @@ LDNI_ECUDA = -6
 AXIS_ALL = 3
 MODE_EXACT2 = 0
 MODE_LEARNED1 = 1
+MODE_BINNED2 = 2
 OP_UNION, OP_INTER, OP_DIFF = 0, 1, 2
 
 ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX, ST_EVENTS = 1, 2, 4, 8, 16, 32, 64
@@ -89,6 +90,9 @@ SIGNATURES = {
     "ldni_sample": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _I32, _PL, _P, _P, _SZ, _P]),
     "ldni_sample_count": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
     "ldni_sample_fill": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
+    "ldni_sample_binned_workspace_size": (ctypes.c_int, [_I64, _I64, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "ldni_sample_binned_count": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
+    "ldni_sample_binned_fill": (ctypes.c_int, [_P, _I64, _P, _I64, _PG, _I32, _PL, _P, _P, _SZ, _P]),
     "ldni_boolean_workspace_size": (ctypes.c_int, [_I32, ctypes.POINTER(_SZ)]),
     "ldni_boolean": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P, _SZ, _P]),
     "ldni_boolean_static": (ctypes.c_int, [_PL, _PG, _PL, _PG, _I32, ctypes.c_float, _PL, _P, _P]),

@@ -43,7 +43,9 @@ enum KernelId : int {
     K_CODEC = 27,
     K_CONTOUR = 28,
     K_CHAIN = 29,
-    K_NUM = 30
+    K_BIN = 30,
+    K_TILE = 31,
+    K_NUM = 32
 };
 
 struct ProfState {

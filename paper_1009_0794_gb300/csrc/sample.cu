@@ -186,6 +186,196 @@ __global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo
     }
 }
 
+// ---- tile binning (exact two-pass, binned) ------------------------------------
+//
+// The same crossings, counted and placed tile by tile instead of triangle by
+// triangle: a counting sort bins every (triangle, image) pair to the 16 x 16
+// pixel tiles its pixel box touches; one block per tile then stages the
+// exact setup (snapped, oriented edge functions, depths, normal) of its
+// triangles in shared memory, 128 at a time, and every thread - one pixel -
+// tests them all.  A pixel counts its crossings in a register and, in the
+// fill, writes them to its own front slots without any atomic; pairs whose
+// box touches more than kMaxBinTiles tiles go to the big-triangle queue of
+// the direct form, which takes the back slots.  The per-ray order comes from
+// sort_rays, so the output equals the direct form's bit for bit.
+constexpr int kBinTile = 16;      // pixels per tile side (one per thread)
+constexpr int kMaxBinTiles = 16;  // tiles a binned pair may touch
+static_assert(kBinTile * kBinTile == kThreads, "a tile is one pixel per thread");
+
+struct BinImg {
+    int *tile_cnt[3];   // pairs per tile (count), then the scatter's cursor
+    int *tile_off[3];   // exclusive prefix of tile_cnt, tiles + 1 entries
+    int *list[3];       // triangle indices, tile by tile
+    int tiles_x;        // tiles per image side
+};
+
+// Pixel box of triangle T on image A, with its setup: 0 none, 1 small
+// (Setup32 in S), 2 big (Setup64 in L); i0..i1, j0..j1 the pixel box.
+template <int A>
+__device__ __forceinline__ int classify(const TriView &T, int res, Setup32 &S, Setup64 &L, int &i0, int &i1,
+                                        int &j0, int &j1, bool with_depth) {
+    const int kind = with_depth ? setup_axis<A, true>(T, res, S) : setup_axis<A, false>(T, res, S);
+    if (kind == kNone) return 0;
+    if (kind == kSmall) {
+        i0 = S.i0;
+        j0 = S.j0;
+        i1 = S.i0 + S.w - 1;
+        j1 = S.j0 + S.h - 1;
+        return 1;
+    }
+    return setup_big(T, A, res, L, i0, i1, j0, j1) ? 2 : 0;
+}
+
+__device__ __forceinline__ int tiles_touched(int i0, int i1, int j0, int j1) {
+    return ((i1 / kBinTile) - (i0 / kBinTile) + 1) * ((j1 / kBinTile) - (j0 / kBinTile) + 1);
+}
+
+// kScatter false: count the pairs of every tile; true: write them into the
+// tile lists, and queue the pairs that touch too many tiles.
+template <bool kScatter, int A>
+__device__ __forceinline__ void bin_axis(const TriView &T, int t, int res, const BinImg &b, int *big_q, long long qcap,
+                                         int *big_n) {
+    Setup32 S;
+    Setup64 L;
+    int i0, i1, j0, j1;
+    const int kind = classify<A>(T, res, S, L, i0, i1, j0, j1, false);
+    if (kind == 0) return;
+    if (tiles_touched(i0, i1, j0, j1) > kMaxBinTiles) {
+        if (kScatter) enqueue_big(big_q, qcap, big_n, t * 4 + A, (long long)(i1 - i0 + 1) * (j1 - j0 + 1));
+        return;
+    }
+    for (int ty = j0 / kBinTile; ty <= j1 / kBinTile; ++ty)
+        for (int tx = i0 / kBinTile; tx <= i1 / kBinTile; ++tx) {
+            const int tile = ty * b.tiles_x + tx;
+            if (!kScatter) {
+                atomicAdd(b.tile_cnt[A] + tile, 1);
+            } else {
+                const int pos = atomicAdd(b.tile_cnt[A] + tile, 1);
+                b.list[A][b.tile_off[A][tile] + pos] = t;
+            }
+        }
+}
+
+template <bool kScatter>
+__global__ void __launch_bounds__(kThreads) bin_pass(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                     int nt, int nv, GridDev g, int ax_lo, int ax_hi, BinImg b,
+                                                     int *big_q, long long qcap, int *big_n, ldni_info_t *info) {
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nt; t += gridDim.x * blockDim.x) {
+        TriView T;
+        const unsigned bad = load_tri(verts, tris, t, nv, g, T);
+        if (bad) {
+            if (!kScatter) set_status(info, bad);
+            continue;
+        }
+        if (ax_lo <= 0 && 0 <= ax_hi) bin_axis<kScatter, 0>(T, t, g.res, b, big_q, qcap, big_n);
+        if (ax_lo <= 1 && 1 <= ax_hi) bin_axis<kScatter, 1>(T, t, g.res, b, big_q, qcap, big_n);
+        if (ax_lo <= 2 && 2 <= ax_hi) bin_axis<kScatter, 2>(T, t, g.res, b, big_q, qcap, big_n);
+    }
+}
+
+// One staged triangle of a tile: its setup (small: Setup32, big: Setup64),
+// pixel box, id and normal.
+struct TileTri {
+    Setup64 L;
+    Setup32 S;
+    int kind;  // 0 none, 1 small, 2 big
+    int t;
+    int i0, i1, j0, j1;
+    float nx, ny, nz;
+};
+
+template <int A>
+__device__ __forceinline__ void stage_tri(const float *__restrict__ verts, const int *__restrict__ tris, int nv,
+                                          const GridDev &g, int t, bool fill, TileTri &R) {
+    TriView T;
+    R.kind = 0;
+    R.t = t;
+    if (load_tri(verts, tris, t, nv, g, T)) return;
+    R.kind = classify<A>(T, g.res, R.S, R.L, R.i0, R.i1, R.j0, R.j1, fill);
+    if (fill && R.kind) face_normal(T.p[0], T.p[1], T.p[2], R.nx, R.ny, R.nz);
+}
+
+// Block = tile (blockIdx.x) of image ax_lo + blockIdx.y; thread = pixel.
+// Count pass: counts[p] = the pixel's binned crossings (before the big pairs
+// add theirs).  Fill pass: the crossings go to the ray's first slots.
+constexpr int kTileStage = 128;  // triangles staged per round (26 KB of shared memory)
+
+template <bool kFill>
+__global__ void __launch_bounds__(kThreads) tile_pass(const float *__restrict__ verts, const int *__restrict__ tris,
+                                                      int nv, GridDev g, int ax_lo, BinImg b, Img o,
+                                                      ldni_info_t *info) {
+    __shared__ TileTri st[kTileStage];
+    const int a = ax_lo + blockIdx.y;
+    const int tile = blockIdx.x;
+    const int tx = tile % b.tiles_x, ty = tile / b.tiles_x;
+    const int i = tx * kBinTile + (threadIdx.x % kBinTile), j = ty * kBinTile + (threadIdx.x / kBinTile);
+    const bool mine = i < g.res && j < g.res;
+    const int *lst = sel(b.list, a) + sel(b.tile_off, a)[tile];
+    const int n = sel(b.tile_off, a)[tile + 1] - sel(b.tile_off, a)[tile];
+    const long long p = (long long)j * g.res + i;
+    int found = 0;
+    long long slot_end = 0;  // fill: the pixel's crossings take its last slots, downwards from here
+    long long cap = 0;
+    if (kFill && mine) {
+        slot_end = (long long)(a == 0 ? o.offsets[0] : (a == 1 ? o.offsets[1] : o.offsets[2]))[p] +
+                   sel(o.count, a)[p];
+        cap = a == 0 ? o.cap[0] : (a == 1 ? o.cap[1] : o.cap[2]);
+    }
+    for (int k0 = 0; k0 < n; k0 += kTileStage) {
+        const int k = k0 + threadIdx.x;
+        if (threadIdx.x < kTileStage && k < n) {
+            if (a == 0) stage_tri<0>(verts, tris, nv, g, lst[k], kFill, st[threadIdx.x]);
+            else if (a == 1) stage_tri<1>(verts, tris, nv, g, lst[k], kFill, st[threadIdx.x]);
+            else stage_tri<2>(verts, tris, nv, g, lst[k], kFill, st[threadIdx.x]);
+        }
+        __syncthreads();
+        const int m = min(kTileStage, n - k0);
+        for (int r = 0; r < m && mine; ++r) {
+            const TileTri &R = st[r];
+            if (R.kind == 0 || i < R.i0 || i > R.i1 || j < R.j0 || j > R.j1) continue;
+            float d = 0.0f;
+            bool hit;
+            if (R.kind == 1) {
+                int e0, e1, e2;
+                R.S.edges(i, j, e0, e1, e2);
+                hit = (e0 > 0) & (e1 > 0) & (e2 > 0);
+                if (kFill && hit) d = R.S.depth_from(e0, e1, e2);
+            } else {
+                hit = R.L.inside(i, j);
+                if (kFill && hit) d = R.L.depth(i, j);
+            }
+            if (!hit) continue;
+            if (kFill) {
+                const long long at = slot_end - 1 - found;
+                if (at >= cap || at < 0) {
+                    set_status(info, LDNI_ST_CAPACITY);
+                } else {
+                    (a == 0 ? o.depth[0] : (a == 1 ? o.depth[1] : o.depth[2]))[at] = d;
+                    (a == 0 ? o.tri[0] : (a == 1 ? o.tri[1] : o.tri[2]))[at] = R.t;
+                    float *X = a == 0 ? o.nx[0] : (a == 1 ? o.nx[1] : o.nx[2]);
+                    float *Y = a == 0 ? o.ny[0] : (a == 1 ? o.ny[1] : o.ny[2]);
+                    float *Z = a == 0 ? o.nz[0] : (a == 1 ? o.nz[1] : o.nz[2]);
+                    if (Y) {
+                        X[at] = R.nx;
+                        Y[at] = R.ny;
+                        Z[at] = R.nz;
+                    } else {  // approximate normals (Section 3 item 1)
+                        X[at] = __uint_as_float(encode_normal8(R.nx, R.ny, R.nz));
+                    }
+                }
+            }
+            ++found;
+        }
+        __syncthreads();
+    }
+    if (!mine) return;
+    int *cnt = sel(o.count, a) + p;
+    if (!kFill)
+        *cnt = found;  // the big pairs add theirs afterwards
+    else
+        *cnt -= found;  // the big pairs take the remaining (first) slots
+}
+
 struct SampleWs {
     int *count[3];
     int *big_n;          // two queue counts right after the counts: one memset clears all
@@ -296,6 +486,121 @@ int run_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, co
     return cuda_status();
 }
 
+// ---- binned form: workspace and launches --------------------------------------
+
+struct BinWs {
+    BinImg b;
+    int *tile_cnt0;           // every image's tile counts (one clear)
+    size_t tile_bytes;
+    long long *tile_words;    // scan partials of the tile counts
+    ldni_info_t *tile_info;   // the tile scan's report (not the caller's)
+    int ntiles;
+};
+
+BinWs carve_bin_ws(Carver &c, long long nt, int res, int naxes) {
+    BinWs w{};
+    w.b.tiles_x = (res + kBinTile - 1) / kBinTile;
+    w.ntiles = w.b.tiles_x * w.b.tiles_x;
+    const long long stride = ((long long)w.ntiles + 1 + 63) / 64 * 64;
+    int *cnt = c.take<int>((size_t)(stride * naxes));
+    int *off = c.take<int>((size_t)(stride * naxes));
+    const long long lcap = (long long)kMaxBinTiles * (nt > 0 ? nt : 1);
+    int *lst = c.take<int>((size_t)(lcap * naxes));
+    for (int a = 0; a < naxes; ++a) {
+        w.b.tile_cnt[a] = cnt ? cnt + (size_t)a * stride : nullptr;
+        w.b.tile_off[a] = off ? off + (size_t)a * stride : nullptr;
+        w.b.list[a] = lst ? lst + (size_t)a * lcap : nullptr;
+    }
+    w.tile_cnt0 = cnt;
+    w.tile_bytes = sizeof(int) * (size_t)(stride * naxes);
+    w.tile_words = c.take<long long>(csr_scan_partials(w.ntiles) * naxes);
+    w.tile_info = c.take<ldni_info_t>(1);
+    return w;
+}
+
+// The binned image arrays indexed by image (a = ax_lo + k).
+BinImg bin_view(const BinWs &w, const Call &C) {
+    BinImg b{};
+    b.tiles_x = w.b.tiles_x;
+    for (int k = 0; k < C.naxes; ++k) {
+        b.tile_cnt[C.ax_lo + k] = w.b.tile_cnt[k];
+        b.tile_off[C.ax_lo + k] = w.b.tile_off[k];
+        b.list[C.ax_lo + k] = w.b.list[k];
+    }
+    return b;
+}
+
+int run_binned_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const Call &C, const BinWs &w,
+                     ldni_info_t *info) {
+    if (int rc_ = cuda_check(cudaMemsetAsync(C.w.count[0], 0, C.w.clear_bytes, C.s))) return rc_;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.tile_cnt0, 0, w.tile_bytes, C.s))) return rc_;
+    const BinImg b = bin_view(w, C);
+    if (nt > 0)
+        LDNI_LAUNCH(K_BIN, C.s,
+                    bin_pass<false><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g, C.ax_lo,
+                                                                          C.ax_hi, b, C.w.big_q, C.w.qcap, C.w.big_n,
+                                                                          info));
+    const int *tc[3];
+    int *to[3];
+    for (int k = 0; k < C.naxes; ++k) {
+        tc[k] = w.b.tile_cnt[k];
+        to[k] = w.b.tile_off[k];
+    }
+    int rc = cuda_status();
+    if (rc != LDNI_OK) return rc;
+    rc = csr_scan(tc, to, C.naxes, w.ntiles, w.tile_words, w.tile_info, 0, C.s);
+    if (rc != LDNI_OK) return rc;
+    if (int rc_ = cuda_check(cudaMemsetAsync(w.tile_cnt0, 0, w.tile_bytes, C.s))) return rc_;  // the scatter's cursors
+    if (nt > 0)
+        LDNI_LAUNCH(K_BIN, C.s,
+                    bin_pass<true><<<grid_blocks(nt), kThreads, 0, C.s>>>(verts, tris, (int)nt, (int)nv, C.g, C.ax_lo,
+                                                                         C.ax_hi, b, C.w.big_q, C.w.qcap, C.w.big_n,
+                                                                         info));
+    LDNI_LAUNCH(K_TILE, C.s,
+                tile_pass<false><<<dim3(w.ntiles, C.naxes), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.ax_lo, b,
+                                                                               C.o, info));
+    if (nt > 0)
+        LDNI_LAUNCH(K_COUNT_BIG, C.s,
+                    big_pass<false><<<5 * num_sms(), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                        C.w.qcap, C.w.big_n, num_sms(), info));
+    const int *cnt[3];
+    int *off[3];
+    for (int k = 0; k < C.naxes; ++k) {
+        cnt[k] = C.w.count[k];
+        off[k] = const_cast<int *>(C.o.offsets[C.ax_lo + k]);
+    }
+    rc = cuda_status();
+    if (rc != LDNI_OK) return rc;
+    return csr_scan(cnt, off, C.naxes, C.nrays, C.w.scan_words, info, C.ax_lo, C.s);
+}
+
+int run_binned_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const Call &C, const BinWs &w,
+                    ldni_info_t *info) {
+    const BinImg b = bin_view(w, C);
+    LDNI_LAUNCH(K_TILE, C.s,
+                tile_pass<true><<<dim3(w.ntiles, C.naxes), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.ax_lo, b,
+                                                                              C.o, info));
+    if (nt > 0)
+        LDNI_LAUNCH(K_FILL_BIG, C.s,
+                    big_pass<true><<<5 * num_sms(), kThreads, 0, C.s>>>(verts, tris, (int)nv, C.g, C.o, C.w.big_q,
+                                                                       C.w.qcap, C.w.big_n, num_sms(), info));
+    LDNI_LAUNCH(K_SORT, C.s,
+                sort_rays<<<dim3(grid_blocks(C.nrays), C.naxes), kThreads, 0, C.s>>>(C.nrays, C.ax_lo, C.o, info));
+    return cuda_status();
+}
+
+// prepare() plus the binned part of the workspace (after the direct form's).
+int prepare_binned(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
+                   int32_t axis, ldni_layers_t *out, ldni_info_t *info, void *ws, size_t ws_bytes, void *stream,
+                   bool need_samples, Call &C, BinWs &w) {
+    int rc = prepare(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream, need_samples, C);
+    if (rc != LDNI_OK) return rc;
+    Carver c(ws, ws_bytes);
+    carve_sample_ws(c, nt, grid->res, C.naxes);
+    w = carve_bin_ws(c, nt, grid->res, C.naxes);
+    return c.fits() ? LDNI_OK : LDNI_EWORKSPACE;
+}
+
 }  // namespace
 }  // namespace ldni
 
@@ -337,9 +642,46 @@ static int ldni_sample_exact2(const float *verts, int64_t nv, const int32_t *tri
     return run_fill(verts, nv, tris, nt, C, info);
 }
 
+extern "C" int ldni_sample_binned_workspace_size(int64_t nv, int64_t nt, int32_t res, int32_t axis, size_t *bytes) {
+    if (!bytes || res < 1 || res > 8192 || nt < 0 || nv < 0 || axis < 0 || axis > LDNI_AXIS_ALL) return LDNI_EINVAL;
+    if (nt > (INT_MAX / (4 * kMaxBinTiles))) return LDNI_ETOOLARGE;
+    Carver c(nullptr, 0);
+    const int naxes = axis == LDNI_AXIS_ALL ? 3 : 1;
+    carve_sample_ws(c, nt, res, naxes);
+    carve_bin_ws(c, nt, res, naxes);
+    *bytes = align_up(c.off);
+    return LDNI_OK;
+}
+
+extern "C" int ldni_sample_binned_count(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                        const ldni_grid_t *grid, int32_t axis, ldni_layers_t *out, ldni_info_t *info,
+                                        void *ws, size_t ws_bytes, void *stream) {
+    if (nt > (INT_MAX / (4 * kMaxBinTiles))) return LDNI_ETOOLARGE;
+    Call C;
+    BinWs w;
+    int rc = prepare_binned(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream, false, C, w);
+    if (rc != LDNI_OK) return rc;
+    return run_binned_count(verts, nv, tris, nt, C, w, info);
+}
+
+extern "C" int ldni_sample_binned_fill(const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                                       const ldni_grid_t *grid, int32_t axis, ldni_layers_t *out, ldni_info_t *info,
+                                       void *ws, size_t ws_bytes, void *stream) {
+    if (nt > (INT_MAX / (4 * kMaxBinTiles))) return LDNI_ETOOLARGE;
+    Call C;
+    BinWs w;
+    int rc = prepare_binned(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream, true, C, w);
+    if (rc != LDNI_OK) return rc;
+    return run_binned_fill(verts, nv, tris, nt, C, w, info);
+}
+
 extern "C" int ldni_sample(const float *verts, int64_t nv, const int32_t *tris, int64_t nt, const ldni_grid_t *grid,
                            int32_t axis, int32_t mode, ldni_layers_t *out, ldni_info_t *info, void *ws,
                            size_t ws_bytes, void *stream) {
-    if (mode != LDNI_MODE_EXACT2) return LDNI_EINVAL;  // the learned one-pass form is ldni_sample_learned
-    return ldni_sample_exact2(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream);
+    if (mode == LDNI_MODE_EXACT2) return ldni_sample_exact2(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes,
+                                                            stream);
+    if (mode != LDNI_MODE_BINNED2) return LDNI_EINVAL;  // the learned one-pass form is ldni_sample_learned
+    int rc = ldni_sample_binned_count(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream);
+    if (rc != LDNI_OK) return rc;
+    return ldni_sample_binned_fill(verts, nv, tris, nt, grid, axis, out, info, ws, ws_bytes, stream);
 }

@@ -22,6 +22,15 @@ constexpr int kHugePixels = 2048;         // boxes above this take a whole block
 // function |d_u (c_v - v) - d_v (c_u - u)| < 2 * 32767^2 < 2^31.
 constexpr int kSmallExtent = 32000;
 
+// Depth of a crossing, d = sum_k lambda_k a_k with lambda_k = E_k / A2 from
+// the exact edge functions E_k (FP32 values of integers) and inv = 1 / A2:
+// every operation is an explicit rounding, so every traversal (direct,
+// binned, one-pass, batched) computes the same bits wherever it is inlined.
+__device__ __forceinline__ float depth_of(float E0, float E1, float E2, float inv, float a0, float a1, float a2) {
+    const float l0 = __fmul_rn(E0, inv), l1 = __fmul_rn(E1, inv), l2 = __fmul_rn(E2, inv);
+    return __fmaf_rn(l2, a2, __fmaf_rn(l1, a1, __fmul_rn(l0, a0)));
+}
+
 // Per-thread view of one triangle: snapped lattice coordinates of its three
 // vertices (all three world axes) and the world positions.
 struct TriView {
@@ -69,10 +78,7 @@ struct Setup32 {
     // depth from the biased edge functions at a crossing: lambda_k from the
     // exact edge functions (bias removed); the edge opposite vertex k is k+1
     __device__ __forceinline__ float depth_from(int e0, int e1, int e2) const {
-        const float l0 = __int2float_rn(e1 - b1) * inv;
-        const float l1 = __int2float_rn(e2 - b2) * inv;
-        const float l2 = __int2float_rn(e0 - b0) * inv;
-        return l0 * a0 + l1 * a1 + l2 * a2;
+        return depth_of(__int2float_rn(e1 - b1), __int2float_rn(e2 - b2), __int2float_rn(e0 - b0), inv, a0, a1, a2);
     }
     __device__ __forceinline__ float depth(int i, int j) const {
         int e0, e1, e2;
@@ -111,10 +117,7 @@ struct Setup64 {
     __device__ __forceinline__ float depth(int i, int j) const {
         long long e0, e1, e2;
         edges(i, j, e0, e1, e2);
-        const float l0 = (float)(e1 - b1) * inv;
-        const float l1 = (float)(e2 - b2) * inv;
-        const float l2 = (float)(e0 - b0) * inv;
-        return l0 * a0 + l1 * a1 + l2 * a2;
+        return depth_of(__ll2float_rn(e1 - b1), __ll2float_rn(e2 - b2), __ll2float_rn(e0 - b0), inv, a0, a1, a2);
     }
 };
 
@@ -236,7 +239,7 @@ __device__ __forceinline__ bool setup_big(const TriView &T, int a, int res, Setu
     S.b0 = (v1 - v0 > 0 || (v1 == v0 && u1 - u0 < 0)) ? 1 : 0;
     S.b1 = (v2 - v1 > 0 || (v2 == v1 && u2 - u1 < 0)) ? 1 : 0;
     S.b2 = (v0 - v2 > 0 || (v0 == v2 && u0 - u2 < 0)) ? 1 : 0;
-    S.inv = 1.0f / (float)A2;
+    S.inv = __frcp_rn(__ll2float_rn(A2));
     const long long umin = min(u0, min(u1, u2)), umax = max(u0, max(u1, u2));
     const long long vmin = min(v0, min(v1, v2)), vmax = max(v0, max(v1, v2));
     i0 = (int)max((umin + 127) >> 8, 0ll);
@@ -258,21 +261,27 @@ __device__ __forceinline__ void enqueue_big(Code *q, long long qcap, int *n, Cod
 }
 
 // Visit every queued pair with body(code, first, step), which walks the
-// pair's box pixels first, first + step, ...  Blocks blk of nblk: the last
-// huge_blocks take the huge pairs a block each, the others the rest a warp each.
+// pair's box pixels first, first + step, ...  Blocks blk of nblk: the
+// medium pairs a warp each; the huge pairs are shared out to groups of
+// nblk / (huge pairs) blocks (at least one), each group sweeping its pairs
+// with all its threads, so that a few faces of hundreds of thousands of
+// pixels keep every SM busy and many huge faces run side by side.
+// huge_blocks is unused (kept for the callers' launch shapes).
 template <class Code, class F>
 __device__ __forceinline__ void for_each_big(const Code *q, long long qcap, const int *n, int blk, int nblk,
                                              int huge_blocks, F &&body) {
-    const int med_blocks = nblk - huge_blocks;
-    if (blk < med_blocks) {
-        const int nmed = n[0];
-        const int wpb = blockDim.x >> 5;
-        for (int e = blk * wpb + (threadIdx.x >> 5); e < nmed; e += med_blocks * wpb)
-            body(q[e], (int)(threadIdx.x & 31), 32);
-    } else {
-        const int nh = n[1];
-        for (int e = blk - med_blocks; e < nh; e += huge_blocks) body(q[qcap - 1 - e], (int)threadIdx.x, (int)blockDim.x);
-    }
+    (void)huge_blocks;
+    const int nmed = n[0];
+    const int wpb = blockDim.x >> 5;
+    for (int e = blk * wpb + (threadIdx.x >> 5); e < nmed; e += nblk * wpb)
+        body(q[e], (int)(threadIdx.x & 31), 32);
+    const int nh = n[1];
+    if (nh <= 0) return;
+    const int G = max(1, nblk / nh);  // blocks per huge pair
+    const int groups = nblk / G, grp = blk / G, sub = blk - grp * G;
+    if (grp >= groups) return;  // the blocks left over when nblk is no multiple of G
+    for (int e = grp; e < nh; e += groups)
+        body(q[qcap - 1 - e], sub * (int)blockDim.x + (int)threadIdx.x, G * (int)blockDim.x);
 }
 
 __device__ __forceinline__ bool key_less(float d0, int t0, float d1, int t1) {

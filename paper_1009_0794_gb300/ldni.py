@@ -203,27 +203,42 @@ def empty_layers_flat(grid: Grid, axes: Sequence[int], capacities: Sequence[int]
     return out, flat
 
 
+def sample_binned_workspace_size(nv: int, nt: int, res: int, axis=_lib.AXIS_ALL) -> int:
+    sz = ctypes.c_size_t(0)
+    _lib.check(_lib.load().ldni_sample_binned_workspace_size(int(nv), int(nt), int(res),
+                                                             _lib.AXIS_ALL if axis in ("all", None) else int(axis),
+                                                             ctypes.byref(sz)), "ldni_sample_binned_workspace_size")
+    return int(sz.value)
+
+
 def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=None,
            check_odd: bool = False, packed: bool = False) -> Union[LDNI, List[LDNI]]:
     """Sample a closed mesh into LDNIs (Section 3, Definitions 1-4); packed:
-    approximate 8-bit normals (Section 3 item 1).
+    approximate 8-bit normals (Section 3 item 1).  mode "exact2" traverses
+    triangle by triangle, "binned2" tile by tile (identical output).
 
     Exact sizing: the count pass runs, the sample totals are read back (one
     device->host read, the only synchronisation), the sample arrays are
     allocated to size, then the fill pass and per-ray sort run."""
     lib = _lib.load()
+    if mode not in ("exact2", "binned2"):
+        raise _lib.LDNIError(-1, f"sample: mode {mode!r}")
+    binned = mode == "binned2"
+    count_fn = lib.ldni_sample_binned_count if binned else lib.ldni_sample_count
+    fill_fn = lib.ldni_sample_binned_fill if binned else lib.ldni_sample_fill
     v = _dev(verts, torch.float32).reshape(-1, 3)
     t = _dev(tris, torch.int32).reshape(-1, 3)
     axes = _axes(axis)
     cax = _lib.AXIS_ALL if len(axes) == 3 else axes[0]
-    ws = torch.empty(sample_workspace_size(v.shape[0], t.shape[0], grid.res, cax), dtype=torch.uint8, device="cuda")
+    wsz = (sample_binned_workspace_size if binned else sample_workspace_size)(v.shape[0], t.shape[0], grid.res, cax)
+    ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
     info = new_info()
     outs = [empty_layers(grid, a, 0) for a in axes]
     arr = (_CLayers * len(axes))(*[o.c() for o in outs])
     g = grid.c()
     sp = _stream_ptr(stream)
-    _lib.check(lib.ldni_sample_count(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
-                                     info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_count")
+    _lib.check(count_fn(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
+                        info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_count")
     meta = info_decode(info)
     _raise_status(meta["status"], "ldni_sample_count")
     res_list = []
@@ -234,8 +249,8 @@ def sample(verts, tris, grid: Grid, axis="all", mode: str = "exact2", stream=Non
         L.n = n
         res_list.append(L)
     arr = (_CLayers * len(axes))(*[o.c() for o in res_list])
-    _lib.check(lib.ldni_sample_fill(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
-                                    info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_fill")
+    _lib.check(fill_fn(v.data_ptr(), v.shape[0], t.data_ptr(), t.shape[0], ctypes.byref(g), cax, arr,
+                       info.data_ptr(), ws.data_ptr(), ws.numel(), sp), "ldni_sample_fill")
     if check_odd:
         meta = info_decode(info)
         _raise_status(meta["status"], "ldni_sample_fill")
@@ -251,20 +266,23 @@ class SamplePlan:
     LDNI_ST_CAPACITY in ``info``."""
 
     def __init__(self, nv: int, nt: int, grid: Grid, capacities: Sequence[int], axis="all", slack: float = 1.0,
-                 packed: bool = False):
+                 packed: bool = False, mode: str = "exact2"):
         self.grid = grid
         self.axes = _axes(axis)
         self.cax = _lib.AXIS_ALL if len(self.axes) == 3 else self.axes[0]
-        self.ws = torch.empty(sample_workspace_size(nv, nt, grid.res, self.cax), dtype=torch.uint8, device="cuda")
+        self.mode = _lib.MODE_BINNED2 if mode == "binned2" else _lib.MODE_EXACT2
+        wsz = (sample_binned_workspace_size if mode == "binned2" else sample_workspace_size)(nv, nt, grid.res,
+                                                                                           self.cax)
+        self.ws = torch.empty(wsz, dtype=torch.uint8, device="cuda")
         self.info = new_info()
         self.outs = [empty_layers(grid, a, int(np.ceil(c * slack)), packed) for a, c in zip(self.axes, capacities)]
         self._arr = (_CLayers * len(self.axes))(*[o.c() for o in self.outs])
         self._g = grid.c()
 
-    def run(self, verts: torch.Tensor, tris: torch.Tensor, stream=None, mode: int = _lib.MODE_EXACT2):
+    def run(self, verts: torch.Tensor, tris: torch.Tensor, stream=None):
         lib = _lib.load()
         _lib.check(lib.ldni_sample(verts.data_ptr(), verts.shape[0], tris.data_ptr(), tris.shape[0],
-                                   ctypes.byref(self._g), self.cax, mode, self._arr, self.info.data_ptr(),
+                                   ctypes.byref(self._g), self.cax, self.mode, self._arr, self.info.data_ptr(),
                                    self.ws.data_ptr(), self.ws.numel(), _stream_ptr(stream)), "ldni_sample")
 
     def finish(self) -> List[LDNI]:

@@ -8,6 +8,7 @@ JSON file so that later processes skip the measurement.
     from paper_1009_0794_gb300 import tune
     tune.tune_boolean(A, B, "union")          # picks and applies
     tune.tune_sampling(verts, tris, grid)
+    tune.choose_sampling_mode(verts, tris, grid)  # direct or tile-binned traversal
 """
 from __future__ import annotations
 
@@ -178,3 +179,28 @@ def tune_sampling(verts, tris, grid: "L.Grid", reps: int = 10, candidates: Itera
         set(**choice)
     _store_cache(key, {"choice": choice, "ms": ms})
     return {"choice": choice, "ms": ms, "cached": False}
+
+
+def choose_sampling_mode(verts, tris, grid: "L.Grid", reps: int = 10, use_cache: bool = True) -> dict:
+    """Time the two exact traversals of one mesh - triangle by triangle
+    ("exact2") and tile by tile after binning ("binned2"), which give the same
+    bits - and return the faster: {"mode": ..., "ms": {...}, "cached": bool}.
+    The choice is cached per device, resolution and mesh size class; pass it
+    to sample(..., mode=) or SamplePlan(..., mode=)."""
+    v = L._dev(verts, torch.float32).reshape(-1, 3)
+    t = L._dev(tris, torch.int32).reshape(-1, 3)
+    key = f"mode/{_device_key()}/res{grid.res}/T{_bucket(t.shape[0])}"
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            return {"mode": hit["mode"], "ms": hit.get("ms", {}), "cached": True}
+    sizes = [X.n for X in L.sample(v, t, grid, "all")]
+    flush = _flush_buffer()
+    ms = {}
+    for mode in ("exact2", "binned2"):
+        plan = L.SamplePlan(v.shape[0], t.shape[0], grid, sizes, mode=mode)
+        ms[mode] = _time(lambda: plan.run(v, t), reps, flush)
+        plan.finish()
+    mode = min(ms, key=ms.get)
+    _store_cache(key, {"mode": mode, "ms": ms})
+    return {"mode": mode, "ms": ms, "cached": False}
