@@ -126,7 +126,8 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------
-# CPU oracle leg
+# CPU oracle leg: the oracle as it stands, on every host core (one process
+# per core, each running whole units of the workload on its own)
 # ----------------------------------------------------------------------------
 def _oracle_step(sphere, knot_ref, axes, res):
     import oracle
@@ -140,23 +141,95 @@ def _oracle_step(sphere, knot_ref, axes, res):
     return rays
 
 
-def cpu_baseline(sphere, knot, budget_s: float = 10.0) -> dict:
-    """The oracle as it stands (single thread) on a bounded sample of the
-    same workload: whole steps (3 axes) repeated for about budget_s."""
+def _oracle_worker(conn, res):
+    """One host core: builds the workload once, then runs oracle steps on
+    command ("axes", [a, ...]) -> rays, or ("for", seconds) -> (rays, steps,
+    seconds of whole 3-axis steps), until ("stop",)."""
+    sys.path.insert(0, ROOT)
     import oracle
+    sphere, knot = _meshes()
     o = (-0.5, -0.5, -0.5)
-    knot_ref = [oracle.as_f32(oracle.sample(*knot, o, 1.0, RES, a, "scan")) for a in range(3)]
-    t0 = time.perf_counter()
-    rays, steps = 0, 0
+    knot_ref = [oracle.as_f32(oracle.sample(*knot, o, 1.0, res, a, "scan")) for a in range(3)]
+    conn.send("ready")
     while True:
-        rays += _oracle_step(sphere, knot_ref, (0, 1, 2), RES)
-        steps += 1
-        if time.perf_counter() - t0 >= budget_s:
-            break
-    dt = time.perf_counter() - t0
-    return {"value": rays / dt, "unit": "rays/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full steps (3 axes at {RES}^2: scan-mode FP64 sampling, union, volume), "
-                      f"{dt:.1f} s single-threaded C"}
+        msg = conn.recv()
+        if msg[0] == "axes":
+            conn.send(_oracle_step(sphere, knot_ref, msg[1], res))
+        elif msg[0] == "for":
+            t0 = time.perf_counter()
+            rays = steps = 0
+            while True:
+                rays += _oracle_step(sphere, knot_ref, (0, 1, 2), res)
+                steps += 1
+                if time.perf_counter() - t0 >= msg[1]:
+                    break
+            conn.send((rays, steps, time.perf_counter() - t0))
+        else:
+            conn.close()
+            return
+
+
+class OraclePool:
+    """One spawned process per host core, each with its own copy of the
+    workload (started before any GPU work: no process is forked from a
+    process that holds a CUDA context)."""
+
+    def __init__(self, workers: int, res: int):
+        import multiprocessing as mp
+        ctx = mp.get_context("spawn")
+        self.conns, self.procs = [], []
+        for _ in range(workers):
+            a, b = ctx.Pipe()
+            p = ctx.Process(target=_oracle_worker, args=(b, res), daemon=True)
+            p.start()
+            self.conns.append(a)
+            self.procs.append(p)
+        for c in self.conns:
+            assert c.recv() == "ready"
+
+    def run(self, msgs):
+        for c, m in zip(self.conns, msgs):
+            c.send(m)
+        return [c.recv() for c in self.conns[:len(msgs)]]
+
+    def close(self):
+        for c in self.conns:
+            try:
+                c.send(("stop",))
+            except Exception:
+                pass
+        for p in self.procs:
+            p.join(timeout=10)
+
+
+def host_cpu() -> dict:
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cpu_count": os.cpu_count(), "model": model}
+
+
+def cpu_baseline(pool: "OraclePool", budget_s: float = 10.0) -> dict:
+    """The oracle as it stands on a bounded sample of the same workload:
+    whole steps (3 images at 1024^2: sampling, union, volume) repeated for
+    about budget_s, first by one core alone, then by every core at once."""
+    one = pool.run([("for", budget_s / 3.0)])[0]
+    res = pool.run([("for", budget_s)] * len(pool.conns))
+    rays = sum(r[0] for r in res)
+    steps = sum(r[1] for r in res)
+    wall = max(r[2] for r in res)
+    cpu = host_cpu()
+    return {"value": rays / wall, "unit": "rays/s", "cores": len(pool.conns), "kind": "oracle",
+            "sample": f"{steps} full steps (3 axes at {RES}^2: scan-mode FP64 sampling, union, volume) on "
+                      f"{len(pool.conns)} processes, one per host core, {wall:.1f} s",
+            "single_core": {"value": one[0] / one[2], "unit": "rays/s", "steps": one[1], "seconds": one[2]},
+            "host": cpu}
 
 
 def run_reference(args):
@@ -165,26 +238,32 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    sphere, knot = _meshes()
-    o = (-0.5, -0.5, -0.5)
-    knot_ref = [oracle.as_f32(oracle.sample(*knot, o, 1.0, RES, a, "scan")) for a in range(3)]
-    for w in range(args.warmup):
-        _oracle_step(sphere, knot_ref, (w % 3,), RES)
-    times = []
-    rays = 0
-    for k in range(args.steps):
-        t0 = time.perf_counter()
-        rays += _oracle_step(sphere, knot_ref, (k % 3,), RES)
-        times.append(time.perf_counter() - t0)
+    cores = max(1, os.cpu_count() or 1)
+    pool = OraclePool(cores, RES)
+    try:
+        # a step: every core runs one image (x, y, z in turn) of the workload: oracle sampling + union + volume
+        msgs = lambda k: [("axes", [(k + w) % 3]) for w in range(cores)]
+        for w in range(args.warmup):
+            pool.run(msgs(w))
+        times = []
+        rays = 0
+        for k in range(args.steps):
+            t0 = time.perf_counter()
+            rays += sum(pool.run(msgs(k)))
+            times.append(time.perf_counter() - t0)
+    finally:
+        pool.close()
     total = sum(times)
     value = rays / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "res": RES,
-                       "reference_step": "one axis per step (x, y, z in turn): oracle sampling + union + volume"},
-            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps of one axis each, single-threaded C"},
+                       "reference_step": f"{cores} host processes, each one image (x, y, z in turn): "
+                                         "oracle sampling + union + volume"},
+            "cpu_baseline": {"value": value, "unit": "rays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} steps of {cores} images each, one process per host core",
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "rays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -399,13 +478,24 @@ def _capture(lib, fn, warm=3):
     return g, int(lib.ldni_launch_count()) - c0
 
 
-def _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, reps):
-    """Sampling alone, exact two-pass vs learned one-pass, each as one CUDA
-    graph, same mesh and GPU, L2 flushed before every replay; outputs
-    compared bit for bit."""
+def _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, reps, kmax):
+    """Sampling alone, each form replayed as one CUDA graph on the same mesh
+    and GPU, L2 flushed before every replay, outputs compared bit for bit:
+    exact two-pass; learned one-pass; and the one-pass form without the
+    network, with a fixed capacity of 2 layers per ray (overflowing tiles
+    redone exactly) and of k_max layers (the deepest ray of the mesh, so
+    nothing overflows, at the price of the largest slab)."""
     import torch
     res = {}
-    for name, p in (("exact2", plan), ("learned1", lplan)):
+    grid = plan.grid
+    N = grid.res * grid.res
+    kmax += kmax & 1
+    caps = [L.capacity for L in plan.outs]
+    fixed2 = ldni.LearnedPlan(vt.shape[0], tt.shape[0], grid, caps, slab_samples=SLAB_LAYERS * 3 * N, net=None,
+                              layers=2)
+    fixedk = ldni.LearnedPlan(vt.shape[0], tt.shape[0], grid, caps, slab_samples=kmax * 3 * N, net=None,
+                              layers=kmax)
+    for name, p in (("exact2", plan), ("learned1", lplan), ("fixed2", fixed2), ("fixed_kmax", fixedk)):
         g, nl = _capture(lib, lambda: p.run(vt, tt))
         res[name + "_kernels"] = nl
         ts = []
@@ -420,10 +510,17 @@ def _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, reps):
             ts.append(e0.elapsed_time(e1))
         res[name + "_ms"] = float(np.median(ts))
         p.finish()
+        if p is not plan:
+            res[name + "_overflow_tiles"] = p.overflow_tiles()
+            res[name + "_identical_output"] = all(ldni.identical(a, b) for a, b in zip(plan.outs, p.outs))
     res["speedup"] = res["exact2_ms"] / res["learned1_ms"]
+    res["speedup_vs_fixed2"] = res["fixed2_ms"] / res["learned1_ms"]
+    res["speedup_vs_fixed_kmax"] = res["fixed_kmax_ms"] / res["learned1_ms"]
+    res["kmax"] = kmax
+    res["slab_slots"] = {"learned1": SLAB_LAYERS * 3 * N, "fixed2": SLAB_LAYERS * 3 * N, "fixed_kmax": kmax * 3 * N}
     res["overflow_tiles"] = lplan.overflow_tiles()
     res["tiles"] = 3 * ldni.ntiles(plan.grid.res)
-    res["identical_output"] = all(ldni.identical(a, b) for a, b in zip(plan.outs, lplan.outs))
+    res["identical_output"] = res["learned1_identical_output"]
     return res
 
 
@@ -597,10 +694,82 @@ def info_ok(ldni, info):
     return ldni.info_decode(info)["status"] == 0
 
 
-def _other_workloads(ldni, lib, flush, reps):
-    """The batched workload (256 meshes of 1k-200k triangles at 64..512^2,
-    one batch call) and the 64-step union chain of a translated torus at
-    512^2 (three images), each replayed as one CUDA graph."""
+def merge_bytes(N: int, nA: float, nB: float, nout: float, images: int = 3) -> float:
+    """Algorithmic bytes of one Boolean of `images` images: both operands'
+    offsets read and the result's written (3 x 4 B per ray), every operand
+    sample read and every result sample written once (20 B each)."""
+    return (2 * 4.0 + 4.0) * images * (N + 1) + 20.0 * (nA + nB) + 20.0 * nout
+
+
+def _flower_knot_512(ldni, timed, peak):
+    """The flower (523,264 triangles) and the (2,3) knot (16,384) at 512^2:
+    sampling by both exact traversals (direct and tile-binned; the tuner
+    keeps the faster) and the three Booleans of the sampled images, each one
+    CUDA graph replay with L2 flushed before it."""
+    import torch
+    import meshgen
+    g = ldni.Grid.cube((-0.5, -0.5, -0.5), 1.0, 512)
+    out = {"workload": "flower 512x512 (theta, phi) grid (523,264 tris) and (2,3) torus knot (16,384 tris) at "
+                       "512^2, three images each; union, intersection and difference"}
+    imgs = {}
+    for name, (v, t) in (("flower", meshgen.flower(512, 512)),
+                         ("knot", meshgen.torus_knot(2, 3, 0.25, 0.1, 0.035, 256, 32))):
+        vt, tt = torch.from_numpy(v).cuda(), torch.from_numpy(t).cuda()
+        sizes = [L.n for L in ldni.sample(vt, tt, g, "all")]
+        row = {"tris": len(t), "samples": int(sum(sizes))}
+        for mode in ("exact2", "binned2"):
+            plan = ldni.SamplePlan(len(v), len(t), g, sizes, mode=mode)
+            ms, nl = timed(lambda: plan.run(vt, tt))
+            plan.finish()
+            row[mode + "_ms"] = ms
+            row[mode + "_rays_per_s"] = 3 * 512 * 512 / (ms * 1e-3)
+            imgs.setdefault(name, plan.outs)
+        row["faster"] = min(("exact2", "binned2"), key=lambda m: row[m + "_ms"])
+        out[name] = row
+    F, K = imgs["flower"], imgs["knot"]
+    ws = torch.empty(ldni.boolean_many_workspace_size(512, 3), dtype=torch.uint8, device="cuda")
+    infos = torch.zeros(3, 4, dtype=torch.int64, device="cuda")
+    vols = torch.zeros(3, dtype=torch.float64, device="cuda")
+    for op in ("union", "inter", "diff"):
+        outs = [ldni.empty_layers(g, a, F[a].capacity + K[a].capacity) for a in range(3)]
+        ms, nl = timed(lambda: ldni.boolean_many(F, K, op, outs=outs, ws=ws, infos=infos, sync=False, vols=vols))
+        nout = [int(x) for x in infos[:, 0].cpu().numpy()]
+        ab = merge_bytes(512 * 512, sum(L.n for L in F), sum(L.n for L in K), sum(nout))
+        out[op] = {"ms": ms, "samples_out": nout, "algorithmic_bytes": ab, "gbs": ab / (ms * 1e-3) / 1e9,
+                   "frac_of_measured_hbm": ab / (ms * 1e-3) / 1e9 / peak, "kernels": nl}
+    return out
+
+
+def _scale_sphere_2048(ldni, timed, net, margin):
+    """The 1,310,720-triangle sphere at 2048^2 x 3: exact two-pass and
+    learned one-pass sampling, each one CUDA graph replay, output compared."""
+    import torch
+    import meshgen
+    v, t = meshgen.scale_sphere()
+    g = ldni.Grid.cube((-0.5, -0.5, -0.5), 1.0, 2048)
+    vt, tt = torch.from_numpy(v).cuda(), torch.from_numpy(t).cuda()
+    sizes = [L.n for L in ldni.sample(vt, tt, g, "all")]
+    N = 2048 * 2048
+    exact = ldni.SamplePlan(len(v), len(t), g, sizes)
+    learned = ldni.LearnedPlan(len(v), len(t), g, sizes, slab_samples=SLAB_LAYERS * 3 * N, net=net, margin=margin,
+                               feature_stride=32)
+    ms_e, nl_e = timed(lambda: exact.run(vt, tt))
+    ms_l, nl_l = timed(lambda: learned.run(vt, tt))
+    exact.finish()
+    learned.finish()
+    same = all(ldni.identical(a, b) for a, b in zip(exact.outs, learned.outs))
+    return {"workload": "noisy geodesic sphere freq 256 (1,310,720 tris) -> 3 LDNIs at 2048^2",
+            "samples": int(sum(sizes)), "exact2_ms": ms_e, "learned1_ms": ms_l,
+            "rays_per_s": 3 * N / (min(ms_e, ms_l) * 1e-3), "samples_per_s": sum(sizes) / (min(ms_e, ms_l) * 1e-3),
+            "learned_speedup": ms_e / ms_l, "overflow_tiles": learned.overflow_tiles(), "identical_output": same,
+            "kernels": {"exact2": nl_e, "learned1": nl_l}}
+
+
+def _other_workloads(ldni, lib, flush, reps, net=None, margin=0.25, peak=6800.0):
+    """The flower and knot at 512^2, the sphere at 2048^2, the batched
+    workload (256 meshes of 1k-200k triangles at 64..512^2, one batch call),
+    the 64-step union chain of a translated torus at 512^2 (three images)
+    and the volume gradient, each replayed as one CUDA graph."""
     import torch
     import meshgen
     o = (-0.5, -0.5, -0.5)
@@ -619,6 +788,8 @@ def _other_workloads(ldni, lib, flush, reps):
             ts.append(e0.elapsed_time(e1))
         return float(np.median(ts)), nl
 
+    extra = {"flower_knot_512": _flower_knot_512(ldni, timed, peak),
+             "scale_sphere_2048": _scale_sphere_2048(ldni, timed, net, margin)}
     batch = meshgen.batch_meshes(256, seed=7)
     plan = ldni.BatchPlan([(v, t) for v, t, _ in batch], [ldni.Grid.cube(o, 1.0, r) for _, _, r in batch])
     ms_b, nl_b = timed(plan.run)
@@ -650,7 +821,7 @@ def _other_workloads(ldni, lib, flush, reps):
     ms_a, nl_a = timed(adjoint)
     n_a = sum(L.n for L in AL)
     ab_a = sum(8.0 * L.n + 12.0 * len(at) + 24.0 * len(av) for L in AL)  # tri_id + depth, mesh, gradient
-    return {"adjoint_200k_512": {"workload": f"volume gradient of the {len(at)}-triangle noisy icosphere at 512^2, "
+    return {**extra, "adjoint_200k_512": {"workload": f"volume gradient of the {len(at)}-triangle noisy icosphere at 512^2, "
                                              f"three images, {n_a} kept crossings", "ms": ms_a,
                                  "crossings_per_s": n_a / (ms_a * 1e-3), "algorithmic_bytes": ab_a,
                                  "gbs": ab_a / (ms_a * 1e-3) / 1e9, "kernels": nl_a},
@@ -675,11 +846,17 @@ def _events(n):
 
 
 def run_ours(args):
+    ws, rank, local = _dist_env()
+    pool = None
+    if not args.no_cpu_baseline and rank == 0:
+        import oracle
+        oracle.build()
+        pool = OraclePool(max(1, os.cpu_count() or 1), RES)  # before any CUDA work in this process
+
     import torch
     import paper_1009_0794_gb300 as ldni
     from paper_1009_0794_gb300 import _lib
 
-    ws, rank, local = _dist_env()
     dist = None
     if ws > 1:
         import torch.distributed as dist
@@ -738,13 +915,21 @@ def run_ours(args):
     _lib.check(lib.ldni_profile_set(None, None, None, 0, 0), "ldni_profile_set")
     kid_of = [int(ids[k]) for k in range(nrec)]
 
-    learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)))
-    learned["train"] = train_meta
-    next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
-    next_rows.update(_offsetting(ldni, lib, U, flush, 10))
-    next_rows["contour_cells"] = _contouring(ldni, lib, U, flush, 10)
-    next_rows["step_packed_normals"] = _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush, 20)
-    other = _other_workloads(ldni, lib, flush, 5)
+    kmax = max(int(L.counts().max()) for L in A0)  # the deepest ray of the mesh
+    if args.only_step:  # the step alone (profiling runs): no comparisons, next rows or other workloads
+        learned, next_rows, other = {"train": train_meta}, {}, {}
+    else:
+        learned = _learned_vs_exact(ldni, lib, plan, lplan, vt, tt, flush, max(10, min(args.steps, 50)), kmax)
+        learned["train"] = train_meta
+        next_rows = {"node_classify": _node_classify(ldni, lib, U, flush, 10)}
+        next_rows.update(_offsetting(ldni, lib, U, flush, 10))
+        next_rows["contour_cells"] = _contouring(ldni, lib, U, flush, 10)
+        next_rows["step_packed_normals"] = _packed_step(ldni, lib, args, net, n_sphere, vt, tt, kv, kt, grid, flush,
+                                                        20)
+    peak_hbm = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    if not args.only_step:
+        other = _other_workloads(ldni, lib, flush, 5, net=net, margin=args.margin, peak=peak_hbm)
 
     # timed region: K graph replays, per-step events, L2 flushed between steps
     steps = args.steps
@@ -816,6 +1001,7 @@ def run_ours(args):
     achieved = ab / (dk_avg_ms * 1e-3) / 1e9
     traffic = None
     ncu_note = None
+    tj = None
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             tj = _json.load(fh)
@@ -835,6 +1021,35 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": ab_k or None,
             "gbs": (ab_k / (st_ms * 1e-3) / 1e9) if ab_k else None,
             "frac_of_measured_hbm": (ab_k / (st_ms * 1e-3) / 1e9 / peak) if ab_k else None}
+    # the whole merge of the step (count, tile scan, write of three images) against its algorithmic bytes
+    N = RES * RES
+    merge_ms = sum(totals.get(k, 0.0) for k in (9, 32, 10))
+    mb = merge_bytes(N, sum(n_sphere), sum(L.n for L in K), sum(n_union))
+    merge = {"kernels": ["bool_count", "bool_scan", "bool_write"], "ms_per_step": merge_ms,
+             "algorithmic_bytes": mb, "gbs": mb / (merge_ms * 1e-3) / 1e9 if merge_ms else None,
+             "frac_of_measured_hbm": mb / (merge_ms * 1e-3) / 1e9 / peak if merge_ms else None,
+             "bytes_formula": "12 B per ray and image (both operands' offsets, the result's) + 20 B per operand "
+                              "sample read + 20 B per result sample written"}
+    # the whole sampling call of the step (every kernel of the learned one-pass form)
+    samp_ids = (14, 15, 17, 18, 4, 5, 19, 20, 25) if args.mode == "learned1" else (1, 2, 4, 5, 6, 7, 8)
+    samp_ms = sum(totals.get(k, 0.0) for k in samp_ids)
+    sb = 12.0 * len(sv) + 12.0 * len(st) + 3 * 4.0 * (N + 1) + 20.0 * sum(n_sphere)
+    sampling = {"ms_per_step": samp_ms, "algorithmic_bytes": sb, "gbs": sb / (samp_ms * 1e-3) / 1e9 if samp_ms else None,
+                "frac_of_measured_hbm": sb / (samp_ms * 1e-3) / 1e9 / peak if samp_ms else None,
+                "bytes_formula": "12 B per vertex and per triangle (mesh read once) + 4 B per CSR offset + "
+                                 "20 B per sample (depth, normal, triangle id)"}
+    # the dominant kernel's issue bound: its warp instructions (ncu, same sources) at 4 per SM and clock
+    issue = None
+    try:
+        name = lib.ldni_kernel_name(dominant).decode()
+        rec = tj.get(name, {}) if tj else {}
+        if rec.get("warp_instructions") and rec.get("source_hash") == _source_hash(rec.get("unit")) and clk.get("sm_mhz"):
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            t_issue = rec["warp_instructions"] / (sms * 4 * clk["sm_mhz"] * 1e6) * 1e3
+            issue = {"warp_instructions": rec["warp_instructions"], "ms_at_full_issue": t_issue,
+                     "frac": t_issue / dk_avg_ms, "sms": sms, "sm_mhz": clk["sm_mhz"]}
+    except Exception:
+        issue = None
     line = {
         "metric": METRIC, "value": value, "unit": "rays/s", "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": total_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -846,12 +1061,15 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "samples_per_s": samples_per_s,
         "samples_per_step": int(sum(n_sphere)),
-        "learned_speedup": learned["speedup"],
+        "learned_speedup": learned.get("speedup"),
         "learned": learned,
         "roofline": {"bound": "hbm", "kernel": lib.ldni_kernel_name(dominant).decode(), "achieved": achieved,
                      "peak": peak, "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dk_avg_ms, "ncu": ncu_note},
+                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dk_avg_ms, "ncu": ncu_note,
+                     "issue": issue},
+        "merge": merge,
+        "sampling_call": sampling,
         "gpu_launches": launches,
         "clocks": clk,
         "stages_ms_per_step": stages,
@@ -859,8 +1077,11 @@ def run_ours(args):
         "next_rows": next_rows,
         "other_workloads": other,
     }
-    if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(*_meshes(), budget_s=args.cpu_budget)
+    if pool is not None:
+        try:
+            line["cpu_baseline"] = cpu_baseline(pool, budget_s=args.cpu_budget)
+        finally:
+            pool.close()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -882,6 +1103,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the step alone (no comparisons, next rows, other workloads; for profiling)")
     ap.add_argument("--settle", type=float, default=1.0, help="seconds of untimed load before the timed steps")
     ap.add_argument("--mode", default="learned1", choices=["learned1", "exact2"])
     ap.add_argument("--margin", type=float, default=0.25)

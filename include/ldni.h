@@ -653,7 +653,7 @@ int64_t ldni_profile_recorded(void);
  * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
  * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour, 29 chain, 30 bin,
- * 31 tile). */
+ * 31 tile, 32 bool_scan). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

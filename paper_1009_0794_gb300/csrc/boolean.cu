@@ -713,7 +713,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
             const float *dA = A.d + a, *dB = B.d + b;
             if (want_vol)
                 cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int) {
-                    len = df_add(len, df_diff((cb ? dB : dA)[ci], (pb ? dB : dA)[pi]));
+                    len = df_add_lazy(len, df_diff((cb ? dB : dA)[ci], (pb ? dB : dA)[pi]));
                 });
             else
                 cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, NoEmit{});
@@ -722,11 +722,11 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
             cnt[k] = two_two(op, eps, d0[k], d1[k], e0[k], e1[k], src);
             if (want_vol) {
                 const float dd[4] = {d0[k], d1[k], e0[k], e1[k]};
-                for (int m = 0; m < cnt[k]; m += 2) len = df_add(len, df_diff(dd[src[m + 1]], dd[src[m]]));
+                for (int m = 0; m < cnt[k]; m += 2) len = df_add_lazy(len, df_diff(dd[src[m + 1]], dd[src[m]]));
             }
         } else {
             cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
-            if (want_vol && cnt[k]) len = df_add(len, df_diff(d1[k], d0[k]));
+            if (want_vol && cnt[k]) len = df_add_lazy(len, df_diff(d1[k], d0[k]));
         }
         mine += cnt[k];
     }
@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
     if (!want_vol) return;  // block-uniform
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1)  // a fixed tree
-        len = df_add(len, DF{__shfl_down_sync(0xffffffffu, len.hi, w), __shfl_down_sync(0xffffffffu, len.lo, w)});
+        len = df_add_lazy(len, DF{__shfl_down_sync(0xffffffffu, len.hi, w), __shfl_down_sync(0xffffffffu, len.lo, w)});
     if ((threadIdx.x & 31) == 0)
         warp_vol[(size_t)blockIdx.x * (kBoolThreads / 32) + (threadIdx.x >> 5)] = make_float2(len.hi, len.lo);
 }
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
 #pragma unroll
             for (int u = 0; u < 4; ++u) v[u] = k0 + u * 1024 < n ? __ldcg(wv + k0 + u * 1024) : make_float2(0.0f, 0.0f);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc = df_add(acc, DF{v[u].x, v[u].y});
+            for (int u = 0; u < 4; ++u) acc = df_add_lazy(acc, DF{v[u].x, v[u].y});
         }
         const DF t = df_block_sum<1024>(acc, shdf);
         if (threadIdx.x == 0) *J.vol[job] = ((double)t.hi + (double)t.lo) * h2;
@@ -1012,7 +1012,8 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
         return rc_;
     LDNI_LAUNCH(K_BOOL_COUNT, s,
                 bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj, warp_vol));
-    LDNI_LAUNCH(K_SCAN_TOP, s, bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol, h2));
+    LDNI_LAUNCH(K_BOOL_SCAN, s,
+                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol, h2));
     LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
     return cuda_status();
 }

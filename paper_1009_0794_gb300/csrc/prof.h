@@ -45,7 +45,8 @@ enum KernelId : int {
     K_CHAIN = 29,
     K_BIN = 30,
     K_TILE = 31,
-    K_NUM = 32
+    K_BOOL_SCAN = 32,
+    K_NUM = 33
 };
 
 struct ProfState {
