@@ -67,7 +67,9 @@ def _compile(nvcc: str, src: str, extra) -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile and link libldni.so unless an up-to-date build exists."""
+    """Compile and link libldni.so unless an up-to-date build exists.  extra:
+    more nvcc flags (also taken, space-separated, from LDNI_EXTRA_NVCC_FLAGS)."""
+    extra = tuple(extra) + tuple(os.environ.get("LDNI_EXTRA_NVCC_FLAGS", "").split())
     os.makedirs(BUILD, exist_ok=True)
     stamp_file = os.path.join(BUILD, "stamp.txt")
     stamp = _stamp() + "|" + " ".join(extra)

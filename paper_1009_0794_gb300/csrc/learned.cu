@@ -35,6 +35,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxLayerCap = 64;   // largest k_t the layout hands out
+#ifndef LDNI_ONEPASS_BLOCKS
+#define LDNI_ONEPASS_BLOCKS 5
+#endif
+// resident blocks per SM of the one-pass traversal (5 measured fastest of 4, 5, 6 and 8)
+constexpr int kOnepassBlocksPerSm = LDNI_ONEPASS_BLOCKS;
 
 struct LImg {
     int *count[3];
@@ -328,7 +333,7 @@ __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const floa
     });
 }
 
-__global__ void __launch_bounds__(kThreads, 5) onepass_kernel(const float *__restrict__ verts,
+__global__ void __launch_bounds__(kThreads, kOnepassBlocksPerSm) onepass_kernel(const float *__restrict__ verts,
                                                            const int *__restrict__ tris, int nt, int nv, GridDev g,
                                                            int ax_lo, int ax_hi, LImg o, int *big_q, long long qcap,
                                                            int *big_n,
@@ -823,7 +828,7 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
                     reinterpret_cast<unsigned long long *>(w.any_over + 2)));  // 8-byte aligned, cleared
     if (nt > 0) {
         // as many blocks as stay resident (five per SM at the kernel's register bound)
-        const int op_blocks = (int)min((long long)grid_blocks(nt), (long long)num_sms() * 5);
+        const int op_blocks = (int)min((long long)grid_blocks(nt), (long long)num_sms() * kOnepassBlocksPerSm);
         LDNI_LAUNCH(K_ONEPASS, s,
                     onepass_kernel<<<op_blocks, kThreads, 0, s>>>(verts, tris, (int)nt, (int)nv, g, ax_lo, ax_hi,
                                                                         o, w.big_q, w.qcap, w.big_n, info));
