@@ -31,6 +31,37 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(1e-30, np.max(np.abs(b))))
 
 
+# The kernel's per-crossing terms are FP32 with error-free determinants (a few
+# ulp each); a vertex's component adds at most some tens of them with FP32
+# atomics.  64 roundings of 2^-24 of the largest component bound the error
+# against the FP64 oracle at 4e-6 of the gradient's scale.
+TOL_SCALE = 4e-6
+
+
+def _far_from_silhouettes(v, t, a, min_na=0.2):
+    """Vertices whose every incident face has |n_a| >= min_na (its normal far
+    from perpendicular to the rays), where the derivative is well conditioned."""
+    V = v.astype(np.float64)
+    n = np.cross(V[t[:, 1]] - V[t[:, 0]], V[t[:, 2]] - V[t[:, 0]])
+    n /= np.linalg.norm(n, axis=1, keepdims=True)
+    bad = np.abs(n[:, a]) < min_na
+    ok = np.ones(len(v), bool)
+    ok[np.unique(t[bad].reshape(-1))] = False
+    return ok
+
+
+def _check_components(g, ref, ok, rtol):
+    """Per component, relative: every component of a well-conditioned vertex
+    that is at least 1e-3 of the scale."""
+    scale = np.max(np.abs(ref))
+    sel = ok[:, None] & (np.abs(ref) >= 1e-3 * scale)
+    if not sel.any():
+        return 0.0
+    rel = np.abs(g[sel] - ref[sel]) / np.abs(ref[sel])
+    assert rel.max() < rtol, rel.max()
+    return float(rel.max())
+
+
 @pytest.mark.parametrize("res", [128, 77])
 def test_volume_grad_matches_oracle(ldni, res):
     A, B = M.pr1_pair()
@@ -41,7 +72,8 @@ def test_volume_grad_matches_oracle(ldni, res):
             g = ldni.volume_grad(vt, tt, L, 1.0).cpu().numpy()
             fs = AD.frozen_set(L.numpy(), res, a, O3, 1.0)
             ref = AD.volume_grad(v, t, fs, a, 1.0 / res)
-            assert _rel(g, ref) < 2e-4
+            assert _rel(g, ref) < TOL_SCALE
+            _check_components(g, ref, _far_from_silhouettes(v, t, a), 1e-4)
 
 
 def test_depth_vjp_matches_oracle(ldni):
@@ -53,7 +85,7 @@ def test_depth_vjp_matches_oracle(ldni):
         g = ldni.depth_vjp(vt, tt, L, w).cpu().numpy()
         fs = AD.frozen_set(L.numpy(), 100, a, O3, 1.0)
         ref = AD.depth_vjp(v, t, fs, a, w.cpu().numpy().astype(np.float64))
-        assert _rel(g, ref) < 2e-4
+        assert _rel(g, ref) < TOL_SCALE
 
 
 def test_autograd_functions(ldni):
@@ -135,6 +167,6 @@ def test_200k_sphere_against_oracle_and_central_differences(ldni):
                 worst_fd = max(worst_fd, abs(f1 - g[j, c]) / scale)
     print(f"adjoint 200k: oracle max rel {worst_oracle:.2e}; FD max rel {worst_fd:.2e} "
           f"on {converged}/{checked} converged components")
-    assert worst_oracle < 2e-4
+    assert worst_oracle < TOL_SCALE
     assert converged >= 0.9 * checked
     assert worst_fd < 1e-3
