@@ -258,7 +258,7 @@ typedef struct {
                                     launches (1), or chosen by image size (-1) */
 } ldni_tuning_t;
 
-/* Current knobs (defaults: 256, 4096, 16, -1). */
+/* Current knobs (defaults: 512, 4096, 16, -1). */
 int ldni_get_tuning(ldni_tuning_t *tuning_host);
 /* Replace the knobs; LDNI_EINVAL (and no change) when a value is out of range.
  * NULL restores the defaults. */

@@ -126,14 +126,31 @@ __device__ __forceinline__ int ray_kind(long long na, long long nb) {
 // merge_core in closed form for one interval [a0, a1] of A and [b0, b1] of B
 // (same events, same tie rules: at a shared depth A's sample is the one
 // emitted, touching intervals of a union merge, a zero-length interval
-// cancels).  Returns the output count; src[k] names output k's source:
-// 0, 1 = A's first, second sample; 2, 3 = B's.
-__device__ __forceinline__ int two_two(int op, float eps, float a0, float a1, float b0, float b1, int (&src)[4]) {
+// cancels).  Returns the output count; bits 2k, 2k + 1 of *src name output
+// k's source (src_of): 0, 1 = A's first, second sample; 2, 3 = B's.  The
+// sources travel packed in one register, not in an indexed array, which
+// would live in local memory.
+__device__ __forceinline__ int src_of(unsigned src, int k) { return (int)(src >> (2 * k)) & 3; }
+
+// The count pass's word of a kind-4 ray: the count (at most 4) in the low
+// bits, the sources above.  The write pass tells kind 4 from the rows.
+constexpr int kSrcShift = 3;
+__device__ __forceinline__ int word_count(int word, int kind) { return kind == 4 ? word & 7 : word; }
+
+// v[i] of four values a0, a1, b0, b1, without an indexed array
+__device__ __forceinline__ float pick4(int i, float a0, float a1, float b0, float b1) {
+    return i < 2 ? (i ? a1 : a0) : (i == 2 ? b0 : b1);
+}
+__device__ __forceinline__ uint32_t pick4u(int i, uint32_t a0, uint32_t a1, uint32_t b0, uint32_t b1) {
+    return i < 2 ? (i ? a1 : a0) : (i == 2 ? b0 : b1);
+}
+
+__device__ __forceinline__ int two_two(int op, float eps, float a0, float a1, float b0, float b1, unsigned &src) {
     int n = 0;
+    src = 0;
     auto put = [&](int s0, int s1, float d0, float d1) {
         if (!(__fsub_rn(d1, d0) < eps)) {
-            src[n] = s0;
-            src[n + 1] = s1;
+            src |= (unsigned)(s0 | (s1 << 2)) << (2 * n);
             n += 2;
         }
     };
@@ -189,11 +206,12 @@ __device__ __forceinline__ int merge_ray_fast(const float *dA, Idx a, Idx ae, co
         return c;
     }
     if (kind == 4) {
-        int src[4];
+        unsigned src;
         const int c = two_two(op, eps, dA[a], dA[a + 1], dB[b], dB[b + 1], src);
-        for (int k = 0; k < c; k += 2)
-            emit(src[k] >= 2, (src[k] >= 2 ? b : a) + (src[k] & 1), src[k + 1] >= 2,
-                 (src[k + 1] >= 2 ? b : a) + (src[k + 1] & 1), k);
+        for (int k = 0; k < c; k += 2) {
+            const int s0 = src_of(src, k), s1 = src_of(src, k + 1);
+            emit(s0 >= 2, (s0 >= 2 ? b : a) + (s0 & 1), s1 >= 2, (s1 >= 2 ? b : a) + (s1 & 1), k);
+        }
         return c;
     }
     return merge_core<Idx>(dA, a, ae, dB, b, be, op, eps, emit);
@@ -657,12 +675,20 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 // every other ray runs the general merge.
 
 // Pass 1: output count of every ray (kept in the output's offset array,
-// which pass 3 overwrites in place) and of every tile (tile_total, cleared
-// before the launch).
+// which pass 3 overwrites in place; a ray of kind 4 keeps its outputs'
+// sources beside the count, from bit kSrcShift on) and of every tile of the
+// write pass
+// (tile_total, cleared before the launch; wtile rays per tile, tpjw tiles per
+// job).  The count pass has its own rays per thread (kR): a warp's 32 * kR
+// rays lie in one write tile, so each warp adds its sum to that tile's total.
+// tpj: count blocks per job.
+#ifndef LDNI_BOOL_COUNT_BLOCKS
+#define LDNI_BOOL_COUNT_BLOCKS 6
+#endif
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const __grid_constant__ BoolJobs J, int op,
-                                                              float eps, unsigned long long *tile_total, int tpj,
-                                                              float2 *warp_vol) {
+__global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
+    bool_count(long long N, const __grid_constant__ BoolJobs J, int op, float eps, unsigned long long *tile_total,
+               int tpj, int wtile, int tpjw, float2 *warp_vol) {
     constexpr int kRays = kR * kBoolThreads;
     const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
     const Side &A = J.A[job];
@@ -675,8 +701,8 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
     int ra[kR + 1], rb[kR + 1];
     load_rows<kR>(A.off, p0, q0, nr, ra);
     load_rows<kR>(B.off, p0, q0, nr, rb);
-    const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;  // rows beyond capacity: general (clamping) path
-    if (clamp) set_status(info, LDNI_ST_CAPACITY);
+    // a ray whose rows run beyond an operand's capacity takes the general (clamping) path
+    if (ra[kR] > A.cap || rb[kR] > B.cap) set_status(info, LDNI_ST_CAPACITY);
     int kind[kR];
     float d0[kR], d1[kR], e0[kR], e1[kR];
 #pragma unroll
@@ -686,7 +712,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
             atomicAdd(&info->odd_rays, 1u);
             set_status(info, LDNI_ST_ODD);
         }
-        kind[k] = clamp ? 3 : ray_kind(na, nb);
+        kind[k] = ra[k + 1] > A.cap || rb[k + 1] > B.cap ? 3 : ray_kind(na, nb);
         const float *d = kind[k] == 2 ? B.d + rb[k] : A.d + ra[k];
         d0[k] = d1[k] = e0[k] = e1[k] = 0.0f;
         if (kind[k] == 1 || kind[k] == 2 || kind[k] == 4) {
@@ -698,7 +724,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
             e1[k] = B.d[rb[k] + 1];
         }
     }
-    int cnt[kR];
+    int cnt[kR], word[kR];
     int mine = 0;
     // inside lengths of the result (its volume, when asked for): each kept interval [x, y] adds
     // y - x as an exact pair of floats, summed in double-float (FP32 arithmetic: this GPU's FP64
@@ -718,22 +744,26 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
             else
                 cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, NoEmit{});
         } else if (kind[k] == 4) {
-            int src[4];
+            unsigned src;
             cnt[k] = two_two(op, eps, d0[k], d1[k], e0[k], e1[k], src);
-            if (want_vol) {
-                const float dd[4] = {d0[k], d1[k], e0[k], e1[k]};
-                for (int m = 0; m < cnt[k]; m += 2) len = df_add_lazy(len, df_diff(dd[src[m + 1]], dd[src[m]]));
-            }
+            if (want_vol)
+                for (int m = 0; m < cnt[k]; m += 2)
+                    len = df_add_lazy(len, df_diff(pick4(src_of(src, m + 1), d0[k], d1[k], e0[k], e1[k]),
+                                                   pick4(src_of(src, m), d0[k], d1[k], e0[k], e1[k])));
+            word[k] = cnt[k] | (int)(src << kSrcShift);
         } else {
             cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
             if (want_vol && cnt[k]) len = df_add_lazy(len, df_diff(d1[k], d0[k]));
         }
+        if (kind[k] != 4) word[k] = cnt[k];
         mine += cnt[k];
     }
-    store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, cnt);
-#pragma unroll
-    for (int w = 16; w > 0; w >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, w);
-    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(tile_total + blockIdx.x, (unsigned long long)mine);  // job * tpj + tile
+    store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, word);
+    mine = (int)__reduce_add_sync(0xffffffffu, (unsigned)mine);  // at most 2^31 - 1: counts are int rows
+    if ((threadIdx.x & 31) == 0 && mine) {
+        const long long pw = p0 + (long long)(threadIdx.x >> 5) * 32 * kR;  // the warp's first ray
+        atomicAdd(tile_total + (size_t)job * tpjw + pw / wtile, (unsigned long long)mine);
+    }
     if (!want_vol) return;  // block-uniform
 #pragma unroll
     for (int w = 16; w > 0; w >>= 1)  // a fixed tree
@@ -747,7 +777,7 @@ __global__ void __launch_bounds__(kBoolThreads, 8) bool_count(long long N, const
 __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total_all, int ntiles,
                                                         long long *tile_pre_all, long long N,
                                                         const __grid_constant__ BoolJobs J, const float2 *warp_vol,
-                                                        double h2) {
+                                                        int nvol, double h2) {
     constexpr int kPer = 4;
     const int job = blockIdx.x;  // one block per job
     const unsigned long long *tile_total = tile_total_all + (size_t)job * ntiles;
@@ -772,11 +802,10 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
         carry += tot;
     }
     if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
-    if (warp_vol) {  // the volume: the count pass's warp partials of this job in a fixed order
+    if (warp_vol) {  // the volume: the count pass's nvol warp partials of this job in a fixed order
         __shared__ DF shdf[1024 / 32];
-        constexpr int kWarps = kBoolThreads / 32;
-        const float2 *wv = warp_vol + (size_t)job * ntiles * kWarps;
-        const int n = ntiles * kWarps;
+        const float2 *wv = warp_vol + (size_t)job * nvol;
+        const int n = nvol;
         DF acc{0.0f, 0.0f};
         for (int k0 = threadIdx.x; k0 < n; k0 += 1024 * 4) {
             float2 v[4];
@@ -790,18 +819,50 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
     }
 }
 
-// Pass 3: offsets from the counts and the tile's prefix, then the samples of
-// every ray at its offset.  A ray that keeps the pair of one operand (kinds 1
-// and 2, most rays of solids with few layers) is a plain copy: the thread
-// first loads the pairs of all its such rays into registers and only then
-// stores them, so their loads are in flight together instead of one ray's
-// loads waiting behind the previous ray's stores.  The other rays run the
-// general merge afterwards.
+// One sample's fields as loaded (normals as raw words: FP32 or one packed word).
+struct Smp {
+    float d;
+    uint32_t x, y, z, t;
+};
+
+// Sample i of side S into v when `on` (zeros otherwise); y, z only for FP32 normals.
+__device__ __forceinline__ void load_smp(const Side &S, bool on, bool three, long long i, Smp &v) {
+    v.d = on ? S.d[i] : 0.0f;
+    v.x = on ? reinterpret_cast<const uint32_t *>(S.nx)[i] : 0u;
+    v.y = on && three ? reinterpret_cast<const uint32_t *>(S.ny)[i] : 0u;
+    v.z = on && three ? reinterpret_cast<const uint32_t *>(S.nz)[i] : 0u;
+    v.t = on ? reinterpret_cast<const uint32_t *>(S.tri)[i] : 0u;
+}
+
+#ifndef LDNI_BOOL_WRITE_BLOCKS
+#define LDNI_BOOL_WRITE_BLOCKS 6
+#endif
+
+// Pass 3: the block first writes its tile's offsets (kR rays per thread),
+// listing every ray with output samples in shared memory, and then its
+// threads take the listed rays in turn: first the rays of kinds 1, 2 and 4,
+// which copy samples of their one or two pairs (every sample a ray copies is
+// loaded before any of its stores; a kind-4 ray's sources come from pass 1,
+// so samples it drops are not read), then the rays of kind 3 (general
+// merge).  Rays without samples (often half of an image) thus leave no
+// thread idle while the others wait on memory, and a block covers kR times
+// as many rays with the same registers per thread.
+struct CopyItem {
+    long long at;  // first output slot; copies: the outputs' sources and count from bit kItemSrcShift on
+    int ra;        // copies: A's row; merges: the ray
+    int rb;        // copies: B's row
+};
+constexpr int kItemSrcShift = 48;  // output slots stay below 2^48
+
 template <int kR>
-__global__ void __launch_bounds__(kBoolThreads, 6) bool_write(long long N, const __grid_constant__ BoolJobs J, int op,
-                                                              float eps, const long long *tile_pre, int tpj) {
+__global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
+    bool_write(long long N, const __grid_constant__ BoolJobs J, int op, float eps, const long long *tile_pre,
+                    int tpj) {
     constexpr int kRays = kR * kBoolThreads;
+    constexpr int kItemBits = 20;  // items per tile < 2^20 in the low bits of the scanned word
     __shared__ long long sh[kBoolThreads / 32 + 1];
+    __shared__ CopyItem items[kRays];  // copies from the front, merges from the back
+    __shared__ int s_merges;
     const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
     const Side &A = J.A[job];
     const Side &B = J.B[job];
@@ -811,107 +872,94 @@ __global__ void __launch_bounds__(kBoolThreads, 6) bool_write(long long N, const
     const int nr = (int)min((long long)kRays, N - p0);
     const int q0 = threadIdx.x * kR;
     const long long tile_base = tile_pre[blockIdx.x];  // = job * tpj + tile
+    if (threadIdx.x == 0) s_merges = 0;  // ordered before its first use by the block scan's barriers
     int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
     load_rows<kR>(A.off, p0, q0, nr, ra);
     load_rows<kR>(B.off, p0, q0, nr, rb);
     load_rows<kR>(o.off, p0, q0, nr, cnt);  // pass 1's counts (cnt[kR] unused)
-    int mine = 0;
+    int kind[kR];
+    unsigned src[kR];
+    long long mine = 0;
+    int listed = 0;
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         if (q0 + k >= nr) cnt[k] = 0;
+        kind[k] = ra[k + 1] > A.cap || rb[k + 1] > B.cap ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k]);
+        // outputs 0, 1 from samples 0, 1 (A) or 2, 3 (B); a kind-4 ray's from pass 1
+        src[k] = kind[k] == 4 ? (unsigned)cnt[k] >> kSrcShift : (kind[k] == 1 ? 0x4u : 0xEu);
+        cnt[k] = word_count(cnt[k], kind[k]);
+        if (cnt[k] == 0) kind[k] = 0;
         mine += cnt[k];
+        listed += kind[k] == 1 || kind[k] == 2 || kind[k] == 4;
     }
     long long total;
-    const long long base = tile_base + block_exclusive_scan<kBoolThreads>(mine, sh, &total);
+    const long long ex = block_exclusive_scan<kBoolThreads>((mine << kItemBits) | listed, sh, &total);
+    const long long base = tile_base + (ex >> kItemBits);
+    const int nitems = (int)(total & ((1 << kItemBits) - 1));
     {
         int w[kR];
+        int slot = (int)(ex & ((1 << kItemBits) - 1));
         long long run = base;
 #pragma unroll
         for (int k = 0; k < kR; ++k) {
             w[k] = (int)min(run, (long long)INT_MAX);
+            if (kind[k] == 1 || kind[k] == 2 || kind[k] == 4)
+                items[slot++] = CopyItem{run | (long long)(src[k] | ((unsigned)cnt[k] << 8)) << kItemSrcShift, ra[k],
+                                         rb[k]};
+            else if (kind[k] == 3)
+                items[kRays - 1 - atomicAdd(&s_merges, 1)] = CopyItem{run, q0 + k, 0};
             run += cnt[k];
         }
         store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, w);
     }
-    const bool clamp = ra[kR] > A.cap || rb[kR] > B.cap;
+    __syncthreads();
+    const int nmerges = s_merges;
     const bool three = o.ny != nullptr;
-    const bool inv = op == LDNI_OP_DIFF;
-    // the kept pairs of one operand: every load first, then every store
-    int kind[kR];
-    float d0[kR], d1[kR];
-    uint32_t x0[kR], x1[kR], y0[kR], y1[kR], z0[kR], z1[kR];
-    int t0[kR], t1[kR];
+    const uint32_t flip = op != LDNI_OP_DIFF ? 0u : (three ? 0x80000000u : kInvert8);  // an inverted normal
+    for (int i = threadIdx.x; i < nitems; i += kBoolThreads) {
+        const CopyItem it = items[i];
+        const unsigned src = (unsigned)(it.at >> kItemSrcShift) & 0xffu;
+        const int c = (int)(it.at >> (kItemSrcShift + 8));
+        const long long at0 = it.at & ((1ll << kItemSrcShift) - 1);
+        unsigned need = 0;  // bit s: some output copies sample s
 #pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        kind[k] = cnt[k] > 0 ? (clamp ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k])) : 0;
-        const bool pair = kind[k] == 1 || kind[k] == 2;
-        const Side &S = kind[k] == 2 ? B : A;
-        const long long i = kind[k] == 2 ? rb[k] : ra[k];
-        const uint32_t *X = reinterpret_cast<const uint32_t *>(S.nx);
-        const uint32_t *Y = reinterpret_cast<const uint32_t *>(S.ny);
-        const uint32_t *Z = reinterpret_cast<const uint32_t *>(S.nz);
-        d0[k] = pair ? S.d[i] : 0.0f;
-        d1[k] = pair ? S.d[i + 1] : 0.0f;
-        x0[k] = pair ? X[i] : 0u;
-        x1[k] = pair ? X[i + 1] : 0u;
-        y0[k] = pair && three ? Y[i] : 0u;
-        y1[k] = pair && three ? Y[i + 1] : 0u;
-        z0[k] = pair && three ? Z[i] : 0u;
-        z1[k] = pair && three ? Z[i + 1] : 0u;
-        t0[k] = pair ? S.tri[i] : 0;
-        t1[k] = pair ? S.tri[i + 1] : 0;
-    }
-    {
-        const uint32_t flip = !inv ? 0u : (three ? 0x80000000u : kInvert8);  // an inverted normal
-        long long at = base;
+        for (int m = 0; m < 4; ++m)
+            if (m < c) need |= 1u << src_of(src, m);
+        Smp a0, a1, b0, b1;  // every sample the ray copies, loaded before any store
+        load_smp(A, need & 1u, three, it.ra, a0);
+        load_smp(A, need & 2u, three, it.ra + 1, a1);
+        load_smp(B, need & 4u, three, it.rb, b0);
+        load_smp(B, need & 8u, three, it.rb + 1, b1);
 #pragma unroll
-        for (int k = 0; k < kR; ++k) {
-            if (kind[k] == 1 || kind[k] == 2) {
-                const bool fb = kind[k] == 2;
-                const uint32_t f = fb ? flip : 0u;
-                const int tb = fb ? (int)0x80000000u : 0;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const long long a2 = at + h;
-                    if (a2 >= o.cap) {
-                        set_status(info, LDNI_ST_CAPACITY);
-                        continue;
-                    }
-                    o.d[a2] = h ? d1[k] : d0[k];
-                    o.nx[a2] = __uint_as_float((h ? x1[k] : x0[k]) ^ f);
-                    if (three) {
-                        o.ny[a2] = __uint_as_float((h ? y1[k] : y0[k]) ^ f);
-                        o.nz[a2] = __uint_as_float((h ? z1[k] : z0[k]) ^ f);
-                    }
-                    o.tri[a2] = (h ? t1[k] : t0[k]) | tb;
-                }
+        for (int m = 0; m < 4; ++m) {
+            if (m >= c) break;
+            const long long at = at0 + m;
+            if (at >= o.cap) {
+                set_status(info, LDNI_ST_CAPACITY);
+                continue;
             }
-            at += cnt[k];
+            const int sm = src_of(src, m);
+            const uint32_t f = sm >= 2 ? flip : 0u;
+            o.d[at] = pick4(sm, a0.d, a1.d, b0.d, b1.d);
+            o.nx[at] = __uint_as_float(pick4u(sm, a0.x, a1.x, b0.x, b1.x) ^ f);
+            if (three) {
+                o.ny[at] = __uint_as_float(pick4u(sm, a0.y, a1.y, b0.y, b1.y) ^ f);
+                o.nz[at] = __uint_as_float(pick4u(sm, a0.z, a1.z, b0.z, b1.z) ^ f);
+            }
+            o.tri[at] = (int)pick4u(sm, a0.t, a1.t, b0.t | 0x80000000u, b1.t | 0x80000000u);
         }
     }
-    long long at = base;
-#pragma unroll
-    for (int k = 0; k < kR; ++k) {
-        if (kind[k] == 4) {
-            const long long a0 = ra[k], b0 = rb[k];
-            int src[4];
-            const float dd[4] = {A.d[a0], A.d[a0 + 1], B.d[b0], B.d[b0 + 1]};
-            const int c = two_two(op, eps, dd[0], dd[1], dd[2], dd[3], src);
-            for (int m = 0; m < c; ++m) {
-                const bool fb = src[m] >= 2;
-                emit_global(fb, (fb ? b0 : a0) + (src[m] & 1), A, B, op, o, at + m, info);
-            }
-        } else if (kind[k] == 3) {
-            const long long a0 = min((long long)ra[k], A.cap), b0 = min((long long)rb[k], B.cap);
-            const int na = (int)(min((long long)ra[k + 1], A.cap) - a0);
-            const int nb = (int)(min((long long)rb[k + 1], B.cap) - b0);
-            const long long at0 = at;
-            merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
-                emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
-                emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
-            });
-        }
-        at += cnt[k];
+    for (int i = threadIdx.x; i < nmerges; i += kBoolThreads) {
+        const CopyItem it = items[kRays - 1 - i];
+        const long long p = p0 + it.ra;  // the ray (its rows again: cached)
+        const long long a0 = min((long long)A.off[p], A.cap), b0 = min((long long)B.off[p], B.cap);
+        const int na = (int)(min((long long)A.off[p + 1], A.cap) - a0);
+        const int nb = (int)(min((long long)B.off[p + 1], B.cap) - b0);
+        const long long at0 = it.at;
+        merge_core<int>(A.d + a0, 0, na, B.d + b0, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int m) {
+            emit_global(pb, (pb ? b0 : a0) + pi, A, B, op, o, at0 + m, info);
+            emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
+        });
     }
 }
 
@@ -956,6 +1004,11 @@ bool layers_ok(const ldni_layers_t *L, bool need) {
 }
 
 constexpr int kMinTileRays = 256;  // the workspace is sized for the smallest tile
+#ifndef LDNI_BOOL_COUNT_RAYS
+#define LDNI_BOOL_COUNT_RAYS 2
+#endif
+// rays per thread of the count pass (1, 2, 4 or 8), whatever the write pass's tile
+constexpr int kBoolCountRays = LDNI_BOOL_COUNT_RAYS;
 constexpr int kMaxDynSmem = 220 * 1024;  // dynamic shared memory of one Boolean block, at most
 
 size_t bool_ws_words(long long N) { return (size_t)((N + kMinTileRays - 1) / kMinTileRays); }
@@ -976,7 +1029,7 @@ bool bulk_aligned(const BoolJobs &J, int njobs, bool rows) {
 }
 
 template <int kR>
-int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, void *ws, int budget, bool split,
+int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, void *ws, int budget, int form,
                 double h2, cudaStream_t s) {
     constexpr int kRays = kR * kBoolThreads;
     const int tpj = (int)((N + kRays - 1) / kRays);
@@ -985,7 +1038,7 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
     // shared memory a block can have
     const int narr = J.packed ? 3 : 5;
     unsigned long long *words = static_cast<unsigned long long *>(ws);
-    if (!split) {
+    if (form == 0) {
         const int per = 4 * (narr + 1);
         budget = min(budget, (kMaxDynSmem / per) & ~3);
         const bool bulk = bulk_aligned(J, njobs, false);
@@ -1010,10 +1063,14 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
     float2 *warp_vol = J.vol[0] ? reinterpret_cast<float2 *>(tile_pre + nblocks) : nullptr;
     if (int rc_ = cuda_check(cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s)))
         return rc_;
+    constexpr int kRc = kBoolCountRays;
+    const int tpjc = (int)((N + kRc * kBoolThreads - 1) / (kRc * kBoolThreads));  // count blocks per job
     LDNI_LAUNCH(K_BOOL_COUNT, s,
-                bool_count<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpj, warp_vol));
+                bool_count<kRc><<<tpjc * njobs, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpjc, kRays, tpj,
+                                                                      warp_vol));
     LDNI_LAUNCH(K_BOOL_SCAN, s,
-                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol, h2));
+                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol,
+                                                       tpjc * (kBoolThreads / 32), h2));
     LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
     return cuda_status();
 }
@@ -1055,13 +1112,14 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int budget = tune.bool_stage_samples;
     const int rays = tune.bool_tile_rays;
-    const bool split = tune.bool_split < 0 ? N * count / rays > 2 * (long long)num_sms() : tune.bool_split != 0;
+    // small images: one staged launch; large ones: count, tile scan, write
+    const int form = tune.bool_split >= 0 ? tune.bool_split : (N * count / rays > 2 * (long long)num_sms() ? 1 : 0);
     const double h = (double)grid->width / (double)grid->res;
     switch (rays) {
-        case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, split, h * h, s);
-        case 512: return launch_bool<2>(N, J, count, op, eps, ws, budget, split, h * h, s);
-        case 2048: return launch_bool<8>(N, J, count, op, eps, ws, budget, split, h * h, s);
-        default: return launch_bool<4>(N, J, count, op, eps, ws, budget, split, h * h, s);
+        case 256: return launch_bool<1>(N, J, count, op, eps, ws, budget, form, h * h, s);
+        case 512: return launch_bool<2>(N, J, count, op, eps, ws, budget, form, h * h, s);
+        case 2048: return launch_bool<8>(N, J, count, op, eps, ws, budget, form, h * h, s);
+        default: return launch_bool<4>(N, J, count, op, eps, ws, budget, form, h * h, s);
     }
 }
 

@@ -141,7 +141,7 @@ extern "C" int ldni_wait_selftest(ldni_info_t *info, void *stream) {
 // ---- launch tuning -----------------------------------------------------------
 namespace ldni {
 namespace {
-constexpr ldni_tuning_t kDefaultTuning = {256, 4096, 16, -1};
+constexpr ldni_tuning_t kDefaultTuning = {512, 4096, 16, -1};
 std::mutex g_tuning_mu;
 ldni_tuning_t g_tuning = kDefaultTuning;
 

@@ -31,16 +31,16 @@ __device__ __forceinline__ void st_status(unsigned long long *p, unsigned long l
 
 // Called by ALL 32 lanes of one warp (the same warp in every block).
 // Returns, in every lane, the exclusive prefix of chunk `c` given its
-// aggregate (>= 0).  One probe inspects kLookbackWindow predecessors (each
-// lane reads kLookbackPerLane consecutive words with independent loads): it
-// waits until all of them have published something, adds the aggregates down
-// to the nearest inclusive prefix, and moves on by a whole window if none was
-// found.  Blocks of one wave finish their local work at about the same time,
+// aggregate (>= 0).  One probe inspects 32 * P predecessors (each lane reads
+// P consecutive words with independent loads): it waits until all of them
+// have published something, adds the aggregates down to the nearest inclusive
+// prefix, and moves on by a whole window if none was found.  Blocks of one wave finish their local work at about the same time,
 // so a chunk usually walks back through its wave's chunks before any of them
 // holds a prefix; a wide window keeps that walk to a few probes.
+// A smaller P (words per lane) costs more probes and fewer registers.
 constexpr int kLookbackPerLane = 8;
-constexpr int kLookbackWindow = 32 * kLookbackPerLane;
 
+template <int P = kLookbackPerLane>
 __device__ __forceinline__ long long lookback_warp(unsigned long long *status, int c, long long aggregate,
                                                    ldni_info_t *info, int spin_limit) {
     const int lane = threadIdx.x & 31;
@@ -55,17 +55,17 @@ __device__ __forceinline__ long long lookback_warp(unsigned long long *status, i
     bool timed_out = false;
     while (hi >= 0) {
         // lane l holds chunks hi - l*P - j, j = 0 (nearest) .. P-1; before chunk 0: prefix 0
-        unsigned long long w[kLookbackPerLane];
+        unsigned long long w[P];
 #pragma unroll
-        for (int j = 0; j < kLookbackPerLane; ++j) {
-            const int k = hi - lane * kLookbackPerLane - j;
+        for (int j = 0; j < P; ++j) {
+            const int k = hi - lane * P - j;
             w[j] = k >= 0 ? ld_status(status + k) : kFlagPrefix;
         }
         int spins = 0;
         while (true) {
             bool missing = false;
 #pragma unroll
-            for (int j = 0; j < kLookbackPerLane; ++j) missing |= (w[j] & ~kValueMask) == 0;
+            for (int j = 0; j < P; ++j) missing |= (w[j] & ~kValueMask) == 0;
             if (!__any_sync(0xffffffffu, missing)) break;
             if (++spins > spin_limit) {
                 timed_out = true;
@@ -73,22 +73,22 @@ __device__ __forceinline__ long long lookback_warp(unsigned long long *status, i
             }
             __nanosleep(32);
 #pragma unroll
-            for (int j = 0; j < kLookbackPerLane; ++j) {
-                const int k = hi - lane * kLookbackPerLane - j;
+            for (int j = 0; j < P; ++j) {
+                const int k = hi - lane * P - j;
                 if ((w[j] & ~kValueMask) == 0) w[j] = ld_status(status + k);
             }
         }
         if (timed_out) break;
         // nearest inclusive prefix: the first j in the first lane that has one
-        int jp = kLookbackPerLane;
+        int jp = P;
 #pragma unroll
-        for (int j = kLookbackPerLane - 1; j >= 0; --j)
+        for (int j = P - 1; j >= 0; --j)
             if ((w[j] & ~kValueMask) == kFlagPrefix) jp = j;
-        const unsigned prefix_lanes = __ballot_sync(0xffffffffu, jp < kLookbackPerLane);
+        const unsigned prefix_lanes = __ballot_sync(0xffffffffu, jp < P);
         const int stop_lane = prefix_lanes ? __ffs(prefix_lanes) - 1 : 32;
         long long v = 0;
 #pragma unroll
-        for (int j = 0; j < kLookbackPerLane; ++j) {
+        for (int j = 0; j < P; ++j) {
             const bool take = lane < stop_lane || (lane == stop_lane && j <= jp);
             if (take) v += (long long)(w[j] & kValueMask);
         }
@@ -96,7 +96,7 @@ __device__ __forceinline__ long long lookback_warp(unsigned long long *status, i
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         excl += v;
         if (prefix_lanes) break;
-        hi -= kLookbackWindow;
+        hi -= 32 * P;
     }
     if (timed_out && lane == 0 && info) atomicOr(&info->status, LDNI_ST_TIMEOUT);
     if (lane == 0) st_status(status + c, kFlagPrefix | (((unsigned long long)(excl + aggregate)) & kValueMask));

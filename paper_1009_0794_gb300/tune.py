@@ -22,7 +22,7 @@ import torch
 from . import _lib
 from . import ldni as L
 
-DEFAULT = {"bool_tile_rays": 256, "bool_stage_samples": 4096, "tri_blocks_per_sm": 16, "bool_split": -1}
+DEFAULT = {"bool_tile_rays": 512, "bool_stage_samples": 4096, "tri_blocks_per_sm": 16, "bool_split": -1}
 BOOL_CANDIDATES = [(r, s, k) for r in (256, 512, 1024, 2048) for s in (0, 2048, 4096, 8192) for k in (0, 1)]
 TRI_CANDIDATES = [2, 4, 8, 16, 32, 64]
 CACHE_ENV = "LDNI_TUNE_CACHE"

@@ -73,15 +73,15 @@ def test_tuning_knobs_validate_on_host():
     lib = _lib.load()
     t = _lib.Tuning()
     assert lib.ldni_get_tuning(ctypes.byref(t)) == 0
-    assert (t.bool_tile_rays, t.bool_stage_samples, t.tri_blocks_per_sm, t.bool_split) == (256, 4096, 16, -1)
+    assert (t.bool_tile_rays, t.bool_stage_samples, t.tri_blocks_per_sm, t.bool_split) == (512, 4096, 16, -1)
     for bad in (_lib.Tuning(300, 4096, 16, 0), _lib.Tuning(1024, 20000, 16, 0), _lib.Tuning(1024, 4096, 0, 0),
                 _lib.Tuning(1024, 4096, 16, 2)):
         assert lib.ldni_set_tuning(ctypes.byref(bad)) == -1
-    good = _lib.Tuning(512, 0, 4, 1)
+    good = _lib.Tuning(1024, 0, 4, 1)
     assert lib.ldni_set_tuning(ctypes.byref(good)) == 0
-    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and (t.bool_tile_rays, t.tri_blocks_per_sm) == (512, 4)
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and (t.bool_tile_rays, t.tri_blocks_per_sm) == (1024, 4)
     assert lib.ldni_set_tuning(None) == 0
-    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 256
+    assert lib.ldni_get_tuning(ctypes.byref(t)) == 0 and t.bool_tile_rays == 512
 
 
 def test_build_stamp_is_the_same_in_another_checkout(tmp_path):

@@ -320,3 +320,34 @@ def test_hand_worked_cases(ldni):
                 assert bit_equal(got, expected(c, A, B)), c["name"]
         finally:
             tune.set(**prev)
+
+
+@pytest.mark.parametrize("split,tile", [(0, 256), (1, 256), (1, 512), (1, 2048)])
+def test_truncated_operand_reported(ldni, split, tile):
+    """An operand whose offsets run past its capacity (its samples were cut
+    off) is reported, nothing past its capacity is read, and every ray before
+    the first cut-off ray is answered as with the whole operand."""
+    from paper_1009_0794_gb300 import tune
+    A, B = M.pr1_pair()
+    LA, LB = _pairs(ldni, A, B, 77)
+    prev = tune.set(bool_split=split, bool_tile_rays=tile)
+    try:
+        for a in range(3):
+            X = LA[a]
+            cap = X.n // 2
+            T = ldni.LDNI(X.grid, X.axis, X.offsets, X.depth[:cap].clone(), X.nx[:cap].clone(), X.ny[:cap].clone(),
+                          X.nz[:cap].clone(), X.tri[:cap].clone(), X.n)
+            full = ldni.boolean(X, LB[a], "union").numpy()
+            info = ldni.new_info()
+            out = ldni.boolean(T, LB[a], "union", info=info, sync=False)
+            torch.cuda.synchronize()
+            assert ldni.info_decode(info)["status"] & ldni._lib.ST_CAPACITY, a
+            offs = X.offsets.cpu().numpy()
+            first = int(np.argmax(offs[1:] > cap))  # the first ray that runs past the capacity
+            got_off = out.offsets.cpu().numpy()[:first + 1]
+            assert np.array_equal(got_off, full["offsets"][:first + 1]), a
+            m = int(full["offsets"][first])
+            for k in ("depth", "tri"):
+                assert np.array_equal(getattr(out, k)[:m].cpu().numpy(), full[k][:m]), (a, k)
+    finally:
+        tune.set(**prev)
