@@ -132,10 +132,17 @@ __device__ __forceinline__ int ray_kind(long long na, long long nb) {
 // would live in local memory.
 __device__ __forceinline__ int src_of(unsigned src, int k) { return (int)(src >> (2 * k)) & 3; }
 
-// The count pass's word of a kind-4 ray: the count (at most 4) in the low
-// bits, the sources above.  The write pass tells kind 4 from the rows.
+// A ray that takes the general merge: more than one interval in an operand,
+// or rows beyond an operand's capacity (then clamped to it).
+__device__ __forceinline__ bool general_ray(int a, int ae, int b, int be, int capA, int capB) {
+    const int na = ae - a, nb = be - b;
+    return ae > capA || be > capB || !((na == 0 || na == 2) && (nb == 0 || nb == 2));
+}
+
+// The count pass's word of a ray in closed form (not general_ray): the count
+// (at most 4) in the low bits, the outputs' sources from bit kSrcShift on.
+// A general ray's word is its count.
 constexpr int kSrcShift = 3;
-__device__ __forceinline__ int word_count(int word, int kind) { return kind == 4 ? word & 7 : word; }
 
 // v[i] of four values a0, a1, b0, b1, without an indexed array
 __device__ __forceinline__ float pick4(int i, float a0, float a1, float b0, float b1) {
@@ -145,12 +152,27 @@ __device__ __forceinline__ uint32_t pick4u(int i, uint32_t a0, uint32_t a1, uint
     return i < 2 ? (i ? a1 : a0) : (i == 2 ? b0 : b1);
 }
 
-__device__ __forceinline__ int two_two(int op, float eps, float a0, float a1, float b0, float b1, unsigned &src) {
+// The ends of the kept intervals, in order (x0, y0), (x1, y1), come back in *ends.
+struct Ends {
+    float x0, y0, x1, y1;
+};
+
+__device__ __forceinline__ int two_two(int op, float eps, float a0, float a1, float b0, float b1, unsigned &src,
+                                       Ends *ends = nullptr) {
     int n = 0;
     src = 0;
     auto put = [&](int s0, int s1, float d0, float d1) {
         if (!(__fsub_rn(d1, d0) < eps)) {
             src |= (unsigned)(s0 | (s1 << 2)) << (2 * n);
+            if (ends) {
+                if (n == 0) {
+                    ends->x0 = d0;
+                    ends->y0 = d1;
+                } else {
+                    ends->x1 = d0;
+                    ends->y1 = d1;
+                }
+            }
             n += 2;
         }
     };
@@ -678,33 +700,38 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 // which pass 3 overwrites in place; a ray of kind 4 keeps its outputs'
 // sources beside the count, from bit kSrcShift on) and of every tile of the
 // write pass
-// (tile_total, cleared before the launch; wtile rays per tile, tpjw tiles per
-// job).  The count pass has its own rays per thread (kR): a warp's 32 * kR
+// (tile_total, cleared before the launch; 2^wshift rays per tile, tpjw tiles
+// per job).  The count pass has its own rays per thread (kR): a warp's 32 * kR
 // rays lie in one write tile, so each warp adds its sum to that tile's total.
 // tpj: count blocks per job.
 #ifndef LDNI_BOOL_COUNT_BLOCKS
 #define LDNI_BOOL_COUNT_BLOCKS 6
 #endif
-template <int kR>
+template <int kR, int kOp>
 __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
-    bool_count(long long N, const __grid_constant__ BoolJobs J, int op, float eps, unsigned long long *tile_total,
-               int tpj, int wtile, int tpjw, float2 *warp_vol) {
+    bool_count(int N, const __grid_constant__ BoolJobs J, float eps, unsigned long long *tile_total, int tpj,
+               int wshift, int tpjw, float2 *vol_part) {
+    // Index arithmetic is 32-bit: rays (at most 8192^2) and rows (int) fit.
     constexpr int kRays = kR * kBoolThreads;
-    const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
+    const int job = blockIdx.y, tile = blockIdx.x;  // the grid is tpj x jobs
     const Side &A = J.A[job];
     const Side &B = J.B[job];
     const Out &o = J.o[job];
     ldni_info_t *info = J.info[job];
-    const long long p0 = (long long)tile * kRays;
-    const int nr = (int)min((long long)kRays, N - p0);
+    const int p0 = tile * kRays;
+    const int nr = min(kRays, N - p0);
     const int q0 = threadIdx.x * kR;
+    const int capA = (int)min(A.cap, (long long)INT_MAX), capB = (int)min(B.cap, (long long)INT_MAX);
     int ra[kR + 1], rb[kR + 1];
-    load_rows<kR>(A.off, p0, q0, nr, ra);
-    load_rows<kR>(B.off, p0, q0, nr, rb);
+    load_rows<kR>(A.off + p0, 0, q0, nr, ra);
+    load_rows<kR>(B.off + p0, 0, q0, nr, rb);
     // a ray whose rows run beyond an operand's capacity takes the general (clamping) path
-    if (ra[kR] > A.cap || rb[kR] > B.cap) set_status(info, LDNI_ST_CAPACITY);
-    int kind[kR];
-    float d0[kR], d1[kR], e0[kR], e1[kR];
+    if (ra[kR] > capA || rb[kR] > capB) set_status(info, LDNI_ST_CAPACITY);
+    // Every ray with at most one interval per operand (kinds 0, 1, 2 and 4) takes
+    // the closed form, an absent operand as the empty interval (0, 0): the
+    // lanes of a warp run the same instructions whatever their rays' kinds.
+    bool gen[kR];
+    float a0[kR], a1[kR], b0[kR], b1[kR];
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         const int na = ra[k + 1] - ra[k], nb = rb[k + 1] - rb[k];
@@ -712,77 +739,80 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
             atomicAdd(&info->odd_rays, 1u);
             set_status(info, LDNI_ST_ODD);
         }
-        kind[k] = ra[k + 1] > A.cap || rb[k + 1] > B.cap ? 3 : ray_kind(na, nb);
-        const float *d = kind[k] == 2 ? B.d + rb[k] : A.d + ra[k];
-        d0[k] = d1[k] = e0[k] = e1[k] = 0.0f;
-        if (kind[k] == 1 || kind[k] == 2 || kind[k] == 4) {
-            d0[k] = d[0];
-            d1[k] = d[1];
-        }
-        if (kind[k] == 4) {
-            e0[k] = B.d[rb[k]];
-            e1[k] = B.d[rb[k] + 1];
-        }
+        gen[k] = general_ray(ra[k], ra[k + 1], rb[k], rb[k + 1], capA, capB);
+        const bool pa = !gen[k] && na == 2, pb = !gen[k] && nb == 2;
+        a0[k] = pa ? A.d[ra[k]] : 0.0f;
+        a1[k] = pa ? A.d[ra[k] + 1] : 0.0f;
+        b0[k] = pb ? B.d[rb[k]] : 0.0f;
+        b1[k] = pb ? B.d[rb[k] + 1] : 0.0f;
     }
     int cnt[kR], word[kR];
     int mine = 0;
     // inside lengths of the result (its volume, when asked for): each kept interval [x, y] adds
     // y - x as an exact pair of floats, summed in double-float (FP32 arithmetic: this GPU's FP64
     // rate would double the pass)
-    const bool want_vol = warp_vol != nullptr;
+    const bool want_vol = vol_part != nullptr;
     DF len{0.0f, 0.0f};
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
-        if (kind[k] == 3) {
+        if (gen[k]) {
             const long long a = min((long long)ra[k], A.cap), b = min((long long)rb[k], B.cap);
             const int na = (int)(min((long long)ra[k + 1], A.cap) - a), nb = (int)(min((long long)rb[k + 1], B.cap) - b);
             const float *dA = A.d + a, *dB = B.d + b;
             if (want_vol)
-                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, [&](bool pb, int pi, bool cb, int ci, int) {
+                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, kOp, eps, [&](bool pb, int pi, bool cb, int ci, int) {
                     len = df_add_lazy(len, df_diff((cb ? dB : dA)[ci], (pb ? dB : dA)[pi]));
                 });
             else
-                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, op, eps, NoEmit{});
-        } else if (kind[k] == 4) {
-            unsigned src;
-            cnt[k] = two_two(op, eps, d0[k], d1[k], e0[k], e1[k], src);
-            if (want_vol)
-                for (int m = 0; m < cnt[k]; m += 2)
-                    len = df_add_lazy(len, df_diff(pick4(src_of(src, m + 1), d0[k], d1[k], e0[k], e1[k]),
-                                                   pick4(src_of(src, m), d0[k], d1[k], e0[k], e1[k])));
-            word[k] = cnt[k] | (int)(src << kSrcShift);
+                cnt[k] = merge_core<int>(dA, 0, na, dB, 0, nb, kOp, eps, NoEmit{});
+            word[k] = cnt[k];
         } else {
-            cnt[k] = kind[k] == 0 ? 0 : two_count(kind[k], op, d0[k], d1[k], eps);
-            if (want_vol && cnt[k]) len = df_add_lazy(len, df_diff(d1[k], d0[k]));
+            unsigned src;
+            Ends e{0.0f, 0.0f, 0.0f, 0.0f};
+            cnt[k] = two_two(kOp, eps, a0[k], a1[k], b0[k], b1[k], src, &e);
+            if (want_vol) {
+                if (cnt[k] >= 2) len = df_add_lazy(len, df_diff(e.y0, e.x0));
+                if (cnt[k] == 4) len = df_add_lazy(len, df_diff(e.y1, e.x1));
+            }
+            word[k] = cnt[k] | (int)(src << kSrcShift);
         }
-        if (kind[k] != 4) word[k] = cnt[k];
         mine += cnt[k];
     }
-    store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, word);
+    store_rows<kR>(const_cast<int *>(o.off) + p0, 0, q0, nr, word);
     mine = (int)__reduce_add_sync(0xffffffffu, (unsigned)mine);  // at most 2^31 - 1: counts are int rows
     if ((threadIdx.x & 31) == 0 && mine) {
-        const long long pw = p0 + (long long)(threadIdx.x >> 5) * 32 * kR;  // the warp's first ray
-        atomicAdd(tile_total + (size_t)job * tpjw + pw / wtile, (unsigned long long)mine);
+        const int pw = p0 + (threadIdx.x >> 5) * 32 * kR;  // the warp's first ray
+        atomicAdd(tile_total + (size_t)job * tpjw + (pw >> wshift), (unsigned long long)mine);
     }
     if (!want_vol) return;  // block-uniform
 #pragma unroll
-    for (int w = 16; w > 0; w >>= 1)  // a fixed tree
+    for (int w = 16; w > 0; w >>= 1)  // a fixed tree; one partial per warp (no barrier)
         len = df_add_lazy(len, DF{__shfl_down_sync(0xffffffffu, len.hi, w), __shfl_down_sync(0xffffffffu, len.lo, w)});
     if ((threadIdx.x & 31) == 0)
-        warp_vol[(size_t)blockIdx.x * (kBoolThreads / 32) + (threadIdx.x >> 5)] = make_float2(len.hi, len.lo);
+        vol_part[((size_t)job * tpj + tile) * (kBoolThreads / 32) + (threadIdx.x >> 5)] = make_float2(len.hi, len.lo);
 }
 
 // Pass 2: exclusive prefix of the tile totals (one block of 1024 threads,
 // kPer consecutive totals per thread and round).
 __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total_all, int ntiles,
                                                         long long *tile_pre_all, long long N,
-                                                        const __grid_constant__ BoolJobs J, const float2 *warp_vol,
+                                                        const __grid_constant__ BoolJobs J, const float2 *vol_part,
                                                         int nvol, double h2) {
     constexpr int kPer = 4;
     const int job = blockIdx.x;  // one block per job
     const unsigned long long *tile_total = tile_total_all + (size_t)job * ntiles;
     long long *tile_pre = tile_pre_all + (size_t)job * ntiles;
     __shared__ long long sh[1024 / 32 + 1];
+    // the first round of the volume partials is loaded first, so that it is
+    // in flight during the scan
+    constexpr int kVol = 8;
+    const float2 *wv = vol_part ? vol_part + (size_t)job * nvol : nullptr;
+    float2 vp[kVol];
+#pragma unroll
+    for (int u = 0; u < kVol; ++u) {
+        const int k = threadIdx.x + u * 1024;
+        vp[u] = wv && k < nvol ? __ldcg(wv + k) : make_float2(0.0f, 0.0f);
+    }
     long long carry = 0;
     for (int b0 = 0; b0 < ntiles; b0 += 1024 * kPer) {
         const int k0 = b0 + threadIdx.x * kPer;
@@ -802,17 +832,17 @@ __global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long
         carry += tot;
     }
     if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
-    if (warp_vol) {  // the volume: the count pass's nvol warp partials of this job in a fixed order
+    if (vol_part) {  // the volume: the count pass's nvol warp partials of this job in a fixed order
         __shared__ DF shdf[1024 / 32];
-        const float2 *wv = warp_vol + (size_t)job * nvol;
-        const int n = nvol;
         DF acc{0.0f, 0.0f};
-        for (int k0 = threadIdx.x; k0 < n; k0 += 1024 * 4) {
-            float2 v[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v[u] = k0 + u * 1024 < n ? __ldcg(wv + k0 + u * 1024) : make_float2(0.0f, 0.0f);
+        for (int u = 0; u < kVol; ++u) acc = df_add_lazy(acc, DF{vp[u].x, vp[u].y});
+        for (int k0 = threadIdx.x + 1024 * kVol; k0 < nvol; k0 += 1024 * kVol) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc = df_add_lazy(acc, DF{v[u].x, v[u].y});
+            for (int u = 0; u < kVol; ++u)
+                vp[u] = k0 + u * 1024 < nvol ? __ldcg(wv + k0 + u * 1024) : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < kVol; ++u) acc = df_add_lazy(acc, DF{vp[u].x, vp[u].y});
         }
         const DF t = df_block_sum<1024>(acc, shdf);
         if (threadIdx.x == 0) *J.vol[job] = ((double)t.hi + (double)t.lo) * h2;
@@ -854,43 +884,42 @@ struct CopyItem {
 };
 constexpr int kItemSrcShift = 48;  // output slots stay below 2^48
 
-template <int kR>
+template <int kR, int kOp>
 __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
-    bool_write(long long N, const __grid_constant__ BoolJobs J, int op, float eps, const long long *tile_pre,
-                    int tpj) {
+    bool_write(int N, const __grid_constant__ BoolJobs J, float eps, const long long *tile_pre, int tpj) {
+    constexpr int op = kOp;
     constexpr int kRays = kR * kBoolThreads;
     constexpr int kItemBits = 20;  // items per tile < 2^20 in the low bits of the scanned word
     __shared__ long long sh[kBoolThreads / 32 + 1];
     __shared__ CopyItem items[kRays];  // copies from the front, merges from the back
     __shared__ int s_merges;
-    const int job = blockIdx.x / tpj, tile = blockIdx.x - job * tpj;
+    const int job = blockIdx.y, tile = blockIdx.x;  // the grid is tpj x jobs
     const Side &A = J.A[job];
     const Side &B = J.B[job];
     const Out &o = J.o[job];
     ldni_info_t *info = J.info[job];
-    const long long p0 = (long long)tile * kRays;
-    const int nr = (int)min((long long)kRays, N - p0);
+    const int p0 = tile * kRays;  // 32-bit index arithmetic, as in pass 1
+    const int nr = min(kRays, N - p0);
     const int q0 = threadIdx.x * kR;
-    const long long tile_base = tile_pre[blockIdx.x];  // = job * tpj + tile
+    const long long tile_base = tile_pre[(size_t)job * tpj + tile];
+    const int capA = (int)min(A.cap, (long long)INT_MAX), capB = (int)min(B.cap, (long long)INT_MAX);
     if (threadIdx.x == 0) s_merges = 0;  // ordered before its first use by the block scan's barriers
     int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
-    load_rows<kR>(A.off, p0, q0, nr, ra);
-    load_rows<kR>(B.off, p0, q0, nr, rb);
-    load_rows<kR>(o.off, p0, q0, nr, cnt);  // pass 1's counts (cnt[kR] unused)
-    int kind[kR];
+    load_rows<kR>(A.off + p0, 0, q0, nr, ra);
+    load_rows<kR>(B.off + p0, 0, q0, nr, rb);
+    load_rows<kR>(o.off + p0, 0, q0, nr, cnt);  // pass 1's words (cnt[kR] unused)
+    bool gen[kR];
     unsigned src[kR];
     long long mine = 0;
     int listed = 0;
 #pragma unroll
     for (int k = 0; k < kR; ++k) {
         if (q0 + k >= nr) cnt[k] = 0;
-        kind[k] = ra[k + 1] > A.cap || rb[k + 1] > B.cap ? 3 : ray_kind(ra[k + 1] - ra[k], rb[k + 1] - rb[k]);
-        // outputs 0, 1 from samples 0, 1 (A) or 2, 3 (B); a kind-4 ray's from pass 1
-        src[k] = kind[k] == 4 ? (unsigned)cnt[k] >> kSrcShift : (kind[k] == 1 ? 0x4u : 0xEu);
-        cnt[k] = word_count(cnt[k], kind[k]);
-        if (cnt[k] == 0) kind[k] = 0;
+        gen[k] = general_ray(ra[k], ra[k + 1], rb[k], rb[k + 1], capA, capB);
+        src[k] = gen[k] ? 0u : (unsigned)cnt[k] >> kSrcShift;
+        cnt[k] = gen[k] ? cnt[k] : cnt[k] & 7;
         mine += cnt[k];
-        listed += kind[k] == 1 || kind[k] == 2 || kind[k] == 4;
+        listed += !gen[k] && cnt[k] > 0;
     }
     long long total;
     const long long ex = block_exclusive_scan<kBoolThreads>((mine << kItemBits) | listed, sh, &total);
@@ -903,14 +932,14 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
 #pragma unroll
         for (int k = 0; k < kR; ++k) {
             w[k] = (int)min(run, (long long)INT_MAX);
-            if (kind[k] == 1 || kind[k] == 2 || kind[k] == 4)
+            if (cnt[k] > 0 && !gen[k])
                 items[slot++] = CopyItem{run | (long long)(src[k] | ((unsigned)cnt[k] << 8)) << kItemSrcShift, ra[k],
                                          rb[k]};
-            else if (kind[k] == 3)
+            else if (cnt[k] > 0)
                 items[kRays - 1 - atomicAdd(&s_merges, 1)] = CopyItem{run, q0 + k, 0};
             run += cnt[k];
         }
-        store_rows<kR>(const_cast<int *>(o.off), p0, q0, nr, w);
+        store_rows<kR>(const_cast<int *>(o.off) + p0, 0, q0, nr, w);
     }
     __syncthreads();
     const int nmerges = s_merges;
@@ -951,7 +980,7 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
     }
     for (int i = threadIdx.x; i < nmerges; i += kBoolThreads) {
         const CopyItem it = items[kRays - 1 - i];
-        const long long p = p0 + it.ra;  // the ray (its rows again: cached)
+        const int p = p0 + it.ra;  // the ray (its rows again: cached)
         const long long a0 = min((long long)A.off[p], A.cap), b0 = min((long long)B.off[p], B.cap);
         const int na = (int)(min((long long)A.off[p + 1], A.cap) - a0);
         const int nb = (int)(min((long long)B.off[p + 1], B.cap) - b0);
@@ -1057,21 +1086,27 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
                                                                        tile_vol, h2, wait_limit()));
         return cuda_status();
     }
-    // workspace: tile totals (cleared) | tile prefixes | warp volumes (kBoolThreads / 32 per tile)
+    // workspace: tile totals (cleared) | tile prefixes | volume partials (one per count warp)
     unsigned long long *tile_total = words;
     long long *tile_pre = reinterpret_cast<long long *>(tile_total + nblocks);
-    float2 *warp_vol = J.vol[0] ? reinterpret_cast<float2 *>(tile_pre + nblocks) : nullptr;
+    float2 *vol_part = J.vol[0] ? reinterpret_cast<float2 *>(tile_pre + nblocks) : nullptr;
     if (int rc_ = cuda_check(cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s)))
         return rc_;
     constexpr int kRc = kBoolCountRays;
     const int tpjc = (int)((N + kRc * kBoolThreads - 1) / (kRc * kBoolThreads));  // count blocks per job
+    auto count = op == LDNI_OP_UNION   ? bool_count<kRc, LDNI_OP_UNION>
+                 : op == LDNI_OP_INTER ? bool_count<kRc, LDNI_OP_INTER>
+                                       : bool_count<kRc, LDNI_OP_DIFF>;
+    auto write = op == LDNI_OP_UNION   ? bool_write<kR, LDNI_OP_UNION>
+                 : op == LDNI_OP_INTER ? bool_write<kR, LDNI_OP_INTER>
+                                       : bool_write<kR, LDNI_OP_DIFF>;
     LDNI_LAUNCH(K_BOOL_COUNT, s,
-                bool_count<kRc><<<tpjc * njobs, kBoolThreads, 0, s>>>(N, J, op, eps, tile_total, tpjc, kRays, tpj,
-                                                                      warp_vol));
+                count<<<dim3(tpjc, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_total, tpjc, __builtin_ctz(kRays),
+                                                                 tpj, vol_part));
     LDNI_LAUNCH(K_BOOL_SCAN, s,
-                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, warp_vol,
+                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, vol_part,
                                                        tpjc * (kBoolThreads / 32), h2));
-    LDNI_LAUNCH(K_BOOL_WRITE, s, bool_write<kR><<<nblocks, kBoolThreads, 0, s>>>(N, J, op, eps, tile_pre, tpj));
+    LDNI_LAUNCH(K_BOOL_WRITE, s, write<<<dim3(tpj, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_pre, tpj));
     return cuda_status();
 }
 
