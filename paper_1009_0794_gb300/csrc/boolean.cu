@@ -903,6 +903,7 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
     const int q0 = threadIdx.x * kR;
     const long long tile_base = tile_pre[(size_t)job * tpj + tile];
     const int capA = (int)min(A.cap, (long long)INT_MAX), capB = (int)min(B.cap, (long long)INT_MAX);
+    const bool three = !J.packed;
     if (threadIdx.x == 0) s_merges = 0;  // ordered before its first use by the block scan's barriers
     int ra[kR + 1], rb[kR + 1], cnt[kR + 1];
     load_rows<kR>(A.off + p0, 0, q0, nr, ra);
@@ -943,13 +944,36 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
     }
     __syncthreads();
     const int nmerges = s_merges;
-    const bool three = o.ny != nullptr;
     const uint32_t flip = op != LDNI_OP_DIFF ? 0u : (three ? 0x80000000u : kInvert8);  // an inverted normal
     for (int i = threadIdx.x; i < nitems; i += kBoolThreads) {
         const CopyItem it = items[i];
         const unsigned src = (unsigned)(it.at >> kItemSrcShift) & 0xffu;
         const int c = (int)(it.at >> (kItemSrcShift + 8));
         const long long at0 = it.at & ((1ll << kItemSrcShift) - 1);
+        if (c == 2 && (src == 0x4u || src == 0xEu) && at0 + 1 < o.cap) {
+            // one operand's pair, in order (most rays): a plain copy
+            const bool fb = src == 0xEu;
+            const Side &S = fb ? B : A;
+            const int i0 = fb ? it.rb : it.ra;
+            Smp v0, v1;
+            load_smp(S, true, three, i0, v0);
+            load_smp(S, true, three, i0 + 1, v1);
+            const uint32_t f = fb ? flip : 0u;
+            const uint32_t tb = fb ? 0x80000000u : 0u;
+            o.d[at0] = v0.d;
+            o.d[at0 + 1] = v1.d;
+            o.nx[at0] = __uint_as_float(v0.x ^ f);
+            o.nx[at0 + 1] = __uint_as_float(v1.x ^ f);
+            if (three) {
+                o.ny[at0] = __uint_as_float(v0.y ^ f);
+                o.ny[at0 + 1] = __uint_as_float(v1.y ^ f);
+                o.nz[at0] = __uint_as_float(v0.z ^ f);
+                o.nz[at0 + 1] = __uint_as_float(v1.z ^ f);
+            }
+            o.tri[at0] = (int)(v0.t | tb);
+            o.tri[at0 + 1] = (int)(v1.t | tb);
+            continue;
+        }
         unsigned need = 0;  // bit s: some output copies sample s
 #pragma unroll
         for (int m = 0; m < 4; ++m)
