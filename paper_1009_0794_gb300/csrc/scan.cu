@@ -50,6 +50,9 @@ __device__ __forceinline__ int clamp_int(long long x) { return (int)(x < INT_MAX
 // Pass 1 sums every chunk; pass 2 gives every chunk the sum of the sums before
 // it by reading them directly, so no block ever waits for another.
 constexpr int kMaxSumChunks = 1024;
+#ifndef LDNI_SCAN_ONE_LAUNCH
+#define LDNI_SCAN_ONE_LAUNCH 0
+#endif
 
 __device__ __forceinline__ void load_chunk(const int *cnt, long long base, long long N, int4 (&v)[kSlices],
                                            long long (&tsum)[kSlices]) {
@@ -82,44 +85,74 @@ __device__ __forceinline__ void verify_chunk(const AxisPtrs &ap, int a, int c, l
     }
 }
 
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ long long warp_sum(long long x) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ long long warp_inclusive(long long x, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    return x;
+}
+
 // ---- one-launch form: decoupled look-back ---------------------------------------
 
-__global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long N, int nchunk,
-                                                          unsigned long long *words, ldni_info_t *info,
-                                                          int info_base, int spin_limit) {
-    __shared__ long long sh[kThreads / 32 + 1];
+__global__ void __launch_bounds__(kThreads, 6) scan_lookback(AxisPtrs ap, long long N, int nchunk,
+                                                             unsigned long long *words, ldni_info_t *info,
+                                                             int info_base, int spin_limit) {
+    __shared__ long long sh[kSlices][kThreads / 32];  // per slice: warp totals
+    __shared__ int4 sv[kSlices][kThreads];            // the chunk's counts, until the offsets are written
     __shared__ int s_chunk;
     __shared__ long long s_base;
     const int a = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned long long *status = words + (long long)a * (nchunk + 1);
     unsigned long long *ticket = status + nchunk;
     if (threadIdx.x == 0) s_chunk = (int)atomicAdd(ticket, 1ull);
     __syncthreads();
     const int c = s_chunk;
-    const int *cnt = ap.counts[a];
     int *out = ap.offsets[a];
     const long long base = (long long)c * kChunk;
-
-    // e is a multiple of 4, so 16-byte access is legal iff the base is aligned
-    const bool vec_in = ((reinterpret_cast<uintptr_t>(cnt) & 15) == 0);
-    int4 v[kSlices];
-    long long tsum[kSlices];
+    // as in scan_prefix: counts in shared memory, one 64-bit value per slice in registers, one
+    // barrier for the chunk's scan
+    long long xin[kSlices];
+    {
+        int4 v[kSlices];
+        long long tsum[kSlices];
+        load_chunk(ap.counts[a], base, N, v, tsum);
+        verify_chunk(ap, a, c, base, N, v);
 #pragma unroll
-    for (int m = 0; m < kSlices; ++m) {
-        v[m] = load4(cnt, base + (long long)m * kSlice + threadIdx.x * kVec, N, vec_in);
-        tsum[m] = (long long)v[m].x + v[m].y + v[m].z + v[m].w;
+        for (int m = 0; m < kSlices; ++m) {
+            sv[m][threadIdx.x] = v[m];
+            const long long incl = warp_inclusive(tsum[m], lane);
+            if (lane == 31) sh[m][warp] = incl;
+            xin[m] = incl - tsum[m];
+        }
     }
-    verify_chunk(ap, a, c, base, N, v);
+    __syncthreads();
     long long excl[kSlices];
-    long long carry = 0;
+    long long carry = 0;  // rays of the slices before m; at the end, the chunk's total
 #pragma unroll
     for (int m = 0; m < kSlices; ++m) {
-        long long tot;
-        excl[m] = carry + block_exclusive_scan<kThreads>(tsum[m], sh, &tot);
+        long long lead = 0, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) {
+            const long long t = sh[m][w];
+            tot += t;
+            if (w < warp) lead += t;
+        }
+        excl[m] = carry + lead + xin[m];
         carry += tot;
     }
     if (threadIdx.x < 32) {
-        const long long b = lookback_warp(status, c, carry, info, spin_limit);
+        const long long b = lookback_warp<4>(status, c, carry, info, spin_limit);
         if (threadIdx.x == 0) s_base = b;
     }
     __syncthreads();
@@ -130,8 +163,9 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
     for (int m = 0; m < kSlices; ++m) {
         const long long e = base + (long long)m * kSlice + threadIdx.x * kVec;
         const long long o0 = b0 + excl[m];
-        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v[m].x), clamp_int(o0 + v[m].x + v[m].y),
-                                 clamp_int(o0 + v[m].x + v[m].y + v[m].z));
+        const int4 v = sv[m][threadIdx.x];  // this thread's own counts
+        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v.x), clamp_int(o0 + v.x + v.y),
+                                 clamp_int(o0 + v.x + v.y + v.z));
         if (vec_ok && e + 3 < N) {
             *reinterpret_cast<int4 *>(out + e) = w;
         } else {
@@ -155,23 +189,6 @@ __global__ void __launch_bounds__(kThreads) scan_lookback(AxisPtrs ap, long long
 // leave one value per warp (and per slice) in shared memory, which every
 // thread then adds up itself.
 
-constexpr int kWarps = kThreads / 32;
-
-__device__ __forceinline__ long long warp_sum(long long x) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
-}
-
-__device__ __forceinline__ long long warp_inclusive(long long x, int lane) {
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const long long y = __shfl_up_sync(0xffffffffu, x, o);
-        if (lane >= o) x += y;
-    }
-    return x;
-}
-
 __global__ void __launch_bounds__(kThreads) scan_sums(AxisPtrs ap, long long N, int nchunk, long long *sums) {
     __shared__ long long sh[kWarps];
     const int a = blockIdx.y, c = blockIdx.x;
@@ -191,25 +208,32 @@ __global__ void __launch_bounds__(kThreads) scan_sums(AxisPtrs ap, long long N, 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) scan_prefix(AxisPtrs ap, long long N, int nchunk, const long long *sums,
+__global__ void __launch_bounds__(kThreads, 6) scan_prefix(AxisPtrs ap, long long N, int nchunk, const long long *sums,
                                                         ldni_info_t *info, int info_base) {
     __shared__ long long sh[kSlices + 1][kWarps];  // per slice: warp totals; last row: warp sums of `before`
+    __shared__ int4 sv[kSlices][kThreads];          // the chunk's counts, until the offsets are written
     const int a = blockIdx.y, c = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const long long base = (long long)c * kChunk;
-    int4 v[kSlices];
-    long long tsum[kSlices];
-    load_chunk(ap.counts[a], base, N, v, tsum);
+    // Registers: the counts wait in shared memory and each slice keeps one 64-bit value (the
+    // thread's exclusive prefix within its warp), so six blocks fit per SM and the chunks of
+    // three 1024^2 images run in one wave.
+    long long xin[kSlices];
+    {
+        int4 v[kSlices];
+        long long tsum[kSlices];
+        load_chunk(ap.counts[a], base, N, v, tsum);
+#pragma unroll
+        for (int m = 0; m < kSlices; ++m) {
+            sv[m][threadIdx.x] = v[m];
+            const long long incl = warp_inclusive(tsum[m], lane);
+            if (lane == 31) sh[m][warp] = incl;
+            xin[m] = incl - tsum[m];
+        }
+    }
     long long before = 0;  // this thread's share of the chunk sums before c
     for (int k = threadIdx.x; k < c; k += kThreads) before += sums[(size_t)a * nchunk + k];
-    long long incl[kSlices];
-#pragma unroll
-    for (int m = 0; m < kSlices; ++m) incl[m] = warp_inclusive(tsum[m], lane);
     before = warp_sum(before);
-    if (lane == 31) {
-#pragma unroll
-        for (int m = 0; m < kSlices; ++m) sh[m][warp] = incl[m];
-    }
     if (lane == 0) sh[kSlices][warp] = before;
     __syncthreads();
     long long b0 = 0;  // offset of the chunk's first ray
@@ -226,7 +250,7 @@ __global__ void __launch_bounds__(kThreads) scan_prefix(AxisPtrs ap, long long N
             tot += t;
             if (w < warp) lead += t;
         }
-        excl[m] = carry + lead + incl[m] - tsum[m];
+        excl[m] = carry + lead + xin[m];
         carry += tot;
     }
     int *out = ap.offsets[a];
@@ -236,8 +260,9 @@ __global__ void __launch_bounds__(kThreads) scan_prefix(AxisPtrs ap, long long N
     for (int m = 0; m < kSlices; ++m) {
         const long long e = base + (long long)m * kSlice + threadIdx.x * kVec;
         const long long o0 = b0 + excl[m];
-        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v[m].x), clamp_int(o0 + v[m].x + v[m].y),
-                                 clamp_int(o0 + v[m].x + v[m].y + v[m].z));
+        const int4 v = sv[m][threadIdx.x];  // this thread's own counts: no barrier needed
+        const int4 w = make_int4(clamp_int(o0), clamp_int(o0 + v.x), clamp_int(o0 + v.x + v.y),
+                                 clamp_int(o0 + v.x + v.y + v.z));
         if (vec_ok && e + 3 < N) {
             *reinterpret_cast<int4 *>(out + e) = w;
         } else {
@@ -285,7 +310,7 @@ int csr_scan(const int *const *counts, int *const *offsets, int naxes, long long
         LDNI_LAUNCH(K_SCAN_TOP, s, scan_empty<<<naxes, 1, 0, s>>>(ap, info, info_base));
         return cuda_status();
     }
-    if (nchunk <= kMaxSumChunks) {
+    if (!LDNI_SCAN_ONE_LAUNCH && nchunk <= kMaxSumChunks) {
         LDNI_LAUNCH(K_SCAN_TOP, s, scan_sums<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials));
         LDNI_LAUNCH(K_SCAN_DOWN, s,
                     scan_prefix<<<dim3(nchunk, naxes), kThreads, 0, s>>>(ap, N, nchunk, partials, info, info_base));
