@@ -59,6 +59,8 @@ extern "C" {
 #define LDNI_ST_RANGE 16u         /* a vertex could not be snapped (outside +-2^24 units) */
 #define LDNI_ST_INDEX 32u         /* a triangle referenced a vertex index outside [0, nv) */
 #define LDNI_ST_EVENTS 64u        /* offsetting: a ray met more samples than one warp orders; left empty */
+#define LDNI_ST_BOUNDS 128u       /* checked builds only (LDNI_CHECKS): a CSR or slab index outside its array
+                                     was met and that access skipped; release builds never set it */
 
 /* ---- modes and operations ------------------------------------------ */
 #define LDNI_AXIS_X 0
@@ -280,6 +282,12 @@ int32_t ldni_get_wait_limit(void);
  * LDNI_ST_TIMEOUT once the stream reaches that point.  Nothing else is
  * touched, and the device stays usable. */
 int ldni_wait_selftest(ldni_info_t *info, void *stream);
+
+/* 1 when the loaded library is a checked build (compiled with LDNI_CHECKS:
+ * CSR and slab ranges are tested before they are touched and reported as
+ * LDNI_ST_BOUNDS), 0 for a release build.  A debugging aid in place of a
+ * memory checker; no GPU needed. */
+int32_t ldni_build_checked(void);
 
 /* ---- batches ------------------------------------------------------------ */
 

@@ -23,7 +23,7 @@ MODE_LEARNED1 = 1
 MODE_BINNED2 = 2
 OP_UNION, OP_INTER, OP_DIFF = 0, 1, 2
 
-ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX, ST_EVENTS = 1, 2, 4, 8, 16, 32, 64
+ST_CAPACITY, ST_ODD, ST_TOOLARGE, ST_TIMEOUT, ST_RANGE, ST_INDEX, ST_EVENTS, ST_BOUNDS = 1, 2, 4, 8, 16, 32, 64, 128
 
 
 class Grid(ctypes.Structure):
@@ -126,6 +126,7 @@ SIGNATURES = {
     "ldni_set_wait_limit": (ctypes.c_int, [_I32]),
     "ldni_get_wait_limit": (ctypes.c_int32, []),
     "ldni_wait_selftest": (ctypes.c_int, [_P, _P]),
+    "ldni_build_checked": (ctypes.c_int32, []),
     "ldni_get_tuning": (ctypes.c_int, [_P]),
     "ldni_set_tuning": (ctypes.c_int, [_P]),
     "ldni_sample_batch_workspace_size": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_SZ)]),

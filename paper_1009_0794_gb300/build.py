@@ -15,7 +15,9 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
-BUILD = os.path.join(PKG, "_build")
+# LDNI_BUILD_DIR puts a variant build (other LDNI_EXTRA_NVCC_FLAGS, e.g. the
+# checked build) beside the default one instead of over it.
+BUILD = os.environ.get("LDNI_BUILD_DIR") or os.path.join(PKG, "_build")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(BUILD, "libldni.so")
 

@@ -139,6 +139,15 @@ __device__ __forceinline__ bool general_ray(int a, int ae, int b, int be, int ca
     return ae > capA || be > capB || !((na == 0 || na == 2) && (nb == 0 || nb == 2));
 }
 
+// Bit s set when one of the first c outputs copies sample s.
+__device__ __forceinline__ unsigned src_needs(unsigned src, int c) {
+    unsigned need = 0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+        if (m < c) need |= 1u << src_of(src, m);
+    return need;
+}
+
 // The count pass's word of a ray in closed form (not general_ray): the count
 // (at most 4) in the low bits, the outputs' sources from bit kSrcShift on.
 // A general ray's word is its count.
@@ -740,7 +749,8 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
             set_status(info, LDNI_ST_ODD);
         }
         gen[k] = general_ray(ra[k], ra[k + 1], rb[k], rb[k + 1], capA, capB);
-        const bool pa = !gen[k] && na == 2, pb = !gen[k] && nb == 2;
+        const bool pa = !gen[k] && na == 2 && range_ok(ra[k], ra[k] + 2, capA, info);
+        const bool pb = !gen[k] && nb == 2 && range_ok(rb[k], rb[k] + 2, capB, info);
         a0[k] = pa ? A.d[ra[k]] : 0.0f;
         a1[k] = pa ? A.d[ra[k] + 1] : 0.0f;
         b0[k] = pb ? B.d[rb[k]] : 0.0f;
@@ -950,6 +960,9 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
         const unsigned src = (unsigned)(it.at >> kItemSrcShift) & 0xffu;
         const int c = (int)(it.at >> (kItemSrcShift + 8));
         const long long at0 = it.at & ((1ll << kItemSrcShift) - 1);
+        if (!range_ok(it.ra, it.ra + ((src_needs(src, c) & 3u) ? 2 : 0), capA, info) ||
+            !range_ok(it.rb, it.rb + ((src_needs(src, c) & 12u) ? 2 : 0), capB, info))
+            continue;
         if (c == 2 && (src == 0x4u || src == 0xEu) && at0 + 1 < o.cap) {
             // one operand's pair, in order (most rays): a plain copy
             const bool fb = src == 0xEu;
@@ -974,10 +987,7 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
             o.tri[at0 + 1] = (int)(v1.t | tb);
             continue;
         }
-        unsigned need = 0;  // bit s: some output copies sample s
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            if (m < c) need |= 1u << src_of(src, m);
+        const unsigned need = src_needs(src, c);
         Smp a0, a1, b0, b1;  // every sample the ray copies, loaded before any store
         load_smp(A, need & 1u, three, it.ra, a0);
         load_smp(A, need & 2u, three, it.ra + 1, a1);

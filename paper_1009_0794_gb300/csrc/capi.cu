@@ -131,6 +131,8 @@ extern "C" int ldni_set_wait_limit(int32_t polls) {
 
 extern "C" int32_t ldni_get_wait_limit(void) { return ldni::g_wait_limit.load(); }
 
+extern "C" int32_t ldni_build_checked(void) { return ldni::kChecked ? 1 : 0; }
+
 extern "C" int ldni_wait_selftest(ldni_info_t *info, void *stream) {
     if (!info) return LDNI_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);

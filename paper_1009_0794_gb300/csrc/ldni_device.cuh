@@ -72,4 +72,21 @@ __device__ __forceinline__ void set_status(ldni_info_t *info, unsigned bits) {
     if (info) atomicOr(&info->status, bits);
 }
 
+// Checked builds (-DLDNI_CHECKS, a debugging aid in place of a memory
+// checker): every CSR and slab range a kernel is about to touch is tested
+// against its array; a range outside it is reported as LDNI_ST_BOUNDS and
+// the access skipped, so the kernel neither faults nor traps.  Release builds
+// compile the test away (the ranges are then guaranteed by construction).
+#ifdef LDNI_CHECKS
+constexpr bool kChecked = true;
+#else
+constexpr bool kChecked = false;
+#endif
+// [i0, i1) within [0, n)
+__device__ __forceinline__ bool range_ok(long long i0, long long i1, long long n, ldni_info_t *info) {
+    if (!kChecked || (0 <= i0 && i0 <= i1 && i1 <= n)) return true;
+    set_status(info, LDNI_ST_BOUNDS);
+    return false;
+}
+
 }  // namespace ldni

@@ -62,6 +62,7 @@ struct LImg {
     float4 *nrm;                 // per-triangle unit normal (x, y, z, 0): one 16-byte load per sample
     long long slab_cap;
     int *any_over;
+    ldni_info_t *info;           // the call's status (checked builds report out-of-range indices there)
 };
 
 template <class T>
@@ -305,13 +306,13 @@ __device__ __forceinline__ void onepass_hit(int a, long long p, float d, int t, 
         atomicAdd(pick3(o.count, a) + p, 1);
         if (exiting) atomicAdd(pick3(o.exitc, a) + p, 1);
         const long long slot = pick3(o.slab_base, a)[tile] + (p & (kTilePix - 1)) * 2 + exiting;
-        o.slab[slot] = make_int2(__float_as_int(d), t);
+        if (range_ok(slot, slot + 1, o.slab_cap, o.info)) o.slab[slot] = make_int2(__float_as_int(d), t);
         return;
     }
     const int k = atomicAdd(pick3(o.count, a) + p, 1);
     if (k < kt) {
         const long long slot = pick3(o.slab_base, a)[tile] + (p & (kTilePix - 1)) * kt + k;
-        o.slab[slot] = make_int2(__float_as_int(d), t);
+        if (range_ok(slot, slot + 1, o.slab_cap, o.info)) o.slab[slot] = make_int2(__float_as_int(d), t);
     } else {
         pick3(o.over, a)[tile] = 1;
         *o.any_over = 1;
@@ -389,6 +390,7 @@ __device__ __forceinline__ void redo_hit(int a, long long p, float d, int t, con
         set_status(info, LDNI_ST_CAPACITY);
         return;
     }
+    if (!range_ok(slot, slot + 1, pick3(o.cap, a), info)) return;
     pick3(o.depth, a)[slot] = d;
     pick3(o.tri, a)[slot] = t;
     if (float *Y = pick3(o.ny, a)) {
@@ -557,6 +559,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
             continue;
         }
         const long long s0 = tbase + (p & (kTilePix - 1)) * kt;
+        if (!range_ok(b, e, cap, info) || (!t_over && !range_ok(s0, s0 + c, o.slab_cap, info))) continue;
         if (t_over) {  // filled exactly by the redo pass: order in place
             sort_ray_global(b, e, r.D, r.Tr, r.X, r.Y, r.Z);
             continue;
@@ -648,6 +651,9 @@ __global__ void __launch_bounds__(kThreads) order_deep(long long nrays, int ax_l
                     const long long e = off[p + 1];
                     const int c = (int)(e - b);
                     if (c > kLanePer && e <= cap && (t_over || c <= kt)) n = c;
+                    const long long s0 = sb[tile] + (p & (kTilePix - 1)) * kt;
+                    if (n && (!range_ok(b, e, cap, o.info) || (!t_over && !range_ok(s0, s0 + c, o.slab_cap, o.info))))
+                        n = 0;
                 }
                 if (t_over)  // the same in every lane: a chunk lies in one tile
                     order_warp_rays<true>(b, n, b, in_place, r, st, lane);
@@ -812,6 +818,7 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     o.nrm = w.nrm;
     o.slab_cap = w.slab_cap;
     o.any_over = w.any_over;
+    o.info = info;
 
     if (int rc_ = cuda_check(cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s))) return rc_;
     if (overflow_tiles) if (int rc_ = cuda_check(cudaMemsetAsync(overflow_tiles, 0, sizeof(int32_t), s))) return rc_;

@@ -165,6 +165,7 @@ __global__ void __launch_bounds__(kThreads) sort_rays(long long nrays, int ax_lo
                 set_status(info, LDNI_ST_ODD);
             }
             if (e > cap) e = cap;
+            if (!range_ok(b, max(b, e), cap, info)) e = b;
             if (e - b == 2) {
                 const float d0 = r.D[b], d1 = r.D[b + 1];
                 const int t0 = r.Tr[b], t1 = r.Tr[b + 1];

@@ -56,7 +56,8 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
     __syncthreads();
     DF acc{0.0f, 0.0f};
     if (!s_odd) {
-        const long long s0 = off[R0], s1 = min((long long)off[R1], cap);
+        long long s0 = off[R0], s1 = min((long long)off[R1], cap);
+        if (!range_ok(s0, max(s0, s1), cap, info)) s1 = s0;  // (checked builds)
         const bool aligned = (s0 & 1) == 0;  // 8-byte pairs when the run starts on an even sample
         for (long long k = s0 + 2LL * threadIdx.x; k + 1 < s1; k += 2LL * kThreads) {
             float lo, hi;
@@ -82,6 +83,7 @@ __global__ void __launch_bounds__(kThreads) volume_kernel(long long nrays, const
                 continue;
             }
             if (e > cap) e = cap;
+            if (!range_ok(b, max(b, e), cap, info)) continue;  // (checked builds)
             for (long long k = b; k + 1 < e; k += 2) {
                 DF diff;
                 two_sum(d[k + 1], -d[k], diff.hi, diff.lo);

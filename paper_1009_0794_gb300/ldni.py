@@ -147,6 +147,8 @@ def info_decode(info: torch.Tensor) -> dict:
 
 
 def _raise_status(st: int, what: str):
+    if st & _lib.ST_BOUNDS:  # checked builds only
+        raise _lib.LDNIError(-1, what + " (an index outside its array; checked build)")
     if st & _lib.ST_INDEX:
         raise _lib.LDNIError(-1, what + " (triangle vertex index out of range)")
     if st & _lib.ST_RANGE:
