@@ -61,6 +61,17 @@ struct Out {
     long long cap;
 };
 
+// Elements i, i + 1 of a 4-byte array as one 8-byte access (i even, the
+// array 8-byte aligned).
+template <class T>
+__device__ __forceinline__ uint2 ld_pair(const T *a, long long i) {
+    return *reinterpret_cast<const uint2 *>(a + i);
+}
+template <class T>
+__device__ __forceinline__ void st_pair(T *a, long long i, uint2 v) {
+    *reinterpret_cast<uint2 *>(a + i) = v;
+}
+
 // The images of one call: job j is out[j] = A[j] op B[j], all on one grid.
 // Kernels take it as a __grid_constant__ parameter and index it by job.
 constexpr int kMaxJobs = LDNI_MAX_IMAGES;
@@ -71,6 +82,7 @@ struct BoolJobs {
     ldni_info_t *info[kMaxJobs];
     double *vol[kMaxJobs];  // optional: volume of each result
     bool packed;            // 8-bit normals (one word) instead of FP32 nx, ny, nz, for every image of the call
+    bool pairs8;            // every sample array of the call 8-byte aligned: a pair at an even index is one 8-byte access
 };
 
 // One output sample at slot `at` from sample idx of A or B.
@@ -751,10 +763,24 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
         gen[k] = general_ray(ra[k], ra[k + 1], rb[k], rb[k + 1], capA, capB);
         const bool pa = !gen[k] && na == 2 && range_ok(ra[k], ra[k] + 2, capA, info);
         const bool pb = !gen[k] && nb == 2 && range_ok(rb[k], rb[k] + 2, capB, info);
-        a0[k] = pa ? A.d[ra[k]] : 0.0f;
-        a1[k] = pa ? A.d[ra[k] + 1] : 0.0f;
-        b0[k] = pb ? B.d[rb[k]] : 0.0f;
-        b1[k] = pb ? B.d[rb[k] + 1] : 0.0f;
+        a0[k] = a1[k] = b0[k] = b1[k] = 0.0f;
+        if (J.pairs8 && ((ra[k] | rb[k]) & 1) == 0) {  // even rows: each depth pair is one 8-byte load
+            if (pa) {
+                const uint2 v = ld_pair(A.d, ra[k]);
+                a0[k] = __uint_as_float(v.x);
+                a1[k] = __uint_as_float(v.y);
+            }
+            if (pb) {
+                const uint2 v = ld_pair(B.d, rb[k]);
+                b0[k] = __uint_as_float(v.x);
+                b1[k] = __uint_as_float(v.y);
+            }
+        } else {
+            a0[k] = pa ? A.d[ra[k]] : 0.0f;
+            a1[k] = pa ? A.d[ra[k] + 1] : 0.0f;
+            b0[k] = pb ? B.d[rb[k]] : 0.0f;
+            b1[k] = pb ? B.d[rb[k] + 1] : 0.0f;
+        }
     }
     int cnt[kR], word[kR];
     int mine = 0;
@@ -968,11 +994,24 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
             const bool fb = src == 0xEu;
             const Side &S = fb ? B : A;
             const int i0 = fb ? it.rb : it.ra;
+            const uint32_t f = fb ? flip : 0u;
+            const uint32_t tb = fb ? 0x80000000u : 0u;
+            if (J.pairs8 && ((i0 | (int)at0) & 1) == 0) {
+                // rows and output slots of closed solids are even: each field's pair is one 8-byte access
+                const uint2 d = ld_pair(S.d, i0), x = ld_pair(S.nx, i0), t = ld_pair(S.tri, i0);
+                st_pair(o.d, at0, d);
+                st_pair(o.nx, at0, make_uint2(x.x ^ f, x.y ^ f));
+                if (three) {
+                    const uint2 y = ld_pair(S.ny, i0), z = ld_pair(S.nz, i0);
+                    st_pair(o.ny, at0, make_uint2(y.x ^ f, y.y ^ f));
+                    st_pair(o.nz, at0, make_uint2(z.x ^ f, z.y ^ f));
+                }
+                st_pair(o.tri, at0, make_uint2(t.x | tb, t.y | tb));
+                continue;
+            }
             Smp v0, v1;
             load_smp(S, true, three, i0, v0);
             load_smp(S, true, three, i0 + 1, v1);
-            const uint32_t f = fb ? flip : 0u;
-            const uint32_t tb = fb ? 0x80000000u : 0u;
             o.d[at0] = v0.d;
             o.d[at0 + 1] = v1.d;
             o.nx[at0] = __uint_as_float(v0.x ^ f);
@@ -1164,6 +1203,14 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
             all[3 * j + 2] = out + j;
         }
         if (!same_format(all, 3 * count, &J.packed)) return LDNI_EINVAL;
+        J.pairs8 = true;
+        for (int k = 0; k < 3 * count; ++k) {
+            float *x, *y, *z;
+            normal_arrays(*all[k], x, y, z);
+            for (const void *q : {(const void *)all[k]->depth, (const void *)x, (const void *)y, (const void *)z,
+                                  (const void *)all[k]->tri_id})
+                J.pairs8 &= (reinterpret_cast<uintptr_t>(q) & 7) == 0;
+        }
     }
     for (int j = 0; j < count; ++j) {
         if (!layers_ok(A + j, true) || !layers_ok(B + j, true) || !layers_ok(out + j, true)) return LDNI_EINVAL;
