@@ -63,6 +63,7 @@ struct LImg {
     long long slab_cap;
     int *any_over;
     ldni_info_t *info;           // the call's status (checked builds report out-of-range indices there)
+    bool pairs8;                 // every output array 8-byte aligned (a pair at an even slot: one 8-byte store)
 };
 
 template <class T>
@@ -580,6 +581,18 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int a
                 v1 = w;
             }
             const float4 q0 = NRM[v0.y], q1 = NRM[v1.y];
+            if (o.pairs8 && (b & 1) == 0) {  // even slots (closed meshes): one 8-byte store per field
+                *reinterpret_cast<int2 *>(r.D + b) = make_int2(v0.x, v1.x);
+                *reinterpret_cast<int2 *>(r.Tr + b) = make_int2(v0.y, v1.y);
+                if (r.Y) {
+                    *reinterpret_cast<float2 *>(r.X + b) = make_float2(q0.x, q1.x);
+                    *reinterpret_cast<float2 *>(r.Y + b) = make_float2(q0.y, q1.y);
+                    *reinterpret_cast<float2 *>(r.Z + b) = make_float2(q0.z, q1.z);
+                } else {
+                    *reinterpret_cast<float2 *>(r.X + b) = make_float2(q0.w, q1.w);
+                }
+                continue;
+            }
             r.D[b] = __int_as_float(v0.x);
             r.D[b + 1] = __int_as_float(v1.x);
             r.Tr[b] = v0.y;
@@ -819,6 +832,11 @@ extern "C" int ldni_sample_learned(const float *verts, int64_t nv, const int32_t
     o.slab_cap = w.slab_cap;
     o.any_over = w.any_over;
     o.info = info;
+    o.pairs8 = true;
+    for (int a = ax_lo; a <= ax_lo + naxes - 1; ++a)
+        for (const void *q : {(const void *)o.depth[a], (const void *)o.nx[a], (const void *)o.ny[a],
+                              (const void *)o.nz[a], (const void *)o.tri[a]})
+            o.pairs8 &= (reinterpret_cast<uintptr_t>(q) & 7) == 0;
 
     if (int rc_ = cuda_check(cudaMemsetAsync(w.count[0], 0, w.clear_bytes, s))) return rc_;
     if (overflow_tiles) if (int rc_ = cuda_check(cudaMemsetAsync(overflow_tiles, 0, sizeof(int32_t), s))) return rc_;
