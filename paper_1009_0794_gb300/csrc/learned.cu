@@ -35,6 +35,9 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxLayerCap = 64;   // largest k_t the layout hands out
+#ifndef LDNI_ONEPASS_BATCH
+#define LDNI_ONEPASS_BATCH 2
+#endif
 #ifndef LDNI_ONEPASS_BLOCKS
 #define LDNI_ONEPASS_BLOCKS 5
 #endif
@@ -320,6 +323,62 @@ __device__ __forceinline__ void onepass_hit(int a, long long p, float d, int t, 
     }
 }
 
+// The crossings of one (triangle, image) pair, kHitBatch at a time: their
+// tiles' layer counts are read, then every slot of a tile with more than two
+// layers is claimed (a returned atomic on the ray's count) before any sample
+// is stored, so the claims' round trips overlap instead of following one
+// another.  Two-layer tiles take the shortcut of onepass_hit.  m: the box's
+// crossings, bit x + w y for pixel (i0 + x, j0 + y).
+constexpr int kHitBatch = LDNI_ONEPASS_BATCH;
+template <int A>
+__device__ __forceinline__ void onepass_hits(const Setup32 &S, unsigned m, int t, const float3 &n, int res,
+                                             const LImg &o) {
+    const int wdiv = (256 + S.w - 1) / S.w;  // y = (b * wdiv) >> 8 = b / w for b < 16, w <= 16
+    int *cnt = pick3(o.count, A);
+    const int *kc = pick3(o.kcap, A);
+    const long long *sb = pick3(o.slab_base, A);
+    while (m) {
+        int pr[kHitBatch], kt[kHitBatch], k[kHitBatch];
+        float d[kHitBatch];
+        long long base[kHitBatch];
+        bool v[kHitBatch];
+#pragma unroll
+        for (int u = 0; u < kHitBatch; ++u) {
+            v[u] = m != 0u;
+            const int b = v[u] ? __ffs(m) - 1 : 0;
+            m &= m - 1u;
+            const int y = (b * wdiv) >> 8, x = b - y * S.w;
+            int e0, e1, e2;
+            S.edges(S.i0 + x, S.j0 + y, e0, e1, e2);
+            pr[u] = (S.j0 + y) * res + S.i0 + x;
+            d[u] = S.depth_from(e0, e1, e2);
+            const int tile = pr[u] >> kTileBits;
+            kt[u] = v[u] ? kc[tile] : 2;
+            base[u] = v[u] ? sb[tile] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kHitBatch; ++u) k[u] = v[u] && kt[u] != 2 ? atomicAdd(cnt + pr[u], 1) : 0;
+#pragma unroll
+        for (int u = 0; u < kHitBatch; ++u) {
+            if (!v[u]) continue;
+            const int q = pr[u] & (kTilePix - 1);
+            long long slot;
+            if (kt[u] == 2) {
+                atomicAdd(cnt + pr[u], 1);
+                if (S.exiting) atomicAdd(pick3(o.exitc, A) + pr[u], 1);
+                slot = base[u] + q * 2 + S.exiting;
+            } else if (k[u] < kt[u]) {
+                slot = base[u] + (long long)q * kt[u] + k[u];
+            } else {
+                pick3(o.over, A)[pr[u] >> kTileBits] = 1;
+                *o.any_over = 1;
+                continue;
+            }
+            if (range_ok(slot, slot + 1, o.slab_cap, o.info)) o.slab[slot] = make_int2(__float_as_int(d[u]), t);
+        }
+    }
+}
+
 template <int A>
 __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const float3 &n, int res, const LImg &o,
                                              int *big_q, long long qcap, int *big_n) {
@@ -328,6 +387,10 @@ __device__ __forceinline__ void onepass_axis(const TriView &T, int t, const floa
     if (kind == kNone) return;
     if (kind == kBig) {
         enqueue_big(big_q, qcap, big_n, t * 4 + A, (long long)S.w * S.h);
+        return;
+    }
+    if (kHitBatch > 1 && (S.w > 2 || S.h > 2)) {  // (boxes of up to 2 x 2 centres: the loop-free visit)
+        onepass_hits<A>(S, S.hit_bits(), t, n, res, o);
         return;
     }
     S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {

@@ -94,6 +94,8 @@ struct Setup32 {
     // come in row-major order.
     template <class F>
     __device__ __forceinline__ void for_each_hit(F &&f) const;
+    // the box's crossings as bits x + w y (w * h <= kBigPixels)
+    __device__ __forceinline__ unsigned hit_bits() const;
 };
 
 // 64-bit form for triangles too large for Setup32.
@@ -216,6 +218,22 @@ __device__ __forceinline__ void Setup32::for_each_hit(F &&f) const {
             f(i0 + x, j0 + y, e0, e1, e2);
         }
     }
+}
+
+__device__ __forceinline__ unsigned Setup32::hit_bits() const {
+    if (w <= 2 && h <= 2) {  // loop-free, as in for_each_hit
+        int r0, r1, r2;
+        edges(i0, j0, r0, r1, r2);
+        const int s0 = -(v1 - v0) * kSubpix, s1 = -(v2 - v1) * kSubpix, s2 = -(v0 - v2) * kSubpix;
+        const int t0 = (u1 - u0) * kSubpix, t1 = (u2 - u1) * kSubpix, t2 = (u0 - u2) * kSubpix;
+        const unsigned w2 = w == 2, h2 = h == 2;
+        const unsigned c00 = (r0 > 0) & (r1 > 0) & (r2 > 0);
+        const unsigned c10 = w2 & (r0 + s0 > 0) & (r1 + s1 > 0) & (r2 + s2 > 0);
+        const unsigned c01 = h2 & (r0 + t0 > 0) & (r1 + t1 > 0) & (r2 + t2 > 0);
+        const unsigned c11 = w2 & h2 & (r0 + s0 + t0 > 0) & (r1 + s1 + t1 > 0) & (r2 + s2 + t2 > 0);
+        return c00 | (c10 << 1) | (c01 << w) | (c11 << (w + 1));  // bit x + w y
+    }
+    return (unsigned)hit_mask(*this);
 }
 
 // 64-bit setup of image a for a queued big triangle; false when parallel.
