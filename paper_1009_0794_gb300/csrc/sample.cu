@@ -72,6 +72,57 @@ __device__ __forceinline__ void emit(float d, int a, int t, long long p, const f
     }
 }
 
+// The fill pass over a triangle's box, two crossings at a time: both slot
+// claims (returned atomics on the rays' cursors) and both row offsets are in
+// flight before either sample is stored.  m: the box's crossings, bit x + w y.
+template <int A>
+__device__ __forceinline__ void fill_hits(const Setup32 &S, unsigned m, int t, const float3 &n, const Img &o, int res,
+                                          ldni_info_t *info) {
+    const int wdiv = (256 + S.w - 1) / S.w;  // y = (b * wdiv) >> 8 = b / w for b < 16, w <= 16
+    int *cnt = o.count[A];
+    const int *off = o.offsets[A];
+    const long long cap = o.cap[A];
+    while (m) {
+        int pr[2], k[2], row[2];
+        float d[2];
+        bool v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            v[u] = m != 0u;
+            const int b = v[u] ? __ffs(m) - 1 : 0;
+            m &= m - 1u;
+            const int y = (b * wdiv) >> 8, x = b - y * S.w;
+            int e0, e1, e2;
+            S.edges(S.i0 + x, S.j0 + y, e0, e1, e2);
+            pr[u] = (S.j0 + y) * res + S.i0 + x;
+            d[u] = S.depth_from(e0, e1, e2);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            k[u] = v[u] ? atomicSub(cnt + pr[u], 1) - 1 : -1;
+            row[u] = v[u] ? off[pr[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!v[u]) continue;
+            const long long slot = (long long)row[u] + k[u];
+            if (k[u] < 0 || slot >= cap) {
+                set_status(info, LDNI_ST_CAPACITY);
+                continue;
+            }
+            o.depth[A][slot] = d[u];
+            o.tri[A][slot] = t;
+            if (float *Y = o.ny[A]) {
+                o.nx[A][slot] = n.x;
+                Y[slot] = n.y;
+                o.nz[A][slot] = n.z;
+            } else {  // approximate normals (Section 3 item 1)
+                o.nx[A][slot] = __uint_as_float(encode_normal8(n.x, n.y, n.z));
+            }
+        }
+    }
+}
+
 template <bool kFill, int A>
 __device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &n, const Img &o, int res, int *big_q,
                                          long long qcap, int *big_n, ldni_info_t *info) {
@@ -86,9 +137,7 @@ __device__ __forceinline__ void tri_axis(const TriView &T, int t, const float3 &
         S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(o.count[A] + (long long)j * res + i, 1); });
         return;
     }
-    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
-        emit<true>(S.depth_from(e0, e1, e2), A, t, (long long)j * res + i, n, o, info);
-    });
+    fill_hits<A>(S, S.hit_bits(), t, n, o, res, info);
 }
 
 // One thread per triangle; big triangles are queued (count pass) for big_pass.
