@@ -111,6 +111,57 @@ __device__ __forceinline__ void batch_emit(const ldni_batch_item_t &it, int a, l
     }
 }
 
+// The fill pass over a triangle's box, two crossings at a time: both slot
+// claims and both row offsets are in flight before either sample is stored
+// (as the single-mesh fill).  mk: the box's crossings, bit x + w y.
+template <int A>
+__device__ __forceinline__ void batch_fill_hits(const ldni_batch_item_t &it, const Setup32 &S, unsigned mk, int t,
+                                                const float3 &n, int *cnt, int res, ldni_info_t *info) {
+    const ldni_layers_t &L = it.out[A];
+    const int *off = L.offsets;
+    const long long cap = L.capacity;
+    const int wdiv = (256 + S.w - 1) / S.w;  // y = (b * wdiv) >> 8 = b / w for b < 16, w <= 16
+    while (mk) {
+        int pr[2], k[2], row[2];
+        float d[2];
+        bool v[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            v[u] = mk != 0u;
+            const int b = v[u] ? __ffs(mk) - 1 : 0;
+            mk &= mk - 1u;
+            const int y = (b * wdiv) >> 8, x = b - y * S.w;
+            int e0, e1, e2;
+            S.edges(S.i0 + x, S.j0 + y, e0, e1, e2);
+            pr[u] = (S.j0 + y) * res + S.i0 + x;
+            d[u] = S.depth_from(e0, e1, e2);
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            k[u] = v[u] ? atomicSub(cnt + pr[u], 1) - 1 : -1;
+            row[u] = v[u] ? off[pr[u]] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            if (!v[u]) continue;
+            const long long slot = (long long)row[u] + k[u];
+            if (k[u] < 0 || slot >= cap) {
+                set_status(info, LDNI_ST_CAPACITY);
+                continue;
+            }
+            L.depth[slot] = d[u];
+            L.tri_id[slot] = t;
+            if (L.nrm8) {  // approximate normals (Section 3 item 1)
+                L.nrm8[slot] = encode_normal8(n.x, n.y, n.z);
+            } else {
+                L.nx[slot] = n.x;
+                L.ny[slot] = n.y;
+                L.nz[slot] = n.z;
+            }
+        }
+    }
+}
+
 template <bool kFill, int A>
 __device__ __forceinline__ void batch_axis(const ldni_batch_item_t &it, int m, const TriView &Tv, int t,
                                            const float3 &n, int res, int *counts, const Tables &T, ldni_info_t *info) {
@@ -127,9 +178,7 @@ __device__ __forceinline__ void batch_axis(const ldni_batch_item_t &it, int m, c
         S.for_each_hit([&](int i, int j, int, int, int) { atomicAdd(cnt + (long long)j * res + i, 1); });
         return;
     }
-    S.for_each_hit([&](int i, int j, int e0, int e1, int e2) {
-        batch_emit<true>(it, A, (long long)j * res + i, S.depth_from(e0, e1, e2), t, n, cnt, info);
-    });
+    batch_fill_hits<A>(it, S, S.hit_bits(), t, n, cnt, res, info);
 }
 
 template <bool kFill>
