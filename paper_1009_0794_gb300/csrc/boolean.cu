@@ -713,18 +713,18 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 // ---- three launches per image -----------------------------------------------
 //
 // No block waits for another.  Each thread owns kR consecutive rays and reads
-// their rows and depths straight from global memory: a ray of kind 1 or 2
-// needs its two depths, issued for all the thread's rays before any is used;
-// every other ray runs the general merge.
+// their rows and depths straight from global memory.  A ray with at most one
+// interval per operand (kinds 0, 1, 2 and 4) is answered in closed form from
+// its depths, issued for all the thread's rays before any is used; every
+// other ray runs the general merge.  Both passes are compiled per operation.
 
 // Pass 1: output count of every ray (kept in the output's offset array,
-// which pass 3 overwrites in place; a ray of kind 4 keeps its outputs'
+// which pass 3 overwrites in place; a closed-form ray keeps its outputs'
 // sources beside the count, from bit kSrcShift on) and of every tile of the
-// write pass
-// (tile_total, cleared before the launch; 2^wshift rays per tile, tpjw tiles
-// per job).  The count pass has its own rays per thread (kR): a warp's 32 * kR
-// rays lie in one write tile, so each warp adds its sum to that tile's total.
-// tpj: count blocks per job.
+// write pass (tile_total, cleared before the launch; 2^wshift rays per tile,
+// tpjw tiles per job).  The count pass has its own rays per thread (kR): a
+// warp's 32 * kR rays lie in one write tile, so each warp adds its sum to
+// that tile's total.  tpj: count blocks per job.
 #ifndef LDNI_BOOL_COUNT_BLOCKS
 #define LDNI_BOOL_COUNT_BLOCKS 6
 #endif
@@ -906,11 +906,10 @@ __device__ __forceinline__ void load_smp(const Side &S, bool on, bool three, lon
 
 // Pass 3: the block first writes its tile's offsets (kR rays per thread),
 // listing every ray with output samples in shared memory, and then its
-// threads take the listed rays in turn: first the rays of kinds 1, 2 and 4,
-// which copy samples of their one or two pairs (every sample a ray copies is
-// loaded before any of its stores; a kind-4 ray's sources come from pass 1,
-// so samples it drops are not read), then the rays of kind 3 (general
-// merge).  Rays without samples (often half of an image) thus leave no
+// threads take the listed rays in turn: first the closed-form rays, which
+// copy samples of their one or two pairs (their sources come from pass 1, so
+// samples a ray drops are not read; every sample a ray copies is loaded
+// before any of its stores), then the rays of the general merge.  Rays without samples (often half of an image) thus leave no
 // thread idle while the others wait on memory, and a block covers kR times
 // as many rays with the same registers per thread.
 struct CopyItem {
