@@ -726,7 +726,7 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 // warp's 32 * kR rays lie in one write tile, so each warp adds its sum to
 // that tile's total.  tpj: count blocks per job.
 #ifndef LDNI_BOOL_COUNT_BLOCKS
-#define LDNI_BOOL_COUNT_BLOCKS 6
+#define LDNI_BOOL_COUNT_BLOCKS 8
 #endif
 template <int kR, int kOp>
 __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)

@@ -569,7 +569,11 @@ __device__ __forceinline__ void put_sample(const RayOut &o, long long at, float 
     }
 }
 
-__global__ void __launch_bounds__(kThreads) gather_kernel(long long nrays, int ax_lo, LImg o, ldni_info_t *info,
+#ifndef LDNI_GATHER_BLOCKS
+#define LDNI_GATHER_BLOCKS 8
+#endif
+__global__ void __launch_bounds__(kThreads, LDNI_GATHER_BLOCKS) gather_kernel(long long nrays, int ax_lo, LImg o,
+                                                                             ldni_info_t *info,
                                                           int *n_over) {
     const int a = ax_lo + blockIdx.y;
     const int *off = pick3(o.offsets, a);
