@@ -287,7 +287,7 @@ def algorithmic_bytes(kid: int, nv: int, nt: int, res: int, n: list, n_knot: lis
         17: mesh + 3 * 4.0 * N + 8.0 * ns,
         # gather: counts and slab records read, offsets and CSR samples written
         20: 3 * 4.0 * N + 8.0 * ns + 3 * 4.0 * (N + 1) + 20.0 * ns,
-        # Boolean, three-launch form: count reads rows and depths, writes counts;
+        # Boolean, two-launch form: count reads rows and depths, writes counts;
         # write reads rows, counts and the kept operands' samples, writes the result
         9: 3 * (8.0 * (N + 1) + 4.0 * N) + 4.0 * (ns + nk),
         10: 3 * (8.0 * (N + 1) + 4.0 * N + 4.0 * (N + 1)) + 20.0 * (ns + nk) + 20.0 * nu,
@@ -1021,11 +1021,11 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": ab_k or None,
             "gbs": (ab_k / (st_ms * 1e-3) / 1e9) if ab_k else None,
             "frac_of_measured_hbm": (ab_k / (st_ms * 1e-3) / 1e9 / peak) if ab_k else None}
-    # the whole merge of the step (count, tile scan, write of three images) against its algorithmic bytes
+    # the whole merge of the step (count and write passes of three images) against its algorithmic bytes
     N = RES * RES
-    merge_ms = sum(totals.get(k, 0.0) for k in (9, 32, 10))
+    merge_ms = sum(totals.get(k, 0.0) for k in (9, 10))
     mb = merge_bytes(N, sum(n_sphere), sum(L.n for L in K), sum(n_union))
-    merge = {"kernels": ["bool_count", "bool_scan", "bool_write"], "ms_per_step": merge_ms,
+    merge = {"kernels": ["bool_count", "bool_write"], "ms_per_step": merge_ms,
              "algorithmic_bytes": mb, "gbs": mb / (merge_ms * 1e-3) / 1e9 if merge_ms else None,
              "frac_of_measured_hbm": mb / (merge_ms * 1e-3) / 1e9 / peak if merge_ms else None,
              "bytes_formula": "12 B per ray and image (both operands' offsets, the result's) + 20 B per operand "

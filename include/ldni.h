@@ -256,8 +256,8 @@ typedef struct {
     int32_t bool_stage_samples;  /* samples of a Boolean tile staged in shared memory,
                                     0 (merge from global memory) .. 16384 */
     int32_t tri_blocks_per_sm;   /* grid of the per-triangle sampling passes, 1 .. 64 */
-    int32_t bool_split;          /* Boolean as one launch (0), as count / tile scan / write
-                                    launches (1), or chosen by image size (-1) */
+    int32_t bool_split;          /* Boolean as one launch (0), as count and write launches (1),
+                                    or chosen by image size (-1) */
 } ldni_tuning_t;
 
 /* Current knobs (defaults: 512, 4096, 16, -1). */
@@ -658,10 +658,10 @@ int64_t ldni_profile_recorded(void);
 
 /* Name of a kernel id (1 count_tri, 2 count_big, 4 scan_tiles, 5 scan,
  * 6 fill_tri, 7 fill_big, 8 sort_rays, 9 bool_count and 10 bool_write (the
- * count and write passes of the three-launch Boolean), 11 volume, 13 boolean, 14 features,
+ * count and write passes of the two-launch Boolean), 11 volume, 13 boolean, 14 features,
  * 15 capacity, 16 layout, 17 onepass, 18 onepass_big, 19 redo, 20 gather,
  * 21 mlp, 22 adjoint, 23 batch, 24 nodes, 25 order, 26 offset, 27 normals8, 28 contour, 29 chain, 30 bin,
- * 31 tile, 32 bool_scan). */
+ * 31 tile; 3, 12 and 32 are retired ids, named "unused"). */
 const char *ldni_kernel_name(int32_t id);
 
 #ifdef __cplusplus

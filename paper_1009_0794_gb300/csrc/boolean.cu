@@ -16,9 +16,11 @@
 //   - one launch per image (bool_tiled): a block stages its tile's sample
 //     arrays in shared memory with bulk copies, counts its rays, scans,
 //     finds its first output slot by decoupled look-back and writes;
-//   - three launches per image (bool_count, bool_scan_tiles, bool_write):
-//     no block ever waits for another; the result's volume, when asked for,
-//     is summed by the count pass and finished by the tile scan;
+//   - two launches per image (bool_count, bool_write): no block ever waits
+//     for another; a write tile's first output slot is the sum of the tile
+//     and super-tile totals before it, read directly; the result's volume,
+//     when asked for, is summed by the count pass and finished by the last
+//     write block of the image;
 //   - the two-pass form behind ldni_boolean_static (bool_pass + csr_scan).
 // Launch shapes are chosen by the tuning knobs (ldni_set_tuning).
 #include <climits>
@@ -710,7 +712,12 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
     }
 }
 
-// ---- three launches per image -----------------------------------------------
+// ---- two launches per image -------------------------------------------------
+//
+// Super-tiles of 2^gshift write tiles, at most kMaxSupers per image: a write
+// block reads at most kMaxSupers super-tile totals and 2^gshift - 1 tile
+// totals to find its first output slot.
+constexpr int kMaxSupers = 256;
 //
 // No block waits for another.  Each thread owns kR consecutive rays and reads
 // their rows and depths straight from global memory.  A ray with at most one
@@ -720,18 +727,20 @@ __global__ void __launch_bounds__(kBoolThreads) bool_tiled(long long N, const __
 
 // Pass 1: output count of every ray (kept in the output's offset array,
 // which pass 3 overwrites in place; a closed-form ray keeps its outputs'
-// sources beside the count, from bit kSrcShift on) and of every tile of the
+// sources beside the count, from bit kSrcShift on), of every tile of the
 // write pass (tile_total, cleared before the launch; 2^wshift rays per tile,
-// tpjw tiles per job).  The count pass has its own rays per thread (kR): a
-// warp's 32 * kR rays lie in one write tile, so each warp adds its sum to
-// that tile's total.  tpj: count blocks per job.
+// tpjw tiles per job) and of every super-tile of 2^gshift write tiles
+// (super_total, kMaxSupers per job, cleared).  The count pass has its own
+// rays per thread (kR): a warp's 32 * kR rays lie in one write tile, so each
+// warp adds its sum to that tile's and that super-tile's totals.  tpj: count
+// blocks per job.
 #ifndef LDNI_BOOL_COUNT_BLOCKS
 #define LDNI_BOOL_COUNT_BLOCKS 8
 #endif
 template <int kR, int kOp>
 __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
-    bool_count(int N, const __grid_constant__ BoolJobs J, float eps, unsigned long long *tile_total, int tpj,
-               int wshift, int tpjw, float2 *vol_part) {
+    bool_count(int N, const __grid_constant__ BoolJobs J, float eps, unsigned long long *tile_total,
+               unsigned long long *super_total, int tpj, int wshift, int gshift, int tpjw, float2 *vol_part) {
     // Index arithmetic is 32-bit: rays (at most 8192^2) and rows (int) fit.
     constexpr int kRays = kR * kBoolThreads;
     const int job = blockIdx.y, tile = blockIdx.x;  // the grid is tpj x jobs
@@ -819,6 +828,7 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
     if ((threadIdx.x & 31) == 0 && mine) {
         const int pw = p0 + (threadIdx.x >> 5) * 32 * kR;  // the warp's first ray
         atomicAdd(tile_total + (size_t)job * tpjw + (pw >> wshift), (unsigned long long)mine);
+        atomicAdd(super_total + (size_t)job * kMaxSupers + (pw >> (wshift + gshift)), (unsigned long long)mine);
     }
     if (!want_vol) return;  // block-uniform
 #pragma unroll
@@ -826,63 +836,6 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_COUNT_BLOCKS)
         len = df_add_lazy(len, DF{__shfl_down_sync(0xffffffffu, len.hi, w), __shfl_down_sync(0xffffffffu, len.lo, w)});
     if ((threadIdx.x & 31) == 0)
         vol_part[((size_t)job * tpj + tile) * (kBoolThreads / 32) + (threadIdx.x >> 5)] = make_float2(len.hi, len.lo);
-}
-
-// Pass 2: exclusive prefix of the tile totals (one block of 1024 threads,
-// kPer consecutive totals per thread and round).
-__global__ void __launch_bounds__(1024) bool_scan_tiles(const unsigned long long *tile_total_all, int ntiles,
-                                                        long long *tile_pre_all, long long N,
-                                                        const __grid_constant__ BoolJobs J, const float2 *vol_part,
-                                                        int nvol, double h2) {
-    constexpr int kPer = 4;
-    const int job = blockIdx.x;  // one block per job
-    const unsigned long long *tile_total = tile_total_all + (size_t)job * ntiles;
-    long long *tile_pre = tile_pre_all + (size_t)job * ntiles;
-    __shared__ long long sh[1024 / 32 + 1];
-    // the first round of the volume partials is loaded first, so that it is
-    // in flight during the scan
-    constexpr int kVol = 8;
-    const float2 *wv = vol_part ? vol_part + (size_t)job * nvol : nullptr;
-    float2 vp[kVol];
-#pragma unroll
-    for (int u = 0; u < kVol; ++u) {
-        const int k = threadIdx.x + u * 1024;
-        vp[u] = wv && k < nvol ? __ldcg(wv + k) : make_float2(0.0f, 0.0f);
-    }
-    long long carry = 0;
-    for (int b0 = 0; b0 < ntiles; b0 += 1024 * kPer) {
-        const int k0 = b0 + threadIdx.x * kPer;
-        long long v[kPer], sum = 0;
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            v[u] = k0 + u < ntiles ? (long long)tile_total[k0 + u] : 0;
-            sum += v[u];
-        }
-        long long tot;
-        long long run = carry + block_exclusive_scan<1024>(sum, sh, &tot);
-#pragma unroll
-        for (int u = 0; u < kPer; ++u) {
-            if (k0 + u < ntiles) tile_pre[k0 + u] = run;
-            run += v[u];
-        }
-        carry += tot;
-    }
-    if (threadIdx.x == 0) finish_output(J.o[job], N, carry, J.info[job]);
-    if (vol_part) {  // the volume: the count pass's nvol warp partials of this job in a fixed order
-        __shared__ DF shdf[1024 / 32];
-        DF acc{0.0f, 0.0f};
-#pragma unroll
-        for (int u = 0; u < kVol; ++u) acc = df_add_lazy(acc, DF{vp[u].x, vp[u].y});
-        for (int k0 = threadIdx.x + 1024 * kVol; k0 < nvol; k0 += 1024 * kVol) {
-#pragma unroll
-            for (int u = 0; u < kVol; ++u)
-                vp[u] = k0 + u * 1024 < nvol ? __ldcg(wv + k0 + u * 1024) : make_float2(0.0f, 0.0f);
-#pragma unroll
-            for (int u = 0; u < kVol; ++u) acc = df_add_lazy(acc, DF{vp[u].x, vp[u].y});
-        }
-        const DF t = df_block_sum<1024>(acc, shdf);
-        if (threadIdx.x == 0) *J.vol[job] = ((double)t.hi + (double)t.lo) * h2;
-    }
 }
 
 // One sample's fields as loaded (normals as raw words: FP32 or one packed word).
@@ -904,7 +857,7 @@ __device__ __forceinline__ void load_smp(const Side &S, bool on, bool three, lon
 #define LDNI_BOOL_WRITE_BLOCKS 6
 #endif
 
-// Pass 3: the block first writes its tile's offsets (kR rays per thread),
+// Pass 2: the block first writes its tile's offsets (kR rays per thread),
 // listing every ray with output samples in shared memory, and then its
 // threads take the listed rays in turn: first the closed-form rays, which
 // copy samples of their one or two pairs (their sources come from pass 1, so
@@ -919,13 +872,24 @@ struct CopyItem {
 };
 constexpr int kItemSrcShift = 48;  // output slots stay below 2^48
 
+// The tile's first output slot is the sum of the totals of every earlier tile
+// of its image, which pass 1 left complete: the super-tile totals before the
+// tile's super-tile, then the tile totals of its own super-tile before it,
+// read directly.  With volumes asked for (vol_part), the volume of image j
+// is summed by the block of tile j mod tpj of the first image, one of the
+// first blocks to start: after its own rays it adds all of the count warps'
+// partials of image j in a fixed order (pass 1 left them complete: nothing
+// waits).  The block of an image's last tile writes the image's total.
 template <int kR, int kOp>
 __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
-    bool_write(int N, const __grid_constant__ BoolJobs J, float eps, const long long *tile_pre, int tpj) {
+    bool_write(int N, const __grid_constant__ BoolJobs J, float eps, const unsigned long long *tile_total,
+               const unsigned long long *super_total, int tpj, int gshift, const float2 *vol_part, int nvol,
+               double h2) {
     constexpr int op = kOp;
     constexpr int kRays = kR * kBoolThreads;
     constexpr int kItemBits = 20;  // items per tile < 2^20 in the low bits of the scanned word
     __shared__ long long sh[kBoolThreads / 32 + 1];
+    __shared__ long long s_pre[kBoolThreads / 32];
     __shared__ CopyItem items[kRays];  // copies from the front, merges from the back
     __shared__ int s_merges;
     const int job = blockIdx.y, tile = blockIdx.x;  // the grid is tpj x jobs
@@ -936,7 +900,14 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
     const int p0 = tile * kRays;  // 32-bit index arithmetic, as in pass 1
     const int nr = min(kRays, N - p0);
     const int q0 = threadIdx.x * kR;
-    const long long tile_base = tile_pre[(size_t)job * tpj + tile];
+    const int lane = threadIdx.x & 31;
+    // the totals of the earlier tiles: one load each from the first threads, issued before the rows and
+    // used after them (tiles beyond the first kBoolThreads of a super-tile: only for images of more than
+    // 2^24 rays)
+    const int sup = tile >> gshift, first = sup << gshift;  // sup < kMaxSupers
+    const unsigned long long sv = (int)threadIdx.x < sup ? super_total[(size_t)job * kMaxSupers + threadIdx.x] : 0ull;
+    const unsigned long long tv = first + (int)threadIdx.x < tile ? tile_total[(size_t)job * tpj + first + threadIdx.x]
+                                                                  : 0ull;
     const int capA = (int)min(A.cap, (long long)INT_MAX), capB = (int)min(B.cap, (long long)INT_MAX);
     const bool three = !J.packed;
     if (threadIdx.x == 0) s_merges = 0;  // ordered before its first use by the block scan's barriers
@@ -944,6 +915,17 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
     load_rows<kR>(A.off + p0, 0, q0, nr, ra);
     load_rows<kR>(B.off + p0, 0, q0, nr, rb);
     load_rows<kR>(o.off + p0, 0, q0, nr, cnt);  // pass 1's words (cnt[kR] unused)
+    long long pre = (long long)(sv + tv);
+    for (int k = first + (int)threadIdx.x + kBoolThreads; k < tile; k += kBoolThreads)
+        pre += (long long)tile_total[(size_t)job * tpj + k];
+    // each warp's share of the carry (warps that loaded nothing skip the sum)
+    const int first_idle = max(sup, tile - first);  // threads from here on loaded nothing
+    if ((int)(threadIdx.x & ~31u) < first_idle) {  // warp-uniform
+#pragma unroll
+        for (int w = 16; w > 0; w >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, w);
+    }
+    // read by the block scan after its first barrier, shifted past the item bits of the scanned word
+    if (lane == 0) s_pre[threadIdx.x >> 5] = pre << kItemBits;
     bool gen[kR];
     unsigned src[kR];
     long long mine = 0;
@@ -958,8 +940,10 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
         listed += !gen[k] && cnt[k] > 0;
     }
     long long total;
-    const long long ex = block_exclusive_scan<kBoolThreads>((mine << kItemBits) | listed, sh, &total);
-    const long long base = tile_base + (ex >> kItemBits);
+    // the earlier tiles' total enters the scan as its carry
+    const long long ex = block_exclusive_scan_carry<kBoolThreads>((mine << kItemBits) | listed, s_pre, sh, &total);
+    if (tile == tpj - 1 && threadIdx.x == 0) finish_output(o, N, (ex >> kItemBits) + (total >> kItemBits), info);
+    const long long base = ex >> kItemBits;
     const int nitems = (int)(total & ((1 << kItemBits) - 1));
     {
         int w[kR];
@@ -1062,6 +1046,25 @@ __global__ void __launch_bounds__(kBoolThreads, LDNI_BOOL_WRITE_BLOCKS)
             emit_global(cb, (cb ? b0 : a0) + ci, A, B, op, o, at0 + m + 1, info);
         });
     }
+    if (!vol_part || job != 0) return;  // block-uniform
+    __shared__ DF shdf[kBoolThreads / 32];
+    for (int vjob = tile; vjob < (int)gridDim.y; vjob += tpj) {  // the images whose volumes this block sums
+        // the image's nvol partials, strided per thread in a fixed order, then a fixed tree
+        constexpr int kU = 8;
+        const float2 *vp = vol_part + (size_t)vjob * nvol;
+        DF acc{0.0f, 0.0f};
+        for (int k0 = threadIdx.x; k0 < nvol; k0 += kBoolThreads * kU) {
+            float2 v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u)
+                v[u] = k0 + u * kBoolThreads < nvol ? vp[k0 + u * kBoolThreads] : make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int u = 0; u < kU; ++u) acc = df_add_lazy(acc, DF{v[u].x, v[u].y});
+        }
+        const DF t = df_block_sum<kBoolThreads>(acc, shdf);
+        if (threadIdx.x == 0) *J.vol[vjob] = ((double)t.hi + (double)t.lo) * h2;
+        __syncthreads();  // shdf is reused by the next image
+    }
 }
 
 // ---- host side ------------------------------------------------------------------
@@ -1158,14 +1161,19 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
                                                                        tile_vol, h2, wait_limit()));
         return cuda_status();
     }
-    // workspace: tile totals (cleared) | tile prefixes | volume partials (one per count warp)
+    // super-tiles of 2^gshift write tiles, at most kMaxSupers per job
+    int gshift = 5;
+    while (((long long)tpj + (1ll << gshift) - 1) >> gshift > kMaxSupers) ++gshift;
+    // workspace: tile totals | super-tile totals (cleared together) | volume partials (one per count warp)
     unsigned long long *tile_total = words;
-    long long *tile_pre = reinterpret_cast<long long *>(tile_total + nblocks);
-    float2 *vol_part = J.vol[0] ? reinterpret_cast<float2 *>(tile_pre + nblocks) : nullptr;
-    if (int rc_ = cuda_check(cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * (size_t)nblocks, s)))
+    unsigned long long *super_total = tile_total + nblocks;
+    const size_t cleared = (size_t)nblocks + (size_t)kMaxSupers * njobs;
+    float2 *vol_part = J.vol[0] ? reinterpret_cast<float2 *>(words + cleared) : nullptr;
+    if (int rc_ = cuda_check(cudaMemsetAsync(tile_total, 0, sizeof(unsigned long long) * cleared, s)))
         return rc_;
     constexpr int kRc = kBoolCountRays;
     const int tpjc = (int)((N + kRc * kBoolThreads - 1) / (kRc * kBoolThreads));  // count blocks per job
+    const int nvol = tpjc * (kBoolThreads / 32);
     auto count = op == LDNI_OP_UNION   ? bool_count<kRc, LDNI_OP_UNION>
                  : op == LDNI_OP_INTER ? bool_count<kRc, LDNI_OP_INTER>
                                        : bool_count<kRc, LDNI_OP_DIFF>;
@@ -1173,12 +1181,11 @@ int launch_bool(long long N, const BoolJobs &J, int njobs, int op, float eps, vo
                  : op == LDNI_OP_INTER ? bool_write<kR, LDNI_OP_INTER>
                                        : bool_write<kR, LDNI_OP_DIFF>;
     LDNI_LAUNCH(K_BOOL_COUNT, s,
-                count<<<dim3(tpjc, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_total, tpjc, __builtin_ctz(kRays),
-                                                                 tpj, vol_part));
-    LDNI_LAUNCH(K_BOOL_SCAN, s,
-                bool_scan_tiles<<<njobs, 1024, 0, s>>>(tile_total, tpj, tile_pre, N, J, vol_part,
-                                                       tpjc * (kBoolThreads / 32), h2));
-    LDNI_LAUNCH(K_BOOL_WRITE, s, write<<<dim3(tpj, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_pre, tpj));
+                count<<<dim3(tpjc, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_total, super_total, tpjc,
+                                                                 __builtin_ctz(kRays), gshift, tpj, vol_part));
+    LDNI_LAUNCH(K_BOOL_WRITE, s,
+                write<<<dim3(tpj, njobs), kBoolThreads, 0, s>>>((int)N, J, eps, tile_total, super_total, tpj, gshift,
+                                                               vol_part, nvol, h2));
     return cuda_status();
 }
 
@@ -1227,7 +1234,7 @@ int boolean_jobs(int32_t count, const ldni_layers_t *A, const ldni_layers_t *B, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int budget = tune.bool_stage_samples;
     const int rays = tune.bool_tile_rays;
-    // small images: one staged launch; large ones: count, tile scan, write
+    // small images: one staged launch; large ones: count, then write
     const int form = tune.bool_split >= 0 ? tune.bool_split : (N * count / rays > 2 * (long long)num_sms() ? 1 : 0);
     const double h = (double)grid->width / (double)grid->res;
     switch (rays) {
@@ -1250,9 +1257,10 @@ extern "C" int ldni_boolean_workspace_size(int32_t res, size_t *bytes) {
 extern "C" int ldni_boolean_many_workspace_size(int32_t res, int32_t count, size_t *bytes) {
     if (!bytes || res < 1 || res > 8192 || count < 1 || count > kMaxJobs) return LDNI_EINVAL;
     // look-back words and ticket of the one-launch form, or tile totals,
-    // tile prefixes and warp volumes of the three-launch form, for the
+    // super-tile totals and warp volumes of the two-launch form, for the
     // smallest tile
-    *bytes = align_up(sizeof(long long) * ((2 + kBoolThreads / 32) * bool_ws_words((long long)res * res) * count + 8));
+    *bytes = align_up(sizeof(long long) * ((2 + kBoolThreads / 32) * bool_ws_words((long long)res * res) * count +
+                                           (size_t)kMaxSupers * count + 8));
     return LDNI_OK;
 }
 

@@ -90,7 +90,7 @@ extern "C" const char *ldni_kernel_name(int32_t id) {
                                              "sort_rays",  "bool_count", "bool_write", "volume",
                                              "unused",     "boolean",    "features",  "capacity",
                                              "layout",     "onepass",    "onepass_big", "redo",
-                                             "gather",     "mlp",        "adjoint",   "batch",      "nodes",     "order",     "offset",    "normals8",  "contour",   "chain",     "bin",       "tile",      "bool_scan"};
+                                             "gather",     "mlp",        "adjoint",   "batch",      "nodes",     "order",     "offset",    "normals8",  "contour",   "chain",     "bin",       "tile",      "unused"};
     return (id >= 0 && id < ldni::K_NUM) ? names[id] : "unknown";
 }
 

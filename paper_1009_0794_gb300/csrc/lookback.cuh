@@ -133,4 +133,40 @@ __device__ __forceinline__ long long block_exclusive_scan(long long v, long long
     return excl;
 }
 
+// The same scan with a carry-in: every thread's prefix also holds the sum of
+// carry[0 .. NT/32 - 1], one partial per warp, stored by the warps before the
+// call (read after its first barrier).  Warp 0 scans the carry partials and
+// then the warp totals as one list of 2 NT/32 values, so the carry costs no
+// step of its own.  *total is the block's own sum, without the carry.
+template <int NT>
+__device__ __forceinline__ long long block_exclusive_scan_carry(long long v, const long long *carry, long long *sh,
+                                                                long long *total) {
+    constexpr int W = NT / 32;
+    static_assert(2 * W <= 32, "carry partials and warp totals share one warp");
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sh[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = lane < W ? carry[lane] : (lane < 2 * W ? sh[lane - W] : 0);
+#pragma unroll
+        for (int o = 1; o < 2 * W; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += y;
+        }
+        if (lane >= W && lane < 2 * W) sh[lane - W] = w;  // carry + warps 0 .. lane - W
+        if (lane == W - 1) sh[W] = w;                     // the carry
+    }
+    __syncthreads();
+    const long long excl = x - v + (warp > 0 ? sh[warp - 1] : sh[W]);
+    *total = sh[W - 1] - sh[W];
+    __syncthreads();
+    return excl;
+}
+
 }  // namespace ldni

@@ -45,7 +45,7 @@ enum KernelId : int {
     K_CHAIN = 29,
     K_BIN = 30,
     K_TILE = 31,
-    K_BOOL_SCAN = 32,
+    K_RETIRED_32 = 32,  // the tile scan of the former three-launch Boolean
     K_NUM = 33
 };
 

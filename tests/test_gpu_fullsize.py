@@ -70,7 +70,7 @@ def _upload(ldni, grid, a, L):
 @pytest.mark.parametrize("eps", [0.0, 1e-5])
 def test_bench_boolean_1024_bit_exact(ldni, bench_images, op, eps):
     """The benchmark's three-image call (default launch form at this size:
-    count, tile scan, write, with the volumes summed in the write pass)."""
+    count and write passes, with the volumes finished in the write pass)."""
     grid, S, K, Sn, Kn = bench_images
     vols = torch.zeros(3, dtype=torch.float64, device="cuda")
     got = ldni.boolean_many(S, K, op, eps=eps, vols=vols)
